@@ -1,0 +1,373 @@
+"""Benchmark: null-space projections per second on one GB300, mixed vs float64 form.
+
+One step = the whole hot path on one batch: rtproj_precondition(seed, l) -- the sketch
+S = A G with G generated on the device, the pivoted QR of S^*, the Gram matrix and its
+Cholesky factor -- followed by rtproj_null_project on k right-hand sides (with the
+refinement pass in the mixed form). value = k * steps / (device time of the timed
+steps), all ranks together; each rank runs an independent replica (one GPU each).
+
+Workload (synthetic, seeded): A = U diag(sigma) V^T, 512 x 65536 float64, U and V Haar,
+sigma log-spaced over [1e-10, 1]; G uniform on (-1, 1) (Philox4x32-10), l = 2048;
+k = 64 right-hand sides with N(0,1) entries. A (268 MB) is larger than L2 (129 MB).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+MEASURED_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+# GB300 FP64 pipe: 152 SMs x 2 DFMA/clk/SM x 2 flop at the 2070 MHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
+
+METRIC = "null-space projections/s & % roofline, mixed vs FP64 form at <=1e-10 rel err"
+
+
+def peaks():
+    if os.path.exists(MEASURED_PEAKS):
+        with open(MEASURED_PEAKS) as f:
+            p = json.load(f)
+        p["_source"] = "measured"
+        return p
+    p = dict(FALLBACK_PEAKS)
+    p["_source"] = "fallback"
+    return p
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def setup_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_step(A, B):
+    from oracle import reference
+    t0 = time.perf_counter()
+    reference.project(A, B)
+    return time.perf_counter() - t0
+
+
+def cpu_cores() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n and n[0]:
+            return int(n[0])
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline(A, B, budget_s: float = 12.0):
+    """The oracle's Householder-QR definition (oracle.reference.project) on the same A and
+    all k right-hand sides, repeated until ~budget_s of CPU work."""
+    times = []
+    t_end = time.perf_counter() + budget_s
+    while time.perf_counter() < t_end or not times:
+        times.append(cpu_oracle_step(A, B))
+        if len(times) >= 20:
+            break
+    t = statistics.median(times)
+    return {"value": B.shape[0] / t, "unit": "projections/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"oracle.reference.project (Householder QR of A^T + apply) on the full {A.shape[0]}x{A.shape[1]} "
+                      f"A and all {B.shape[0]} RHS, median of {len(times)} runs"}
+
+
+def run_reference(args, w, world, rank):
+    if rank != 0:
+        return 0
+    A = w.matrix()
+    B = w.rhs()
+    for _ in range(args.warmup):
+        cpu_oracle_step(A, B)
+    ts = [cpu_oracle_step(A, B) for _ in range(args.steps)]
+    total = sum(ts)
+    value = w.k * args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "m": w.m, "n": w.n, "k": w.k, "l": w.l, "kappa": 1.0 / w.sigma_min,
+                   "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "projections/s", "cores": cpu_cores(), "kind": "oracle",
+                         "sample": "oracle.reference.project on the full workload per step"},
+        "e2e": {"value": value, "unit": "projections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(torch, P, Bt, seed, l, steps, stream):
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(steps):
+        P.precondition(seed + i, l)
+        P.null_project(Bt, out=Zbuf_of(P, Bt))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+_ZBUF = {}
+
+
+def Zbuf_of(P, Bt):
+    key = id(P)
+    if key not in _ZBUF:
+        import torch
+        _ZBUF[key] = torch.empty_like(Bt)
+    return _ZBUF[key]
+
+
+def roofline_entry(mode, phase_ms, phase_cnt, w, pk, opts):
+    """Dominant phase -> achieved vs peak (algorithmic work per launch / mean duration)."""
+    m, n, l, k = w.m, w.n, w.l, w.k
+    if mode == "fp64":
+        work = {
+            "sketch": 2.0 * m * n * l,
+            "gram": 2.0 * m * m * n + 2.0 * m * m * n,
+            "apply_a": 2.0 * m * n * k,
+            "apply_at": 2.0 * m * n * k,
+        }
+        dom = max(work, key=lambda p: phase_ms.get(p, 0.0))
+        per_launch_ms = phase_ms[dom] / max(1, phase_cnt[dom])
+        achieved = work[dom] / (per_launch_ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": f"gemm64_kernel ({dom})", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)"}
+    return None
+
+
+def run_ours(args, w, world, rank, local):
+    import torch
+    import paper_0912_1135_gb300 as rt
+    from oracle import exact, metrics
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk = peaks()
+    A = w.matrix()
+    B = w.rhs()
+    At = torch.from_numpy(A).to(dev)
+    Bt = torch.from_numpy(B).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    seed0 = w.seed_omega
+    out = {}
+
+    P = rt.Projector(At, l_max=w.l, k_max=w.k, mode=args.mode, timing=1)
+    for i in range(args.warmup):
+        P.precondition(seed0 + i, w.l)
+        P.null_project(Bt, out=Zbuf_of(P, Bt))
+    torch.cuda.synchronize()
+    P.timings()
+    launches0 = rt.launch_count()
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier(world)
+    ms = time_steps(torch, P, Bt, seed0 + 1000, w.l, args.steps, stream)
+    barrier(world)
+    clocks = sampler.stop()
+    launches = rt.launch_count() - launches0
+    tim = P.timings()
+    ms_max = max_over_ranks(ms, world)
+    value = world * w.k * args.steps / (ms_max * 1e-3)
+    phase_ms = {p: v[0] for p, v in tim.items()}
+    phase_cnt = {p: v[1] for p, v in tim.items()}
+
+    # accuracy of the timed configuration: sampled RHS against the exact oracle
+    Z = Zbuf_of(P, Bt).cpu().numpy()
+    resid = metrics.normalised_residual(A, Z, B, normA=1.0)
+    acc = {"normalised_residual_max": resid}
+    if not args.no_accuracy and rank == 0:
+        Zx, _, _ = exact.exact_project(A, B[:1])
+        acc["z_rel_err_vs_exact_oracle"] = metrics.max_rel_err(Z[:1], Zx)
+        acc["sample"] = "RHS 0 against oracle.exact (double-double refinement)"
+    P.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "projections/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "bf16-slices/f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "mode": args.mode, "m": w.m, "n": w.n, "k": w.k, "l": w.l,
+                   "kappa": 1.0 / w.sigma_min, "omega": "uniform(-1,1), Philox4x32-10",
+                   "step": "precondition(seed, l) + null_project(k RHS)",
+                   "l2": "inputs larger than L2 (A is 268 MB float64)", "parallelism": f"replicas x{world}"},
+        "phase_ms_per_step": {p: phase_ms[p] / args.steps for p in phase_ms if phase_cnt[p]},
+        "accuracy": acc,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    rl = roofline_entry(args.mode, phase_ms, phase_cnt, w, pk, P.opts)
+    if rl is not None:
+        line["roofline"] = rl
+
+    if not args.no_e2e:
+        line["e2e"] = e2e(torch, rt, A, B, w, args, dev)
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(A, B)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def e2e(torch, rt, A, B, w, args, dev):
+    """Same metric through the public API from pinned host buffers: per step the H2D copy of
+    A and B, create + precondition + null_project, and the D2H copy of Z."""
+    Ah = torch.from_numpy(A).pin_memory()
+    Bh = torch.from_numpy(B).pin_memory()
+    Zh = torch.empty(B.shape, dtype=torch.float64).pin_memory()
+    steps = max(1, min(args.steps, 5))
+    stream = torch.cuda.current_stream(dev)
+
+    def one(i):
+        Ad = Ah.to(dev, non_blocking=True)
+        Bd = Bh.to(dev, non_blocking=True)
+        with rt.Projector(Ad, l_max=w.l, k_max=w.k, mode=args.mode) as P:
+            P.precondition(w.seed_omega + i, w.l)
+            Z = P.null_project(Bd)
+            Zh.copy_(Z, non_blocking=True)
+            stream.synchronize()
+
+    one(0)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    t0 = time.perf_counter()
+    for i in range(steps):
+        one(i + 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return {"value": w.k * steps / wall, "unit": "projections/s", "h2d_bytes_per_step": int(A.nbytes + B.nbytes),
+            "d2h_bytes_per_step": int(B.nbytes), "steps": steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--workload", default="dense_512x65536", choices=sorted(workloads.WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    w = workloads.WORKLOADS[args.workload]
+    world, rank, local = setup_dist() if args.impl == "ours" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")))
+    if args.impl == "reference":
+        return run_reference(args, w, world, rank)
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    barrier(world)
+    return run_ours(args, w, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

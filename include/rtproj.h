@@ -1,0 +1,193 @@
+/*
+ * rtproj.h -- C ABI of the GB300 (sm_103a) randomized orthogonal projection library.
+ *
+ * Method: Rokhlin & Tygert, "A fast randomized algorithm for orthogonal projection"
+ * (arXiv 0912.1135). For a full-rank real m x n matrix A (m <= n) the library
+ * computes, for blocks of right-hand sides b,
+ *   - the projection onto the null space of A, Zb = b - A^*(AA^*)^{-1}Ab   (Eq. 1),
+ *     through the preconditioned form of Eq. 11;
+ *   - the projection onto the row space, A^* h;
+ *   - the least-squares solution h = argmin ||A^* h - b||                 (Remark 4.1).
+ * The preconditioner P = Pi^* R^* comes from a pivoted QR of the sketch S = A G
+ * (Eqs. 12-13), G an n x l random matrix generated on the device and never stored.
+ *
+ * Conventions (all functions):
+ *   - Matrices are row-major float64. A is m x n with leading dimension lda >= n.
+ *     Right-hand sides are stored as ROWS: B is k x n (row j is the j-th vector b),
+ *     ldb >= n; null/row-space outputs are k x n; least-squares outputs are k x m.
+ *   - Pointers named A, B, Z, ROW, H, S, workspace are DEVICE pointers unless the
+ *     comment says otherwise. The library never allocates device memory: all
+ *     scratch lives in the caller's workspace. It never frees caller memory.
+ *   - A is borrowed: it must stay alive and unchanged from rtproj_create until
+ *     rtproj_destroy (or the next rtproj_create on the same memory).
+ *   - All work is enqueued on the stream given to rtproj_create (a cudaStream_t
+ *     passed as void*; NULL means the legacy default stream). Calls are
+ *     asynchronous except rtproj_precondition, rtproj_get_info, rtproj_export_state
+ *     and rtproj_sketch, which synchronize that stream once.
+ *   - Errors: invalid arguments return immediately with a status and enqueue
+ *     nothing. Conditions found on the device (rank deficiency, Cholesky breakdown,
+ *     non-finite values, an expired bounded wait) are latched in a device status
+ *     word; rtproj_precondition returns it, and rtproj_get_info reports it for
+ *     the apply calls. No kernel traps, asserts or waits without a bound.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef RTPROJ_H
+#define RTPROJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rtproj_ctx* rtproj_t;
+
+typedef enum {
+    RTPROJ_OK = 0,
+    RTPROJ_EINVAL = 1,       /* invalid argument: sizes, leading dimensions, null pointer */
+    RTPROJ_ESTATE = 2,       /* apply called before a successful rtproj_precondition      */
+    RTPROJ_ERANK = 3,        /* |R_mm| <= rank_tol * |R_11| after the pivoted QR of S^*:
+                                A G is numerically rank deficient (Lemma 2.4 needs full rank) */
+    RTPROJ_ENOTSPD = 4,      /* Cholesky of X = P^{-1} A A^* P^{-*} broke down            */
+    RTPROJ_ENONFINITE = 5,   /* a NaN or infinity reached the factorizations             */
+    RTPROJ_ETIMEOUT = 6,     /* a bounded device-side wait gave up                        */
+    RTPROJ_ENOMEM = 7,       /* workspace smaller than rtproj_workspace_bytes()           */
+    RTPROJ_ECUDA = 8,        /* a CUDA runtime call failed                                */
+    RTPROJ_EUNSUPPORTED = 9  /* option combination not supported                          */
+} rtproj_status;
+
+/* Arithmetic of the whole path. */
+typedef enum {
+    /* Every product in float64 on the FP64 pipe (the plain float64 form). */
+    RTPROJ_PLAIN_FP64 = 0,
+    /* Products with A on the bfloat16 tensor cores through exact fixed-point slicing
+       (each operand split into s bfloat16 slices of 8 bits; slice products summed
+       exactly in float32 and combined in 64-bit integers), a low-slice sketch,
+       and one or more refinement passes (Remark 4.3) whose residuals carry more
+       than float64 accuracy. The m x m stage stays in float64. */
+    RTPROJ_MIXED_REFINED = 1
+} rtproj_mode;
+
+/* Distribution of the entries of G (Eq. 12). Entry (i, j) of G takes byte
+   u = byte (i & 3) of word ((i & 15) >> 2) of Philox4x32-10 (Salmon et al., SC'11)
+   at counter (i >> 4, j, 0, 0) with key (seed mod 2^32, seed >> 32). */
+typedef enum {
+    RTPROJ_OMEGA_UNIFORM = 0,     /* (2u - 255)/256: uniform on (-1,1), as in Tables 1, 2, 5, 6 */
+    RTPROJ_OMEGA_RADEMACHER = 1   /* +1 if u >= 128 else -1                                    */
+} rtproj_omega;
+
+typedef struct {
+    int mode;            /* rtproj_mode (default RTPROJ_MIXED_REFINED)                    */
+    int omega;           /* rtproj_omega (default RTPROJ_OMEGA_UNIFORM)                   */
+    int sketch_slices;   /* mixed: slices of A in S = A G            (default 4, 1..8)   */
+    int gram_slices;     /* mixed: slices in W = P^{-1} A            (default 7, 1..8)   */
+    int gram2_slices;    /* mixed: slices in X = W W^*               (default 3, 1..8)   */
+    int apply_slices;    /* mixed: slices in c = A b and A^* dh      (default 7, 1..8)   */
+    int resid_slices;    /* mixed: slices in the refinement residual (default 8, 1..8)   */
+    int refine_passes;   /* mixed: refinement passes                 (default 1, 0..4)   */
+    int timing;          /* 1: record CUDA events around each phase (rtproj_get_timings)  */
+    double rank_tol;     /* ERANK threshold; <= 0 selects 64 * l * 2^-52                  */
+} rtproj_opts;
+
+/* Phases timed when opts.timing is set (indices into rtproj_get_timings' arrays). */
+typedef enum {
+    RTPROJ_PHASE_SKETCH = 0,    /* S = A G (Eq. 12), Omega generation included        */
+    RTPROJ_PHASE_QR = 1,        /* pivoted QR of S^* (Eq. 13)                          */
+    RTPROJ_PHASE_GRAM = 2,      /* W = P^{-1} A and X = W W^* (Eq. 14, steps a-e)      */
+    RTPROJ_PHASE_FACTOR = 3,    /* R^{-*}, Cholesky of X, T1 = L^{-1} R^{-*}           */
+    RTPROJ_PHASE_APPLY_A = 4,   /* reductions over n: c = A b, r = A s                 */
+    RTPROJ_PHASE_APPLY_M = 5,   /* the m x m stage (steps 2-6)                         */
+    RTPROJ_PHASE_APPLY_AT = 6,  /* products with A^*: b - A^* h, row = A^* h           */
+    RTPROJ_PHASE_SLICE = 7,     /* mixed mode: slicing of operands into bfloat16 planes */
+    RTPROJ_NUM_PHASES = 8
+} rtproj_phase;
+
+typedef struct {
+    int status;              /* latched device status (an rtproj_status value)            */
+    int preconditioned;      /* 1 after a successful rtproj_precondition                  */
+    int64_t m, n, l;
+    double r11, rmm;         /* |R_11| and |R_mm| of the pivoted QR of S^*                */
+    double l11, lmm;         /* largest and smallest diagonal entries of chol(X)          */
+    float ms_precondition;   /* device time of the last rtproj_precondition (ms)          */
+} rtproj_info;
+
+/* Fills *opts with the defaults listed above. */
+void rtproj_default_opts(rtproj_opts* opts);
+
+/* Device workspace (bytes) needed for an m x n matrix, sketches with l <= l_max and
+   applies with k <= k_max right-hand sides, under opts (NULL: defaults). Returns 0
+   for invalid sizes. The workspace must be 256-byte aligned. */
+size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max,
+                              const rtproj_opts* opts);
+
+/* Creates a handle bound to the device matrix A (m x n, row-major, lda >= n, 1 <= m <= n),
+   the caller's device workspace and stream. In the mixed mode it also enqueues the
+   slicing of A into bfloat16 slice planes (kept in the workspace). The current CUDA
+   device must be the one that holds A and the workspace. */
+rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A, int64_t lda,
+                            int64_t l_max, int64_t k_max, void* workspace, size_t ws_bytes,
+                            void* stream, const rtproj_opts* opts);
+
+/* Builds the preconditioner from seed and l (m <= l <= min(n, l_max); Section 4):
+   the sketch S = A G (Eq. 12), the pivoted QR S^* = Q R Pi (Eq. 13), and the Gram
+   matrix X = P^{-1} A A^* P^{-*} (Eq. 14, steps a-e) factored by Cholesky in place of
+   the explicit inverse Y = X^{-1} of Eq. 16. Synchronizes the stream once and returns
+   the latched device status (RTPROJ_ERANK, RTPROJ_ENOTSPD, RTPROJ_ENONFINITE). */
+rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l);
+
+/* Null-space projection (Eq. 11; the seven steps of Section 4, then b - b~):
+   Z = rows of Zb for the k rows of B (k <= k_max). Z may alias B exactly
+   (Z == B, ldz == ldb) but must not partially overlap it. */
+rtproj_status rtproj_null_project(rtproj_t h, const double* B, int64_t ldb, int64_t k,
+                                  double* Z, int64_t ldz);
+
+/* Row-space projection b~ = A^* h (step 7 of Section 4), k x n into ROW. */
+rtproj_status rtproj_row_project(rtproj_t h, const double* B, int64_t ldb, int64_t k,
+                                 double* ROW, int64_t ldr);
+
+/* Least-squares solutions h = argmin ||A^* h - b|| (Remark 4.1), k x m into X. */
+rtproj_status rtproj_lstsq(rtproj_t h, const double* B, int64_t ldb, int64_t k,
+                           double* X, int64_t ldx);
+
+/* All three outputs of one apply; any output pointer may be NULL. */
+rtproj_status rtproj_project(rtproj_t h, const double* B, int64_t ldb, int64_t k,
+                             double* Z, int64_t ldz, double* ROW, int64_t ldr,
+                             double* X, int64_t ldx);
+
+/* Sketch only: S = A G (Eq. 12) into the device buffer S (m x l, row-major, lds >= l),
+   in the handle's mode (float64 products, or sketch_slices bfloat16 slices of A).
+   Synchronizes. Used to test the sketch step on its own. */
+rtproj_status rtproj_sketch(rtproj_t h, uint64_t seed, int64_t l, double* S, int64_t lds);
+
+/* Copies the preconditioner state to HOST buffers (any may be NULL): R (m x m,
+   row-major, upper triangular), perm (m entries: position j of the pivoted QR holds
+   original column perm[j] of S^*, so (Pi x)[j] = x[perm[j]]), and Lc (m x m, the
+   lower-triangular Cholesky factor of X). Synchronizes. */
+rtproj_status rtproj_export_state(rtproj_t h, double* R, int32_t* perm, double* Lc);
+
+/* Synchronizes, then returns per phase the device milliseconds (ms[p]) and the number
+   of timed occurrences (count[p]) accumulated since the previous call, and resets them.
+   Arrays have RTPROJ_NUM_PHASES entries; either may be NULL. Needs opts.timing = 1. */
+rtproj_status rtproj_get_timings(rtproj_t h, double* ms, int64_t* count);
+
+/* Number of kernels this library has enqueued since it was loaded (all handles). */
+uint64_t rtproj_launch_count(void);
+
+/* Synchronizes the stream and reports the latched status and diagnostics. */
+rtproj_status rtproj_get_info(rtproj_t h, rtproj_info* info);
+
+/* Clears the latched device status (after the caller handled it). */
+rtproj_status rtproj_clear_status(rtproj_t h);
+
+/* Releases the host-side handle. Does not touch A or the workspace. */
+rtproj_status rtproj_destroy(rtproj_t h);
+
+/* Static string for a status code. */
+const char* rtproj_status_string(rtproj_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTPROJ_H */

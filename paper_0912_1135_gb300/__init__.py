@@ -1,0 +1,261 @@
+"""Python binding of librtproj (randomized orthogonal projection on GB300).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels of
+``librtproj.so`` behind the C ABI declared in ``include/rtproj.h``. PyTorch supplies
+device memory (the caller-owned workspace and outputs) and the CUDA stream. There is
+no CPU fallback: if the library is missing this module raises on first use.
+
+    >>> P = Projector(A)                 # A: cuda float64, m x n, row-major
+    >>> P.precondition(seed=1, l=4 * m)  # sketch, pivoted QR, Gram, Cholesky
+    >>> Z = P.null_project(B)            # B: k x n (each row a right-hand side)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+__all__ = ["Projector", "RtprojError", "load_library", "library_path", "STATUS", "MODES", "OMEGAS"]
+
+MODES = {"fp64": 0, "mixed": 1}
+OMEGAS = {"uniform": 0, "rademacher": 1}
+STATUS = {
+    0: "RTPROJ_OK", 1: "RTPROJ_EINVAL", 2: "RTPROJ_ESTATE", 3: "RTPROJ_ERANK", 4: "RTPROJ_ENOTSPD",
+    5: "RTPROJ_ENONFINITE", 6: "RTPROJ_ETIMEOUT", 7: "RTPROJ_ENOMEM", 8: "RTPROJ_ECUDA", 9: "RTPROJ_EUNSUPPORTED",
+}
+
+
+class RtprojError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        super().__init__(f"{where}: {STATUS.get(self.code, self.code)}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int), ("omega", ctypes.c_int), ("sketch_slices", ctypes.c_int),
+        ("gram_slices", ctypes.c_int), ("gram2_slices", ctypes.c_int), ("apply_slices", ctypes.c_int),
+        ("resid_slices", ctypes.c_int), ("refine_passes", ctypes.c_int), ("timing", ctypes.c_int),
+        ("rank_tol", ctypes.c_double),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("preconditioned", ctypes.c_int), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
+        ("l", ctypes.c_int64), ("r11", ctypes.c_double), ("rmm", ctypes.c_double), ("l11", ctypes.c_double),
+        ("lmm", ctypes.c_double), ("ms_precondition", ctypes.c_float),
+    ]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+EXPORTS = {
+    "rtproj_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "rtproj_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I64, _I64, ctypes.POINTER(Opts)]),
+    "rtproj_create": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _P, _I64, _I64, _I64, _P, ctypes.c_size_t, _P,
+                                     ctypes.POINTER(Opts)]),
+    "rtproj_precondition": (ctypes.c_int, [_P, ctypes.c_uint64, _I64]),
+    "rtproj_null_project": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _I64]),
+    "rtproj_row_project": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _I64]),
+    "rtproj_lstsq": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _I64]),
+    "rtproj_project": (ctypes.c_int, [_P, _P, _I64, _I64, _P, _I64, _P, _I64, _P, _I64]),
+    "rtproj_sketch": (ctypes.c_int, [_P, ctypes.c_uint64, _I64, _P, _I64]),
+    "rtproj_export_state": (ctypes.c_int, [_P, _P, _P, _P]),
+    "rtproj_get_info": (ctypes.c_int, [_P, ctypes.POINTER(Info)]),
+    "rtproj_clear_status": (ctypes.c_int, [_P]),
+    "rtproj_destroy": (ctypes.c_int, [_P]),
+    "rtproj_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rtproj_get_timings": (ctypes.c_int, [_P, _P, _P]),
+    "rtproj_launch_count": (ctypes.c_uint64, []),
+}
+
+PHASES = ["sketch", "qr", "gram", "factor", "apply_a", "apply_m", "apply_at", "slice"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library():
+    """Loads librtproj.so (built by ``_build.build()``); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"librtproj.so is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise RtprojError(code, where)
+
+
+def default_opts() -> Opts:
+    o = Opts()
+    load_library().rtproj_default_opts(ctypes.byref(o))
+    return o
+
+
+def make_opts(mode="mixed", omega="uniform", **slices) -> Opts:
+    o = default_opts()
+    o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
+    o.omega = OMEGAS[omega] if isinstance(omega, str) else int(omega)
+    for k, v in slices.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _dev_ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Projector:
+    """One matrix A bound to a workspace and a stream (see ``include/rtproj.h``)."""
+
+    def __init__(self, A: torch.Tensor, l_max: int | None = None, k_max: int = 64, mode: str = "mixed",
+                 omega: str = "uniform", stream: torch.cuda.Stream | None = None, **slices):
+        lib = load_library()
+        if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2 and A.stride(1) == 1):
+            raise TypeError("A must be a CUDA float64 matrix with unit column stride")
+        self.A = A
+        self.m, self.n = A.shape
+        self.lda = A.stride(0)
+        self.l_max = int(l_max if l_max is not None else min(self.n, 4 * self.m))
+        self.k_max = int(k_max)
+        self.device = A.device
+        self.opts = make_opts(mode, omega, **slices)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = lib.rtproj_workspace_bytes(self.m, self.n, self.l_max, self.k_max, ctypes.byref(self.opts))
+        if nbytes == 0:
+            raise RtprojError(1, "rtproj_workspace_bytes")
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            code = lib.rtproj_create(ctypes.byref(h), self.m, self.n, _dev_ptr(A), self.lda, self.l_max, self.k_max,
+                                     _dev_ptr(self.workspace), ctypes.c_size_t(int(nbytes)),
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.opts))
+        _check(code, "rtproj_create")
+        self._h = h
+
+    # -- lifecycle -------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().rtproj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- preconditioner ----------------------------------------------------------------
+    def precondition(self, seed: int, l: int | None = None):
+        l = self.l_max if l is None else int(l)
+        with torch.cuda.device(self.device):
+            _check(load_library().rtproj_precondition(self._h, ctypes.c_uint64(seed), l), "rtproj_precondition")
+        self.l = l
+        return self
+
+    def sketch(self, seed: int, l: int) -> torch.Tensor:
+        S = torch.empty((self.m, l), dtype=torch.float64, device=self.device)
+        with torch.cuda.device(self.device):
+            _check(load_library().rtproj_sketch(self._h, ctypes.c_uint64(seed), l, _dev_ptr(S), l), "rtproj_sketch")
+        return S
+
+    def export_state(self):
+        import numpy as np
+        R = np.empty((self.m, self.m))
+        perm = np.empty(self.m, dtype=np.int32)
+        L = np.empty((self.m, self.m))
+        _check(load_library().rtproj_export_state(self._h, R.ctypes.data_as(_P), perm.ctypes.data_as(_P),
+                                                  L.ctypes.data_as(_P)), "rtproj_export_state")
+        return R, perm, L
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(load_library().rtproj_get_info(self._h, ctypes.byref(inf)), "rtproj_get_info")
+        return {f: getattr(inf, f) for f, _ in Info._fields_}
+
+    def timings(self) -> dict:
+        """Per-phase device ms and counts since the last call (needs timing=1)."""
+        import numpy as np
+        ms = np.zeros(len(PHASES))
+        cnt = np.zeros(len(PHASES), dtype=np.int64)
+        _check(load_library().rtproj_get_timings(self._h, ms.ctypes.data_as(_P), cnt.ctypes.data_as(_P)),
+               "rtproj_get_timings")
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(PHASES)}
+
+    def clear_status(self):
+        _check(load_library().rtproj_clear_status(self._h), "rtproj_clear_status")
+
+    # -- apply -----------------------------------------------------------------------
+    def _rhs(self, B: torch.Tensor) -> torch.Tensor:
+        if not (B.is_cuda and B.dtype == torch.float64 and B.stride(-1) == 1):
+            raise TypeError("B must be a CUDA float64 tensor with unit last stride")
+        return B if B.dim() == 2 else B.reshape(1, -1)
+
+    def project(self, B: torch.Tensor, null: bool = True, row: bool = False, lstsq: bool = False,
+                out_null: torch.Tensor | None = None):
+        B = self._rhs(B)
+        k = B.shape[0]
+        Z = (out_null if out_null is not None else torch.empty((k, self.n), dtype=torch.float64, device=self.device)) if null else None
+        ROW = torch.empty((k, self.n), dtype=torch.float64, device=self.device) if row else None
+        X = torch.empty((k, self.m), dtype=torch.float64, device=self.device) if lstsq else None
+        ptr = lambda t: _dev_ptr(t) if t is not None else None
+        ld = lambda t: t.stride(0) if t is not None else 0
+        with torch.cuda.device(self.device):
+            code = load_library().rtproj_project(self._h, _dev_ptr(B), B.stride(0), k, ptr(Z), ld(Z), ptr(ROW), ld(ROW),
+                                                 ptr(X), ld(X))
+        _check(code, "rtproj_project")
+        return Z, ROW, X
+
+    def null_project(self, B, out=None):
+        return self.project(B, null=True, out_null=out)[0]
+
+    def row_project(self, B):
+        return self.project(B, null=False, row=True)[1]
+
+    def lstsq(self, B):
+        return self.project(B, null=False, lstsq=True)[2]
+
+
+def launch_count() -> int:
+    """Kernels enqueued by librtproj since it was loaded."""
+    return int(load_library().rtproj_launch_count())
+
+
+def project_from_host(A_host: torch.Tensor, B_host: torch.Tensor, seed: int, l: int, device="cuda", **kw):
+    """End-to-end call from host buffers: copies A and B to the device, preconditions,
+    projects, and copies Z back (into pinned host memory)."""
+    A = A_host.to(device, non_blocking=True)
+    B = B_host.to(device, non_blocking=True)
+    with Projector(A, l_max=l, k_max=B.shape[0], **kw) as P:
+        P.precondition(seed, l)
+        Z = P.null_project(B)
+        out = torch.empty(Z.shape, dtype=Z.dtype, pin_memory=True)
+        out.copy_(Z, non_blocking=True)
+        torch.cuda.current_stream(A.device).synchronize()
+    return out

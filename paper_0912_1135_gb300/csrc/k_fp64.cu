@@ -1,0 +1,252 @@
+// float64 GEMM on the FP64 pipe (the plain float64 form) and small helpers.
+//
+// The plain form runs every product of the method -- the sketch S = A G (Eq. 12),
+// the Gram matrix X = P^{-1} A A^* P^{-*} (Section 4, steps a-e, done as two GEMMs),
+// and the apply c = A b, the m x m stage, b - A^* h (the seven steps) -- through this
+// kernel. GB300's FP64 pipe is ~1.2 TFLOP/s, so a 64x64 tile with a 4x4 register
+// block per thread already saturates it; no tensor cores are involved here.
+#include "rtproj_internal.cuh"
+
+#include <algorithm>
+
+namespace rtp {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+struct Gemm64Dev {
+    int M, N, K, k_per_split;
+    const double* A; int64_t a_rs, a_cs; const int32_t* arow;
+    const double* B; int64_t b_rs, b_cs; const int32_t* bk;
+    int omega_dist; uint32_t key0, key1;
+    double* P;                     // partial slabs (split > 1)
+    int lower_only;
+    // direct epilogue (one split)
+    double* C; int64_t c_rs, c_cs; const int32_t* crow;
+    double alpha, beta;
+    const double* Cin; int64_t cin_rs, cin_cs;
+};
+
+__global__ void __launch_bounds__(NT) gemm64_kernel(Gemm64Dev p) {
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN, z = blockIdx.z;
+    const int t = threadIdx.x;
+    const int tx = t & 15, ty = t >> 4;
+    double* out = gridDim.z > 1 ? p.P + (size_t)z * p.M * p.N : nullptr;
+    if (p.lower_only && j0 > i0 + BM - 1) return;   // tile strictly above the diagonal
+    const int kbeg = z * p.k_per_split;
+    const int kend = min(p.K, kbeg + p.k_per_split);
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const int e = t + NT * r;
+            int ii, kk;
+            if (p.a_cs == 1) { ii = e / BK; kk = e % BK; } else { kk = e / BM; ii = e % BM; }
+            const int gi = i0 + ii, gk = k0 + kk;
+            double v = 0.0;
+            if (gi < p.M && gk < kend) {
+                const int64_t row = p.arow ? (int64_t)p.arow[gi] : (int64_t)gi;
+                v = p.A[row * p.a_rs + (int64_t)gk * p.a_cs];
+            }
+            As[kk][ii] = v;
+        }
+        if (p.omega_dist >= 0) {
+            // k0 is a multiple of 16: one Philox block covers the 16 rows of column j.
+            if (t < BN) {
+                const int gj = j0 + t;
+                uint4 w = make_uint4(0, 0, 0, 0);
+                if (gj < p.N) w = philox4x32_10(make_uint4((uint32_t)(k0 >> 4), (uint32_t)gj, 0u, 0u), p.key0, p.key1);
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    const int gk = k0 + kk;
+                    Bs[kk][t] = (gj < p.N && gk < kend) ? (double)omega_from_byte(block_byte(w, kk), p.omega_dist) : 0.0;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int e = t + NT * r;
+                int jj, kk;
+                if (p.b_cs == 1) { kk = e / BN; jj = e % BN; } else { jj = e / BK; kk = e % BK; }
+                const int gj = j0 + jj, gk = k0 + kk;
+                double v = 0.0;
+                if (gj < p.N && gk < kend) {
+                    const int64_t row = p.bk ? (int64_t)p.bk[gk] : (int64_t)gk;
+                    v = p.B[row * p.b_rs + (int64_t)gj * p.b_cs];
+                }
+                Bs[kk][jj] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { a[q] = As[kk][ty * 4 + q]; b[q] = Bs[kk][tx * 4 + q]; }
+#pragma unroll
+            for (int x = 0; x < 4; ++x)
+#pragma unroll
+                for (int y = 0; y < 4; ++y) acc[x][y] = fma(a[x], b[y], acc[x][y]);
+        }
+        __syncthreads();
+    }
+    const bool direct = gridDim.z == 1;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        const int gi = i0 + ty * 4 + x;
+        if (gi >= p.M) continue;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+            const int gj = j0 + tx * 4 + y;
+            if (gj >= p.N) continue;
+            if (!direct) {
+                out[(size_t)gi * p.N + gj] = acc[x][y];
+            } else if (!(p.lower_only && gj > gi)) {
+                double v = p.alpha * acc[x][y];
+                if (p.beta != 0.0) v += p.beta * p.Cin[(int64_t)gi * p.cin_rs + (int64_t)gj * p.cin_cs];
+                const int64_t row = p.crow ? (int64_t)p.crow[gi] : (int64_t)gi;
+                p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = v;
+            }
+        }
+    }
+}
+
+struct ReduceDev {
+    int M, N, splits;
+    const double* P;
+    double* C; int64_t c_rs, c_cs; const int32_t* crow;
+    double alpha, beta;
+    const double* Cin; int64_t cin_rs, cin_cs;
+    int lower_only;
+};
+
+__global__ void reduce_kernel(ReduceDev r) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)r.M * r.N;
+    if (idx >= total) return;
+    const int i = (int)(idx / r.N), j = (int)(idx % r.N);
+    if (r.lower_only && j > i) return;
+    double s = 0.0;
+    for (int z = 0; z < r.splits; ++z) s += r.P[(size_t)z * total + idx];
+    double v = r.alpha * s;
+    if (r.beta != 0.0) v += r.beta * r.Cin[(int64_t)i * r.cin_rs + (int64_t)j * r.cin_cs];
+    const int64_t row = r.crow ? (int64_t)r.crow[i] : (int64_t)i;
+    r.C[row * r.c_rs + (int64_t)j * r.c_cs] = v;
+}
+
+__global__ void set_identity_kernel(double* X, int m) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    X[idx] = (idx / m == idx % m) ? 1.0 : 0.0;
+}
+
+__global__ void zero_upper_kernel(double* X, int m) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    if (idx % m > idx / m) X[idx] = 0.0;
+}
+
+__global__ void transpose_kernel(const double* src, int64_t s_rs, double* dst, int64_t d_rs, int rows, int cols) {
+    __shared__ double tile[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) tile[y][threadIdx.x] = src[(int64_t)r * s_rs + c];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[(int64_t)c * d_rs + r] = tile[threadIdx.x][y];
+    }
+}
+
+__global__ void check_finite_kernel(const double* X, int64_t rs, int rows, int cols, int* status) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    const double v = X[(idx / cols) * rs + idx % cols];
+    if (!isfinite(v)) set_status(status, RTPROJ_ENONFINITE);
+}
+
+}  // namespace
+
+cudaError_t gemm64(const Gemm64& g, double* part, size_t part_elems, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    const int tiles_m = (g.M + BM - 1) / BM, tiles_n = (g.N + BN - 1) / BN;
+    const size_t slab = (size_t)g.M * g.N;
+    int splits = 1;
+    if (g.K > 0) {
+        const int tiles = tiles_m * tiles_n;
+        const int want = std::max(1, (4 * 152 + tiles - 1) / tiles);
+        const int maxk = std::max(1, (g.K + 255) / 256);
+        splits = std::min(want, maxk);
+        splits = (int)std::min<size_t>((size_t)splits, std::max<size_t>(1, part_elems / slab));
+    }
+    if (slab > part_elems) splits = 1;
+    int kps = (g.K + splits - 1) / splits;
+    kps = ((kps + BK - 1) / BK) * BK;
+    splits = g.K > 0 ? (g.K + kps - 1) / kps : 1;
+    Gemm64Dev p;
+    p.M = g.M; p.N = g.N; p.K = g.K; p.k_per_split = std::max(kps, BK);
+    p.A = g.A; p.a_rs = g.a_rs; p.a_cs = g.a_cs; p.arow = g.arow;
+    p.B = g.B; p.b_rs = g.b_rs; p.b_cs = g.b_cs; p.bk = g.bk;
+    p.omega_dist = g.omega_dist;
+    p.key0 = (uint32_t)(g.seed & 0xFFFFFFFFull); p.key1 = (uint32_t)(g.seed >> 32);
+    p.P = part;
+    p.lower_only = g.lower_only ? 1 : 0;
+    p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
+    p.alpha = g.alpha; p.beta = g.beta; p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
+    if (g.K <= 0) return cudaErrorInvalidValue;
+    {
+        dim3 grid(tiles_n, tiles_m, splits);
+        gemm64_kernel<<<grid, NT, 0, s>>>(p);
+        note_launch();
+    }
+    if (splits == 1) return cudaGetLastError();
+    ReduceDev r;
+    r.M = g.M; r.N = g.N; r.splits = splits; r.P = part;
+    r.C = g.C; r.c_rs = g.c_rs; r.c_cs = g.c_cs; r.crow = g.crow;
+    r.alpha = g.alpha; r.beta = g.beta; r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
+    r.lower_only = g.lower_only ? 1 : 0;
+    const int64_t total = (int64_t)slab;
+    reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t set_identity(double* X, int m, cudaStream_t s) {
+    const int64_t total = (int64_t)m * m;
+    set_identity_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, m);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t zero_upper(double* X, int m, cudaStream_t s) {
+    const int64_t total = (int64_t)m * m;
+    zero_upper_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, m);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_copy(const double* src, int64_t s_rs, double* dst, int64_t d_rs, int rows, int cols, cudaStream_t s) {
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+    transpose_kernel<<<grid, dim3(32, 8), 0, s>>>(src, s_rs, dst, d_rs, rows, cols);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t check_finite(const double* X, int64_t rs, int rows, int cols, int* status, cudaStream_t s) {
+    const int64_t total = (int64_t)rows * cols;
+    if (total == 0) return cudaSuccess;
+    check_finite_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, rs, rows, cols, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace rtp

@@ -1,0 +1,166 @@
+// Triangular solves and the Cholesky factorization of X (float64, FP64 pipe).
+//
+// Section 4 forms Y = X^{-1} explicitly (Eq. 16). This library factors X = L L^*
+// instead (X is symmetric positive definite with kappa(X) = kappa(P^{-1}A)^2, small)
+// and folds R and L into T1 = L^{-1} R^{-*}, so that steps 3-5 of the apply become
+// two dense triangular products: P^{-*} Y P^{-1} c = Pi^* T1^* T1 Pi c.
+#include "rtproj_internal.cuh"
+
+#include <algorithm>
+
+namespace rtp {
+namespace {
+
+constexpr int TRSM_NB = 4;
+constexpr int TRSM_THREADS = 256;
+
+// Solves op(T) X = B for TRSM_NB columns of B per CTA, B held in shared memory.
+__global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int64_t t_rs, int64_t t_cs, int lower,
+                                                            int m, double* B, int64_t b_rs, int ncols, int* status) {
+    extern __shared__ double x[];   // m * TRSM_NB
+    const int j0 = blockIdx.x * TRSM_NB;
+    const int nc = min(TRSM_NB, ncols - j0);
+    const int t = threadIdx.x;
+    for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
+        const int i = e / TRSM_NB, jj = e % TRSM_NB;
+        x[e] = jj < nc ? B[(int64_t)i * b_rs + j0 + jj] : 0.0;
+    }
+    __syncthreads();
+    for (int step = 0; step < m; ++step) {
+        const int i = lower ? step : m - 1 - step;
+        if (t < TRSM_NB) {
+            double d = T[(int64_t)i * t_rs + (int64_t)i * t_cs];
+            if (!(d != 0.0) || !isfinite(d)) {
+                set_status(status, RTPROJ_ENONFINITE);
+                d = 1.0;
+            }
+            x[i * TRSM_NB + t] /= d;
+        }
+        __syncthreads();
+        double xi[TRSM_NB];
+#pragma unroll
+        for (int jj = 0; jj < TRSM_NB; ++jj) xi[jj] = x[i * TRSM_NB + jj];
+        if (lower) {
+            for (int r = i + 1 + t; r < m; r += TRSM_THREADS) {
+                const double tv = T[(int64_t)r * t_rs + (int64_t)i * t_cs];
+#pragma unroll
+                for (int jj = 0; jj < TRSM_NB; ++jj) x[r * TRSM_NB + jj] = fma(-tv, xi[jj], x[r * TRSM_NB + jj]);
+            }
+        } else {
+            for (int r = t; r < i; r += TRSM_THREADS) {
+                const double tv = T[(int64_t)r * t_rs + (int64_t)i * t_cs];
+#pragma unroll
+                for (int jj = 0; jj < TRSM_NB; ++jj) x[r * TRSM_NB + jj] = fma(-tv, xi[jj], x[r * TRSM_NB + jj]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
+        const int i = e / TRSM_NB, jj = e % TRSM_NB;
+        if (jj < nc) B[(int64_t)i * b_rs + j0 + jj] = x[e];
+    }
+}
+
+constexpr int CH_NB = 32;
+
+// Unblocked Cholesky of the nb x nb diagonal block at (p0, p0), in shared memory.
+__global__ void chol_diag_kernel(double* X, int m, int p0, int nb, int* status) {
+    __shared__ double a[CH_NB][CH_NB + 1];
+    const int t = threadIdx.x;
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        a[i][j] = X[(int64_t)(p0 + i) * m + p0 + j];
+    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
+        if (t == 0) {
+            double d = a[c][c];
+            if (!(d > 0.0) || !isfinite(d)) {
+                set_status(status, RTPROJ_ENOTSPD);
+                d = 1.0;
+            }
+            a[c][c] = sqrt(d);
+        }
+        __syncthreads();
+        for (int r = c + 1 + t; r < nb; r += blockDim.x) a[r][c] /= a[c][c];
+        __syncthreads();
+        for (int e = t; e < nb * nb; e += blockDim.x) {
+            const int r = e / nb, q = e % nb;
+            if (q > c && r >= q) a[r][q] = fma(-a[r][c], a[q][c], a[r][q]);
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        X[(int64_t)(p0 + i) * m + p0 + j] = (j <= i) ? a[i][j] : 0.0;
+    }
+}
+
+// Rows below the diagonal block: x L_pp^* = X[r][p0..p0+nb), one thread per row.
+__global__ void chol_panel_kernel(double* X, int m, int p0, int nb) {
+    __shared__ double L[CH_NB][CH_NB + 1];
+    const int t = threadIdx.x;
+    for (int e = t; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, j = e % nb;
+        L[i][j] = X[(int64_t)(p0 + i) * m + p0 + j];
+    }
+    __syncthreads();
+    const int r = p0 + nb + blockIdx.x * blockDim.x + t;
+    if (r >= m) return;
+    double x[CH_NB];
+    double* row = X + (int64_t)r * m + p0;
+#pragma unroll
+    for (int c = 0; c < CH_NB; ++c) x[c] = c < nb ? row[c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < CH_NB; ++c) {
+        if (c < nb) {
+            double s = x[c];
+#pragma unroll
+            for (int q = 0; q < CH_NB; ++q)
+                if (q < c) s = fma(-x[q], L[c][q], s);
+            x[c] = s / L[c][c];
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CH_NB; ++c)
+        if (c < nb) row[c] = x[c];
+}
+
+}  // namespace
+
+cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
+                 double* Bm, int64_t b_rs, int ncols, int* status, cudaStream_t s) {
+    if (m <= 0 || ncols <= 0) return cudaSuccess;
+    const size_t smem = (size_t)m * TRSM_NB * sizeof(double);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    trsm_kernel<<<(ncols + TRSM_NB - 1) / TRSM_NB, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, lower ? 1 : 0, m, Bm, b_rs,
+                                                                               ncols, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s) {
+    for (int p0 = 0; p0 < m; p0 += CH_NB) {
+        const int nb = std::min(CH_NB, m - p0);
+        chol_diag_kernel<<<1, 256, 0, s>>>(X, m, p0, nb, status);
+        note_launch();
+        const int rest = m - p0 - nb;
+        if (rest <= 0) break;
+        chol_panel_kernel<<<(rest + 127) / 128, 128, 0, s>>>(X, m, p0, nb);
+        note_launch();
+        Gemm64 g;
+        g.M = rest; g.N = rest; g.K = nb;
+        g.A = X + (int64_t)(p0 + nb) * m + p0; g.a_rs = m; g.a_cs = 1;
+        g.B = X + (int64_t)(p0 + nb) * m + p0; g.b_rs = 1; g.b_cs = m;
+        g.C = X + (int64_t)(p0 + nb) * m + (p0 + nb); g.c_rs = m; g.c_cs = 1;
+        g.alpha = -1.0; g.beta = 1.0;
+        g.Cin = g.C; g.cin_rs = m; g.cin_cs = 1;
+        g.lower_only = true;
+        cudaError_t e = gemm64(g, part, part_elems, s);
+        if (e != cudaSuccess) return e;
+    }
+    return zero_upper(X, m, s);
+}
+
+}  // namespace rtp

@@ -1,0 +1,188 @@
+// Internal declarations shared by the CUDA translation units of librtproj.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "rtproj.h"
+
+namespace rtp {
+
+// Counts kernels enqueued by this library (reported by rtproj_launch_count).
+void note_launch(int n = 1);
+
+// Per-phase CUDA-event timing (opts.timing).
+struct PhaseTimer {
+    static constexpr int kMax = 64;
+    cudaEvent_t b[kMax] = {};
+    cudaEvent_t e[kMax] = {};
+    int phase[kMax] = {};
+    int n = 0;
+    int open = -1;
+    double ms[RTPROJ_NUM_PHASES] = {};
+    int64_t cnt[RTPROJ_NUM_PHASES] = {};
+    bool enabled = false;
+};
+
+// ---------------------------------------------------------------------------
+// Device status word: the first error code written wins (never trap/assert).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void set_status(int* st, int code) {
+    if (st) atomicCAS(st, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) and the entries of G.
+// Entry (i, j) of the n x l test matrix uses byte (i & 3) of word ((i & 15) >> 2)
+// of the block at counter (i >> 4, j, 0, 0), key (seed lo, seed hi).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Byte b (0..15) of a Philox block -> entry of G.
+__device__ __forceinline__ float omega_from_byte(uint32_t u, int dist) {
+    return dist == RTPROJ_OMEGA_RADEMACHER ? (u >= 128u ? 1.0f : -1.0f)
+                                           : (float)(2 * (int)u - 255) * (1.0f / 256.0f);
+}
+
+__device__ __forceinline__ uint32_t block_byte(const uint4& w, int b) {
+    const uint32_t word = (b >> 2) == 0 ? w.x : (b >> 2) == 1 ? w.y : (b >> 2) == 2 ? w.z : w.w;
+    return (word >> (8 * (b & 3))) & 0xFFu;
+}
+
+// ---------------------------------------------------------------------------
+// float64 tiled GEMM on the FP64 pipe, split over K into partial slabs.
+//   P[z][i][j] = sum_{k in split z} A(i,k) * B(k,j)
+//   A(i,k) = A[(arow ? arow[i] : i) * a_rs + k * a_cs]
+//   B(k,j) = B[(bk ? bk[k] : k) * b_rs + j * b_cs], or G(k, j) when omega_dist >= 0
+// then a reduce kernel writes C[(crow ? crow[i] : i) * c_rs + j * c_cs]
+//   = alpha * sum_z P[z][i][j] + beta * Cin[i * cin_rs + j * cin_cs].
+// ---------------------------------------------------------------------------
+struct Gemm64 {
+    int M = 0, N = 0, K = 0;
+    const double* A = nullptr; int64_t a_rs = 0, a_cs = 0; const int32_t* arow = nullptr;
+    const double* B = nullptr; int64_t b_rs = 0, b_cs = 0; const int32_t* bk = nullptr;
+    int omega_dist = -1; uint64_t seed = 0;
+    double* C = nullptr; int64_t c_rs = 0, c_cs = 0; const int32_t* crow = nullptr;
+    double alpha = 1.0, beta = 0.0;
+    const double* Cin = nullptr; int64_t cin_rs = 0, cin_cs = 0;
+    bool lower_only = false;   // compute/write only entries with i >= j (tiles above skipped)
+};
+
+// Enqueues the GEMM + reduce. part/part_elems: scratch for the partial slabs.
+cudaError_t gemm64(const Gemm64& g, double* part, size_t part_elems, cudaStream_t s);
+
+// Small helpers (k_fp64.cu)
+cudaError_t set_identity(double* X, int m, cudaStream_t s);
+cudaError_t transpose_copy(const double* src, int64_t s_rs, double* dst, int64_t d_rs, int rows, int cols, cudaStream_t s);
+cudaError_t check_finite(const double* X, int64_t rs, int rows, int cols, int* status, cudaStream_t s);
+cudaError_t zero_upper(double* X, int m, cudaStream_t s);
+
+// Pivoted QR of S^* (k_qr.cu). S is m x l row-major (row i of S = column i of S^*),
+// overwritten. On exit R (m x m, upper) and perm (m) hold the factorization
+// S^*[:, perm] = Q R. work: 3*m + l doubles.
+cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
+                       double* work, int* status, cudaStream_t s);
+
+// Triangular solves and Cholesky (k_tri.cu).
+// Solves op(T) X = Bm in place; T (m x m) element (i,j) at T[i*t_rs + j*t_cs];
+// lower selects forward substitution. Bm element (i, j) at Bm[i*b_rs + j], j < ncols.
+cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
+                 double* Bm, int64_t b_rs, int ncols, int* status, cudaStream_t s);
+// In-place lower Cholesky of the m x m row-major X (strict upper part zeroed).
+cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Mixed mode: fixed-point bfloat16 slicing and the sliced tensor-core GEMM.
+// ---------------------------------------------------------------------------
+// A "slice stack" of a rows x cols matrix X (reduction over cols): for each row r an
+// exponent e_r with |X[r][c]| < 2^{e_r}, and s planes D_p (p = 0..s-1) of bfloat16
+// integers in [-128, 128] such that
+//     X[r][c] ~= 2^{e_r} * sum_p D_p[r][c] * 2^{-7-8p}
+// with truncation error below 2^{e_r - 8s}. Plane p is stored row-major with leading
+// dimension ld (a multiple of 8 elements), plane stride plane_stride elements.
+struct SliceStack {
+    __nv_bfloat16* d = nullptr;
+    int32_t* e = nullptr;
+    int rows = 0, cols = 0, s = 0;
+    int64_t ld = 0;
+    int64_t plane_stride = 0;
+};
+
+// Slices X (element (r, c) at X[r*x_rs + c*x_cs]) into the stack; optional row gather.
+cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx,
+                       const SliceStack& st, int* status, cudaStream_t s);
+// Writes G^T (l x n, K-major over n) as one bfloat16 plane with exponent 0 (exact).
+cudaError_t omega_plane(uint64_t seed, int dist, int n, int l, const SliceStack& st, cudaStream_t s);
+
+// C[(crow?crow[i]:i)*c_rs + j*c_cs] = alpha * (A_stack x B_stack^T)[i][j] + beta * Cin[...]
+// where the product keeps slice pairs p + q <= max(sa, sb) - 1 (0-based) -- the
+// Ozaki-scheme truncation -- and is exact up to that truncation.
+struct SlicedGemm {
+    SliceStack a, b;     // a: M x K, b: N x K (both reduce over K)
+    int terms = 0;       // keep pairs with p + q < terms (terms <= sa + sb - 1)
+    double* C = nullptr; int64_t c_rs = 0, c_cs = 0; const int32_t* crow = nullptr;
+    double alpha = 1.0, beta = 0.0;
+    const double* Cin = nullptr; int64_t cin_rs = 0, cin_cs = 0;
+    bool lower_only = false;
+};
+size_t sliced_gemm_scratch_bytes(int M, int N, int K);
+cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s);
+
+}  // namespace rtp
+
+// ---------------------------------------------------------------------------
+// Host-side handle.
+// ---------------------------------------------------------------------------
+struct rtproj_ctx {
+    int64_t m = 0, n = 0, lda = 0, l_max = 0, k_max = 0;
+    const double* A = nullptr;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t stream = nullptr;
+    rtproj_opts opts{};
+
+    int* status = nullptr;       // device status word
+    double* S = nullptr;         // m x l_max sketch, destroyed by the QR
+    double* qr_work = nullptr;   // 3m + l_max
+    int32_t* perm = nullptr;     // m
+    double* R = nullptr;         // m x m
+    double* RinvT = nullptr;     // m x m, R^{-*}
+    double* Lc = nullptr;        // m x m, chol(X)
+    double* T1 = nullptr;        // m x m, Lc^{-1} R^{-*}
+    double* W = nullptr;         // m x n, P^{-1} A (float64 mode)
+    double* part = nullptr;      // split-K partial slabs
+    size_t part_elems = 0;
+    double* cbuf = nullptr;      // m x k_max
+    double* ebuf = nullptr;      // m x k_max
+    double* hbuf = nullptr;      // m x k_max  (h, row-major m x k)
+    double* dhbuf = nullptr;     // m x k_max
+    double* sbuf = nullptr;      // k_max x n  (refinement residual)
+    // mixed mode
+    rtp::SliceStack As;          // A: m x n, s planes
+    rtp::SliceStack Ats;         // A^*: n x m, s planes (row exponents folded, see api)
+    rtp::SliceStack Gs;          // G^*: l x n, one plane
+    rtp::SliceStack tmpA, tmpB;  // scratch stacks for the m x m / m x k operands
+    rtp::SliceStack Wsl;         // W slices (m x n)
+    rtp::SliceStack Bsl;         // right-hand-side slices (k x n)
+    rtp::SliceStack Ssl;         // refinement residual slices (k x n)
+    void* sg_scratch = nullptr;
+    size_t sg_scratch_bytes = 0;
+    double* Wd = nullptr;        // m x n float64 W in mixed mode (shares W)
+
+    rtp::PhaseTimer timer;
+    int64_t l = 0;
+    int preconditioned = 0;
+    float ms_pre = 0.f;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
