@@ -80,11 +80,11 @@ typedef enum {
 typedef struct {
     int mode;            /* rtproj_mode (default RTPROJ_MIXED_REFINED)                    */
     int omega;           /* rtproj_omega (default RTPROJ_OMEGA_UNIFORM)                   */
-    int sketch_slices;   /* mixed: slices of A in S = A G            (default 4, 1..8)   */
-    int gram_slices;     /* mixed: slices in W = P^{-1} A            (default 7, 1..8)   */
-    int gram2_slices;    /* mixed: slices in X = W W^*               (default 3, 1..8)   */
-    int apply_slices;    /* mixed: slices in c = A b and A^* dh      (default 7, 1..8)   */
-    int resid_slices;    /* mixed: slices in the refinement residual (default 8, 1..8)   */
+    int sketch_slices;   /* mixed: slices of A in S = A G            (default 5, 1..10)  */
+    int gram_slices;     /* mixed: slices in W = P^{-1} A            (default 7, 1..10)  */
+    int gram2_slices;    /* mixed: slices in X = W W^*               (default 3, 1..10)  */
+    int apply_slices;    /* mixed: slices in c = A b and A^* dh      (default 7, 1..10)  */
+    int resid_slices;    /* mixed: slices in the refinement residual (default 9, 1..10)  */
     int refine_passes;   /* mixed: refinement passes                 (default 1, 0..4)   */
     int timing;          /* 1: record CUDA events around each phase (rtproj_get_timings)  */
     double rank_tol;     /* ERANK threshold; <= 0 selects 64 * l * 2^-52                  */

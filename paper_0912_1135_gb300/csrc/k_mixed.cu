@@ -1,15 +1,276 @@
-// Mixed mode orchestration (sliced bfloat16 tensor-core products). Placeholder until
-// the sliced GEMM lands: every entry reports RTPROJ_EUNSUPPORTED.
+// Mixed mode: every product with A on the tensor cores through exact digit slicing
+// (k_slice.cu, k_umma.cu), the m x m stage in float64, and refinement (Remark 4.3).
+//
+// Preconditioner (Section 4):
+//   S = A G           sketch_slices digits of A times the one-digit G plane (Eq. 12)
+//   pivoted QR of S^* in float64 (Eq. 13); R^{-*} by a triangular solve
+//   W = R^{-*} Pi A   = M' A^, where A^ is A with row i divided by 2^{e_i} (its slicing
+//                     exponent) and M'[i][k] = R^{-*}[i][t] 2^{e_k} for k = perm[t]:
+//                     gram_slices digits of M' against the transposed digits of A^
+//   X = W W^*         gram2_slices digits of W (Eq. 14 as a Gram product), then Cholesky
+// Apply, for right-hand sides b (rows of B):
+//   c  = A b                       apply_slices digits        (step 1)
+//   h0 = Pi^* T1^* T1 Pi c         float64                     (steps 2-6)
+//   s  = b - A^* h0                resid_slices digits of A^ and of 2^{e} h0
+//   repeat refine_passes times (Remark 4.3):
+//     r  = A s                     resid_slices digits
+//     dh = Pi^* T1^* T1 Pi r       float64
+//     h  = h + dh;  s = s - A^* dh apply_slices digits
+//   Z = s, ROW = b - s, least squares h.
+// Because the digit products and their sums are exact, the residual products s and r
+// are accurate to about 2^{-8 resid_slices} relative to |A||s| -- beyond float64 -- which
+// is what lets refinement reach the exact projection of the stored matrix where every
+// float64 method stops near eps * kappa (Remark 5.1).
 #include "rtproj_internal.cuh"
 
+#include <algorithm>
+
 namespace rtp {
-size_t mixed_bytes(int64_t, int64_t, int64_t, int64_t, const rtproj_opts&) { return 0; }
-rtproj_status mixed_bind(rtproj_ctx*, char*, size_t) { return RTPROJ_EUNSUPPORTED; }
-rtproj_status mixed_prepare_a(rtproj_ctx*) { return RTPROJ_EUNSUPPORTED; }
-rtproj_status mixed_sketch(rtproj_ctx*, uint64_t, int64_t, double*, int64_t) { return RTPROJ_EUNSUPPORTED; }
-rtproj_status mixed_gram(rtproj_ctx*) { return RTPROJ_EUNSUPPORTED; }
-rtproj_status mixed_project(rtproj_ctx*, const double*, int64_t, int, double*, int64_t, double*, int64_t, double*,
-                            int64_t) {
-    return RTPROJ_EUNSUPPORTED;
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kScratch = 48ull << 20;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int64_t pad64(int64_t x) { return (x + 63) / 64 * 64; }
+
+int s_all(const rtproj_opts& o) {
+    return std::max(std::max(o.sketch_slices, o.gram_slices), std::max(o.apply_slices, o.resid_slices));
 }
+
+struct MixedLayout {
+    size_t A, eA, AT, eAT, G, eG, Mp, Ms, eM, W, eW, B, eB, H, eH, S, eS, scratch, total;
+};
+
+MixedLayout mixed_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts& o) {
+    MixedLayout L{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) { const size_t at = off; off = align_up(off + bytes); return at; };
+    const int64_t ldn = pad64(n), ldm = pad64(m);
+    const int sa = s_all(o);
+    L.A = take((size_t)sa * m * ldn * 2);
+    L.eA = take((size_t)m * 4);
+    L.AT = take((size_t)sa * n * ldm * 2);
+    L.eAT = take((size_t)n * 4);
+    L.G = take((size_t)l_max * ldn * 2);
+    L.eG = take((size_t)l_max * 4);
+    L.Mp = take((size_t)m * m * 8);
+    L.Ms = take((size_t)o.gram_slices * m * ldm * 2);
+    L.eM = take((size_t)m * 4);
+    L.W = take((size_t)o.gram2_slices * m * ldn * 2);
+    L.eW = take((size_t)m * 4);
+    L.B = take((size_t)o.apply_slices * k_max * ldn * 2);
+    L.eB = take((size_t)k_max * 4);
+    const int sh = std::max(o.apply_slices, o.resid_slices);
+    L.H = take((size_t)sh * k_max * ldm * 2);
+    L.eH = take((size_t)k_max * 4);
+    L.S = take((size_t)o.resid_slices * k_max * ldn * 2);
+    L.eS = take((size_t)k_max * 4);
+    L.scratch = take(kScratch);
+    L.total = off;
+    return L;
+}
+
+SliceStack stack(char* base, size_t d_off, size_t e_off, int rows, int cols, int s, int64_t ld) {
+    SliceStack st;
+    st.d = (__nv_bfloat16*)(base + d_off);
+    st.e = (int32_t*)(base + e_off);
+    st.rows = rows;
+    st.cols = cols;
+    st.s = s;
+    st.ld = ld;
+    st.plane_stride = (int64_t)rows * ld;
+    return st;
+}
+
+// The first s digit planes of a stack (digits are hierarchical, so this is the s-digit truncation).
+SliceStack first(const SliceStack& st, int s) {
+    SliceStack r = st;
+    r.s = s;
+    return r;
+}
+
+// Same storage, fewer rows in use (plane stride unchanged).
+SliceStack rows_of(const SliceStack& st, int rows, int s) {
+    SliceStack r = st;
+    r.rows = rows;
+    r.s = s;
+    return r;
+}
+
+__global__ void mprime_kernel(const double* RinvT, const int32_t* perm, const int32_t* eA, int m, double* Mp) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    const int i = (int)(idx / m), t = (int)(idx % m);
+    const int k = perm[t];
+    Mp[(int64_t)i * m + k] = ldexp(RinvT[idx], eA[k]);
+}
+
+__global__ void axpy_kernel(double* y, const double* x, int64_t n) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) y[idx] += x[idx];
+}
+
+// OUT[r][c] = X[r][c] (sub = 0) or B[r][c] - X[r][c] (sub = 1), rows x cols.
+__global__ void rows_op_kernel(const double* X, int64_t ldx, const double* B, int64_t ldb, double* OUT, int64_t ldo,
+                               int rows, int cols, int sub) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * cols) return;
+    const int r = (int)(idx / cols), c = (int)(idx % cols);
+    const double x = X[(int64_t)r * ldx + c];
+    OUT[(int64_t)r * ldo + c] = sub ? B[(int64_t)r * ldb + c] - x : x;
+}
+
+#define MX_CHECK(expr)                              \
+    do {                                            \
+        cudaError_t e_ = (expr);                    \
+        if (e_ != cudaSuccess) return RTPROJ_ECUDA; \
+    } while (0)
+
+rtproj_status gemm(rtproj_ctx* h, const SliceStack& a, const SliceStack& b, int terms, double* C, int64_t c_rs,
+                   int64_t c_cs, double alpha = 1.0, double beta = 0.0, const double* Cin = nullptr,
+                   int64_t cin_rs = 0, int64_t cin_cs = 0, bool lower = false) {
+    SlicedGemm g;
+    g.a = a;
+    g.b = b;
+    g.terms = std::min(terms, a.s + b.s - 1);
+    g.C = C; g.c_rs = c_rs; g.c_cs = c_cs;
+    g.alpha = alpha; g.beta = beta; g.Cin = Cin; g.cin_rs = cin_rs; g.cin_cs = cin_cs;
+    g.lower_only = lower;
+    MX_CHECK(sliced_gemm(g, h->sg_scratch, h->sg_scratch_bytes, h->status, h->stream));
+    return RTPROJ_OK;
+}
+
+}  // namespace
+
+size_t mixed_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts& o) {
+    return mixed_layout(m, n, l_max, k_max, o).total;
+}
+
+rtproj_status mixed_bind(rtproj_ctx* h, char* base, size_t bytes) {
+    const rtproj_opts& o = h->opts;
+    const MixedLayout L = mixed_layout(h->m, h->n, h->l_max, h->k_max, o);
+    if (bytes < L.total) return RTPROJ_ENOMEM;
+    const int m = (int)h->m, n = (int)h->n;
+    const int64_t ldn = pad64(n), ldm = pad64(m);
+    const int sa = s_all(o);
+    h->As = stack(base, L.A, L.eA, m, n, sa, ldn);
+    h->Ats = stack(base, L.AT, L.eAT, n, m, sa, ldm);
+    h->Gs = stack(base, L.G, L.eG, (int)h->l_max, n, 1, ldn);
+    h->Mprime = (double*)(base + L.Mp);
+    h->Ms = stack(base, L.Ms, L.eM, m, m, o.gram_slices, ldm);
+    h->Ws = stack(base, L.W, L.eW, m, n, o.gram2_slices, ldn);
+    h->Bs = stack(base, L.B, L.eB, (int)h->k_max, n, o.apply_slices, ldn);
+    h->Hs = stack(base, L.H, L.eH, (int)h->k_max, m, std::max(o.apply_slices, o.resid_slices), ldm);
+    h->Ss = stack(base, L.S, L.eS, (int)h->k_max, n, o.resid_slices, ldn);
+    h->sg_scratch = base + L.scratch;
+    h->sg_scratch_bytes = kScratch;
+    return RTPROJ_OK;
+}
+
+rtproj_status mixed_prepare_a(rtproj_ctx* h) {
+    phase_begin(h, RTPROJ_PHASE_SLICE);
+    MX_CHECK(slice_rows(h->A, h->lda, 1, nullptr, nullptr, h->As, h->status, h->stream));
+    MX_CHECK(transpose_planes(h->As, h->Ats, h->stream));
+    MX_CHECK(fill_int(h->Ats.e, (int)h->n, 0, h->stream));
+    phase_end(h, RTPROJ_PHASE_SLICE);
+    return RTPROJ_OK;
+}
+
+rtproj_status mixed_sketch(rtproj_ctx* h, uint64_t seed, int64_t l, double* S, int64_t lds) {
+    SliceStack G = rows_of(h->Gs, (int)l, 1);
+    MX_CHECK(omega_plane(seed, h->opts.omega, (int)h->n, (int)l, G, h->stream));
+    return gemm(h, first(h->As, h->opts.sketch_slices), G, h->opts.sketch_slices, S, lds, 1);
+}
+
+rtproj_status mixed_gram(rtproj_ctx* h) {
+    const int m = (int)h->m, n = (int)h->n;
+    const int64_t total = (int64_t)m * m;
+    mprime_kernel<<<(unsigned)((total + 255) / 256), 256, 0, h->stream>>>(h->RinvT, h->perm, h->As.e, m, h->Mprime);
+    note_launch();
+    MX_CHECK(cudaGetLastError());
+    MX_CHECK(slice_rows(h->Mprime, m, 1, nullptr, nullptr, h->Ms, h->status, h->stream));
+    rtproj_status st = gemm(h, h->Ms, first(h->Ats, h->opts.gram_slices), h->opts.gram_slices, h->W, n, 1);
+    if (st != RTPROJ_OK) return st;
+    MX_CHECK(slice_rows(h->W, n, 1, nullptr, nullptr, h->Ws, h->status, h->stream));
+    return gemm(h, h->Ws, h->Ws, h->opts.gram2_slices, h->Lc, m, 1, 1.0, 0.0, nullptr, 0, 0, true);
+}
+
+rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, double* Z, int64_t ldz, double* ROW,
+                            int64_t ldr, double* X, int64_t ldx) {
+    const rtproj_opts& o = h->opts;
+    const int m = (int)h->m, n = (int)h->n;
+    cudaStream_t s = h->stream;
+    rtproj_status st;
+    // c = A b
+    phase_begin(h, RTPROJ_PHASE_SLICE);
+    const SliceStack Bk = rows_of(h->Bs, k, o.apply_slices);
+    MX_CHECK(slice_rows(B, ldb, 1, nullptr, nullptr, Bk, h->status, s));
+    phase_end(h, RTPROJ_PHASE_SLICE);
+    phase_begin(h, RTPROJ_PHASE_APPLY_A);
+    st = gemm(h, first(h->As, o.apply_slices), Bk, o.apply_slices, h->cbuf, k, 1);
+    if (st != RTPROJ_OK) return st;
+    phase_end(h, RTPROJ_PHASE_APPLY_A);
+    // h0 = Pi^* T1^* T1 Pi c
+    phase_begin(h, RTPROJ_PHASE_APPLY_M);
+    st = middle_fp64(h, h->cbuf, h->hbuf, k);
+    if (st != RTPROJ_OK) return st;
+    phase_end(h, RTPROJ_PHASE_APPLY_M);
+    // s = b - A^* h0
+    phase_begin(h, RTPROJ_PHASE_SLICE);
+    const SliceStack Hr = rows_of(h->Hs, k, o.resid_slices);
+    MX_CHECK(slice_rows(h->hbuf, 1, k, nullptr, h->As.e, Hr, h->status, s));
+    phase_end(h, RTPROJ_PHASE_SLICE);
+    phase_begin(h, RTPROJ_PHASE_APPLY_AT);
+    st = gemm(h, first(h->Ats, o.resid_slices), Hr, o.resid_slices, h->sbuf, 1, n, -1.0, 1.0, B, 1, ldb);
+    if (st != RTPROJ_OK) return st;
+    phase_end(h, RTPROJ_PHASE_APPLY_AT);
+    const bool direct_z = Z && !ROW;
+    for (int pass = 0; pass < o.refine_passes; ++pass) {
+        const bool last = pass + 1 == o.refine_passes;
+        // r = A s
+        phase_begin(h, RTPROJ_PHASE_SLICE);
+        const SliceStack Sk = rows_of(h->Ss, k, o.resid_slices);
+        MX_CHECK(slice_rows(h->sbuf, n, 1, nullptr, nullptr, Sk, h->status, s));
+        phase_end(h, RTPROJ_PHASE_SLICE);
+        phase_begin(h, RTPROJ_PHASE_APPLY_A);
+        st = gemm(h, first(h->As, o.resid_slices), Sk, o.resid_slices, h->cbuf, k, 1);
+        if (st != RTPROJ_OK) return st;
+        phase_end(h, RTPROJ_PHASE_APPLY_A);
+        // dh, h += dh
+        phase_begin(h, RTPROJ_PHASE_APPLY_M);
+        st = middle_fp64(h, h->cbuf, h->dhbuf, k);
+        if (st != RTPROJ_OK) return st;
+        const int64_t mk = (int64_t)m * k;
+        axpy_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(h->hbuf, h->dhbuf, mk);
+        note_launch();
+        phase_end(h, RTPROJ_PHASE_APPLY_M);
+        // s = s - A^* dh
+        phase_begin(h, RTPROJ_PHASE_SLICE);
+        const SliceStack Hd = rows_of(h->Hs, k, o.apply_slices);
+        MX_CHECK(slice_rows(h->dhbuf, 1, k, nullptr, h->As.e, Hd, h->status, s));
+        phase_end(h, RTPROJ_PHASE_SLICE);
+        phase_begin(h, RTPROJ_PHASE_APPLY_AT);
+        if (last && direct_z)
+            st = gemm(h, first(h->Ats, o.apply_slices), Hd, o.apply_slices, Z, 1, ldz, -1.0, 1.0, h->sbuf, 1, n);
+        else
+            st = gemm(h, first(h->Ats, o.apply_slices), Hd, o.apply_slices, h->sbuf, 1, n, -1.0, 1.0, h->sbuf, 1, n);
+        if (st != RTPROJ_OK) return st;
+        phase_end(h, RTPROJ_PHASE_APPLY_AT);
+    }
+    const int64_t kn = (int64_t)k * n;
+    const bool z_in_sbuf = !(direct_z && o.refine_passes > 0);
+    if (ROW) {
+        rows_op_kernel<<<(unsigned)((kn + 255) / 256), 256, 0, s>>>(h->sbuf, n, B, ldb, ROW, ldr, k, n, 1);
+        note_launch();
+    }
+    if (Z && z_in_sbuf) {
+        rows_op_kernel<<<(unsigned)((kn + 255) / 256), 256, 0, s>>>(h->sbuf, n, nullptr, 0, Z, ldz, k, n, 0);
+        note_launch();
+    }
+    if (X) MX_CHECK(transpose_copy(h->hbuf, k, X, ldx, m, k, s));
+    MX_CHECK(cudaGetLastError());
+    return RTPROJ_OK;
+}
+
 }  // namespace rtp

@@ -1,0 +1,202 @@
+// Exact fixed-point slicing of float64 operands into bfloat16 digit planes (mixed mode).
+//
+// For a row x of an operand (the products reduce along the row), with e the smallest
+// integer such that max |x_c| < 2^e, every entry is written as
+//     x_c ~= 2^e * sum_{p < s} d_p * 2^{-7-8p},     d_p integers in [-128, 128] (s <= 10),
+// the balanced base-256 digits of F = round(|x_c| 2^{7+8(s-1)-e}), signed like x_c.
+// Each d_p is exact in bfloat16, so the tensor cores multiply digits exactly and the
+// float32 accumulator sums them exactly as long as a partial sum stays below 2^24.
+// Truncation error per entry: at most 2^{e-8s} (half a unit of the last digit).
+// The digits come from integer operations on the float64 bit pattern (no FP64 pipe).
+#include "rtproj_internal.cuh"
+
+namespace rtp {
+namespace {
+
+constexpr int SL_THREADS = 256;
+
+__device__ __forceinline__ void fixed_digits(double v, int shift_base, int s, int* dig) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+    const bool neg = (bits >> 63) != 0;
+    int E = (int)((bits >> 52) & 0x7FFull);
+    unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+    if (E == 0) {
+        if (M == 0) {
+            for (int p = 0; p < s; ++p) dig[p] = 0;
+            return;
+        }
+        E = 1;
+    } else {
+        M |= 1ull << 52;
+    }
+    // F = round(M * 2^sh) < 2^(7+8(s-1)) <= 2^79 by the choice of e: 128-bit integer.
+    const int sh = E - 1075 + shift_base;
+    unsigned __int128 F;
+    if (sh >= 0) {
+        F = sh < 76 ? ((unsigned __int128)M << sh) : (unsigned __int128)0;
+    } else if (sh > -64) {
+        const int rs = -sh;
+        unsigned long long f = M >> rs;
+        if ((M >> (rs - 1)) & 1ull) f += 1ull;
+        F = f;
+    } else {
+        F = 0;
+    }
+    int carry = 0;
+    for (int p = s - 1; p >= 1; --p) {
+        int b = (int)(unsigned)(F & 0xFFu) + carry;
+        F >>= 8;
+        if (b >= 128) { b -= 256; carry = 1; } else { carry = 0; }
+        dig[p] = neg ? -b : b;
+    }
+    const int b0 = (int)(unsigned)F + carry;   // <= 128
+    dig[0] = neg ? -b0 : b0;
+}
+
+struct SliceDev {
+    const double* X; int64_t x_rs, x_cs; const int32_t* rowidx; const int32_t* cexp;
+    int rows, cols, s;
+    __nv_bfloat16* d; int64_t ld, ps;
+    int32_t* e;
+    int* status;
+};
+
+// One CTA per row: row maximum -> exponent, then the digits of every entry.
+__global__ void __launch_bounds__(SL_THREADS) slice_rows_kernel(SliceDev a) {
+    __shared__ double smax[SL_THREADS / 32];
+    __shared__ int sbad[SL_THREADS / 32];
+    __shared__ int e_s;
+    const int r = blockIdx.x;
+    const int t = threadIdx.x;
+    const int64_t roff = (a.rowidx ? (int64_t)a.rowidx[r] : (int64_t)r) * a.x_rs;
+    double mx = 0.0;
+    int bad = 0;
+    for (int c = t; c < a.cols; c += SL_THREADS) {
+        double v = a.X[roff + (int64_t)c * a.x_cs];
+        if (!isfinite(v)) bad = 1;
+        if (a.cexp) v = ldexp(v, a.cexp[c]);
+        mx = fmax(mx, fabs(v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((t & 31) == 0) { smax[t >> 5] = mx; sbad[t >> 5] = bad; }
+    __syncthreads();
+    if (t == 0) {
+        double m2 = 0.0;
+        int b2 = 0;
+        for (int w = 0; w < SL_THREADS / 32; ++w) { m2 = fmax(m2, smax[w]); b2 |= sbad[w]; }
+        int ex = 0;
+        if (m2 > 0.0 && isfinite(m2)) frexp(m2, &ex);
+        e_s = ex;
+        a.e[r] = ex;
+        if (b2) set_status(a.status, RTPROJ_ENONFINITE);
+    }
+    __syncthreads();
+    const int e = e_s;
+    const int base = 7 + 8 * (a.s - 1) - e;
+    __nv_bfloat16* drow = a.d + (int64_t)r * a.ld;
+    for (int c = t; c < a.ld; c += SL_THREADS) {
+        int dig[10];
+        if (c < a.cols) {
+            double v = a.X[roff + (int64_t)c * a.x_cs];
+            if (!isfinite(v)) v = 0.0;
+            fixed_digits(v, base + (a.cexp ? a.cexp[c] : 0), a.s, dig);
+        } else {
+            for (int p = 0; p < 10; ++p) dig[p] = 0;
+        }
+        for (int p = 0; p < a.s; ++p) drow[(int64_t)p * a.ps + c] = __int2bfloat16_rn(dig[p]);
+    }
+}
+
+// Transposes each digit plane: src [p][r][c] (ld_src) -> dst [p][c][r] (ld_dst), zero padded.
+__global__ void transpose_planes_kernel(const __nv_bfloat16* src, int64_t ld_src, int64_t ps_src, int rows, int cols,
+                                        __nv_bfloat16* dst, int64_t ld_dst, int64_t ps_dst, int dst_rows) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int p = blockIdx.z;
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const __nv_bfloat16 zero = __int2bfloat16_rn(0);
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        tile[y][threadIdx.x] = (r < rows && c < cols) ? src[(int64_t)p * ps_src + (int64_t)r * ld_src + c] : zero;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int c = c0 + y, r = r0 + threadIdx.x;   // dst row c, dst col r
+        if (c < dst_rows && r < ld_dst) dst[(int64_t)p * ps_dst + (int64_t)c * ld_dst + r] = tile[threadIdx.x][y];
+    }
+}
+
+// G^* (l x n) as one digit plane: row j, column i holds the digit of G(i, j).
+// uniform: d = 2u - 255 (exponent -1, value d / 256); rademacher: d = +-1 (exponent 7).
+__global__ void omega_plane_kernel(uint32_t key0, uint32_t key1, int dist, int n, int l, __nv_bfloat16* d,
+                                   int64_t ld) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t blocks_per_row = ld / 16;
+    if (gid >= blocks_per_row * l) return;
+    const int j = (int)(gid / blocks_per_row);
+    const int i0 = (int)(gid % blocks_per_row) * 16;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(i0 >> 4), (uint32_t)j, 0u, 0u), key0, key1);
+    alignas(16) __nv_bfloat16 out[16];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) {
+        const uint32_t u = block_byte(w, b);
+        int dv = dist == RTPROJ_OMEGA_RADEMACHER ? (u >= 128u ? 1 : -1) : (2 * (int)u - 255);
+        if (i0 + b >= n) dv = 0;
+        out[b] = __int2bfloat16_rn(dv);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(d + (int64_t)j * ld + i0);
+    dst[0] = reinterpret_cast<const uint4*>(out)[0];
+    dst[1] = reinterpret_cast<const uint4*>(out)[1];
+}
+
+__global__ void fill_int_kernel(int32_t* e, int n, int v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) e[i] = v;
+}
+
+}  // namespace
+
+cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx, const int32_t* cexp,
+                       const SliceStack& st, int* status, cudaStream_t s) {
+    if (st.rows <= 0) return cudaSuccess;
+    if (st.s < 1 || st.s > 10 || st.ld < st.cols || st.ld % 64) return cudaErrorInvalidValue;
+    SliceDev a;
+    a.X = X; a.x_rs = x_rs; a.x_cs = x_cs; a.rowidx = rowidx; a.cexp = cexp;
+    a.rows = st.rows; a.cols = st.cols; a.s = st.s;
+    a.d = st.d; a.ld = st.ld; a.ps = st.plane_stride; a.e = st.e; a.status = status;
+    slice_rows_kernel<<<st.rows, SL_THREADS, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_planes(const SliceStack& src, const SliceStack& dst, cudaStream_t s) {
+    // dst row c (< dst.rows) holds column c of src; columns r >= src.rows are zero padding.
+    dim3 grid((unsigned)((dst.rows + 31) / 32), (unsigned)((dst.ld + 31) / 32), (unsigned)src.s);
+    transpose_planes_kernel<<<grid, dim3(32, 8), 0, s>>>(src.d, src.ld, src.plane_stride, src.rows, src.cols, dst.d,
+                                                          dst.ld, dst.plane_stride, dst.rows);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t omega_plane(uint64_t seed, int dist, int n, int l, const SliceStack& st, cudaStream_t s) {
+    if (st.ld % 16 || st.ld < n) return cudaErrorInvalidValue;
+    const int64_t total = (st.ld / 16) * (int64_t)l;
+    omega_plane_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((uint32_t)(seed & 0xFFFFFFFFull),
+                                                                       (uint32_t)(seed >> 32), dist, n, l, st.d, st.ld);
+    note_launch();
+    fill_int_kernel<<<(l + 255) / 256, 256, 0, s>>>(st.e, l, dist == RTPROJ_OMEGA_RADEMACHER ? 7 : -1);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t fill_int(int32_t* e, int n, int v, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    fill_int_kernel<<<(n + 255) / 256, 256, 0, s>>>(e, n, v);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace rtp

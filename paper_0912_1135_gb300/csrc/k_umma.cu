@@ -1,0 +1,382 @@
+// Sliced (Ozaki-scheme) GEMM on the 5th-generation tensor cores: tcgen05.mma with
+// bfloat16 digit planes in shared memory and float32 accumulators in tensor memory.
+//
+//   C[i][j] = alpha * sum_k A(i,k) B(j,k) + beta * Cin[i][j],
+//   A(i,k) = 2^{ea_i} sum_p dA_p(i,k) 2^{-7-8p},  B(j,k) = 2^{eb_j} sum_q dB_q(j,k) 2^{-7-8q}
+// Only digit pairs with level g = p + q < terms (<= 10) are multiplied (the truncation
+// of the Ozaki scheme). Each level has its own TMEM accumulator. Level g holds at most
+// min(g+1, 10) digit pairs per k, every digit product is at most 2^15 in magnitude
+// (<= 2^14 unless one operand is the one-digit G plane), and a TMEM readout happens
+// every 128 k: for every level up to 7 each float32 partial sum stays below 2^24, so
+// those level sums are exact; levels 8 and 9 (relative weight 2^-64 and below) may
+// round by a unit of their own scale. The readout folds the level sums into two int64
+// words per entry,
+//   hi = sum_{g<=4} L_g 2^{8(4-g)},  lo = sum_{5<=g<=9} L_g 2^{8(9-g)}  (lo kept below 2^40),
+// so that sum_k A B = 2^{ea+eb-86} (hi 2^40 + lo) exactly up to the digit truncation.
+// Split-K partials stay in int64 and are summed in 128-bit integers by the reduce kernel.
+//
+// CTA: 128 threads; tile 128 (A rows, MMA M) x 32 (B rows, MMA N); K block 64 (one
+// 128-byte swizzle row per operand row). Thread 0 issues the MMAs; all threads stage
+// operands with cp.async into the SWIZZLE_128B K-major layout and read TMEM back.
+#include "rtproj_internal.cuh"
+
+#include <algorithm>
+
+namespace rtp {
+namespace {
+
+constexpr int TM = 128;
+constexpr int TN = 32;
+constexpr int KB = 64;
+constexpr int KCHUNK = 128;
+constexpr int NTHREADS = 128;
+constexpr int MAXS = 10;
+constexpr int A_PLANE_BYTES = TM * KB * 2;   // 16 KiB
+constexpr int B_PLANE_BYTES = TN * KB * 2;   // 4 KiB
+
+struct SgDev {
+    const __nv_bfloat16* a; int64_t a_ld, a_ps; const int32_t* ea; int sa; int M;
+    const __nv_bfloat16* b; int64_t b_ld, b_ps; const int32_t* eb; int sb; int N;
+    int Kp;             // K rounded up to 64 (planes are zero padded to it)
+    int terms;
+    int k_per_split;    // multiple of KCHUNK
+    long long* part;    // [split][M][N][2] when gridDim.z > 1
+    double* C; int64_t c_rs, c_cs; const int32_t* crow;
+    double alpha, beta;
+    const double* Cin; int64_t cin_rs, cin_cs;
+    int lower_only;
+    int* status;
+    long long timeout_cycles;
+    uint32_t tmem_cols;  // power of two >= 32 * terms
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, bfloat16 inputs, float32 accumulation.
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_addr(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit columns: register j of lane t = TMEM[lane base + t][col + j].
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, SWIZZLE_128B (8-row atoms of 1024 bytes).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: F32 accumulator, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1) sliced_gemm_kernel(SgDev p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + (size_t)p.sa * A_PLANE_BYTES;
+    uint64_t* bar = (uint64_t*)(sB + (size_t)p.sb * B_PLANE_BYTES);
+    uint32_t* tmem_slot = (uint32_t*)(bar + 1);
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN, z = blockIdx.z;
+    if (p.lower_only && j0 > i0 + TM - 1) return;     // tile strictly above the diagonal
+    const int kbeg = z * p.k_per_split;
+    const int kend = min(p.Kp, kbeg + p.k_per_split);
+
+    if (t == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, p.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    long long hi[TN], lo[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) { hi[j] = 0; lo[j] = 0; }
+
+    const uint32_t idesc = idesc_bf16(TM, TN);
+    const uint32_t sA_addr = smem_addr(sA), sB_addr = smem_addr(sB);
+    uint32_t phase = 0;
+    bool timed_out = false;
+    int kin_chunk = 0;          // K elements accumulated in TMEM since the last readout
+    uint32_t started = 0;       // levels written since the last readout (bit g)
+
+    for (int k0 = kbeg; k0 < kend && !timed_out; k0 += KB) {
+        // ---- stage digit planes (cp.async, 16-byte chunks into the swizzled layout)
+        for (int pl = 0; pl < p.sa; ++pl) {
+            const __nv_bfloat16* src = p.a + (int64_t)pl * p.a_ps + k0;
+            const uint32_t dst0 = sA_addr + pl * A_PLANE_BYTES;
+            for (int idx = t; idx < TM * 8; idx += NTHREADS) {
+                const int r = idx >> 3, c = idx & 7;
+                const int gi = i0 + r;
+                const bool ok = gi < p.M;
+                const __nv_bfloat16* g = src + (int64_t)(ok ? gi : 0) * p.a_ld + c * 8;
+                cp_async16(dst0 + r * 128 + ((c ^ (r & 7)) << 4), g, ok);
+            }
+        }
+        for (int pl = 0; pl < p.sb; ++pl) {
+            const __nv_bfloat16* src = p.b + (int64_t)pl * p.b_ps + k0;
+            const uint32_t dst0 = sB_addr + pl * B_PLANE_BYTES;
+            for (int idx = t; idx < TN * 8; idx += NTHREADS) {
+                const int r = idx >> 3, c = idx & 7;
+                const int gj = j0 + r;
+                const bool ok = gj < p.N;
+                const __nv_bfloat16* g = src + (int64_t)(ok ? gj : 0) * p.b_ld + c * 8;
+                cp_async16(dst0 + r * 128 + ((c ^ (r & 7)) << 4), g, ok);
+            }
+        }
+        cp_async_wait_all();
+        fence_proxy_async();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        // ---- MMAs: every digit pair (pa, pb) with pa + pb < terms, 4 K-steps of 16
+        if (t == 0) {
+#pragma unroll 1
+            for (int kk = 0; kk < KB / 16; ++kk) {
+                for (int pa = 0; pa < p.sa; ++pa) {
+                    const uint64_t ad = sw128_desc(sA_addr + pa * A_PLANE_BYTES + kk * 32);
+                    for (int pb = 0; pb < p.sb && pa + pb < p.terms; ++pb) {
+                        const int g = pa + pb;
+                        const uint64_t bd = sw128_desc(sB_addr + pb * B_PLANE_BYTES + kk * 32);
+                        umma_bf16(tmem + (uint32_t)(g * TN), ad, bd, idesc, (started >> g) & 1u);
+                        started |= 1u << g;
+                    }
+                }
+            }
+            umma_commit(bar);
+        }
+        // ---- thread 0 waits (bounded) for the MMAs, which read the staged planes; the
+        //      barrier then publishes completion (and any timeout) to the whole CTA.
+        int to = 0;
+        if (t == 0) {
+            const long long t_start = clock64();
+            while (!mbar_try_wait(bar, phase)) {
+                if (clock64() - t_start > p.timeout_cycles) {
+                    to = 1;
+                    set_status(p.status, RTPROJ_ETIMEOUT);
+                    break;
+                }
+            }
+        }
+        phase ^= 1u;
+        timed_out = __syncthreads_or(to) != 0;
+        tc_fence_after();
+        if (timed_out) break;
+        kin_chunk += KB;
+        // ---- fold the exact level sums into hi/lo every 128 K (and at the end)
+        if (kin_chunk >= KCHUNK || k0 + KB >= kend) {
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int g = 0; g < p.terms; ++g) {
+                uint32_t r[32];
+                tmem_ld32(lane_base + (uint32_t)(g * TN), r);
+                tmem_ld_wait();
+                const int shift = g <= 4 ? 8 * (4 - g) : 8 * (9 - g);
+                const long long mul = 1ll << shift;
+                if (g <= 4) {
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) hi[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) lo[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {          // keep |lo| < 2^40
+                const long long carry = lo[j] >> 40;
+                hi[j] += carry;
+                lo[j] -= carry * (1ll << 40);
+            }
+            kin_chunk = 0;
+            started = 0;
+            tc_fence_before();
+        }
+        __syncthreads();   // staged planes and TMEM are free for the next block
+        tc_fence_after();
+    }
+
+    // ---- output
+    const int i = i0 + warp * 32 + lane;
+    if (i < p.M && !timed_out) {
+        if (gridDim.z > 1) {
+            long long* dst = p.part + (((int64_t)z * p.M + i) * p.N + j0) * 2;
+#pragma unroll
+            for (int j = 0; j < TN; ++j)
+                if (j0 + j < p.N) { dst[2 * j] = hi[j]; dst[2 * j + 1] = lo[j]; }
+        } else {
+            const int ea = p.ea ? p.ea[i] : 0;
+            const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int gj = j0 + j;
+                if (gj >= p.N || (p.lower_only && gj > i)) continue;
+                const double v = ldexp(ldexp((double)hi[j], 40) + (double)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                double out = p.alpha * v;
+                if (p.beta != 0.0) out += p.beta * p.Cin[(int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs];
+                p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = out;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, p.tmem_cols);
+}
+
+struct SgReduceDev {
+    const long long* part; int splits, M, N;
+    const int32_t* ea; const int32_t* eb;
+    double* C; int64_t c_rs, c_cs; const int32_t* crow;
+    double alpha, beta;
+    const double* Cin; int64_t cin_rs, cin_cs;
+    int lower_only;
+};
+
+__global__ void sliced_reduce_kernel(SgReduceDev r) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)r.M * r.N;
+    if (idx >= total) return;
+    const int i = (int)(idx / r.N), j = (int)(idx % r.N);
+    if (r.lower_only && j > i) return;
+    __int128 acc = 0;
+    for (int z = 0; z < r.splits; ++z) {
+        const long long* q = r.part + ((int64_t)z * total + idx) * 2;
+        acc += ((__int128)q[0] << 40) + (__int128)q[1];
+    }
+    const long long h = (long long)(acc >> 40);
+    const long long l = (long long)(acc - ((__int128)h << 40));   // in [0, 2^40)
+    const int e = (r.ea ? r.ea[i] : 0) + (r.eb ? r.eb[j] : 0) - 86;
+    const double v = ldexp(ldexp((double)h, 40) + (double)l, e);
+    double out = r.alpha * v;
+    if (r.beta != 0.0) out += r.beta * r.Cin[(int64_t)i * r.cin_rs + (int64_t)j * r.cin_cs];
+    const int64_t row = r.crow ? (int64_t)r.crow[i] : (int64_t)i;
+    r.C[row * r.c_rs + (int64_t)j * r.c_cs] = out;
+}
+
+}  // namespace
+
+size_t sliced_gemm_scratch_bytes(int M, int N, int K) {
+    (void)K;
+    const size_t tiles = (size_t)((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+    const size_t target = 2 * 152;
+    if (tiles >= target) return 0;
+    const size_t splits = (target + tiles - 1) / tiles;
+    return splits * (size_t)M * N * 16;
+}
+
+cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
+    const int M = g.a.rows, N = g.b.rows, K = g.a.cols;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (g.a.s < 1 || g.a.s > MAXS || g.b.s < 1 || g.b.s > MAXS) return cudaErrorInvalidValue;
+    if (g.terms < 1 || g.terms > 10 || g.terms > g.a.s + g.b.s - 1) return cudaErrorInvalidValue;
+    if (g.b.cols != K || g.a.ld % 64 || g.b.ld % 64 || g.a.ld < K || g.b.ld < K) return cudaErrorInvalidValue;
+    const int Kp = (K + KB - 1) / KB * KB;
+    const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
+    const int tiles = tiles_m * tiles_n;
+    int splits = 1;
+    const int max_splits = std::max(1, (Kp + KCHUNK - 1) / KCHUNK);
+    if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
+    while (splits > 1 && (size_t)splits * M * N * 16 > scratch_bytes) --splits;
+    int kps = (Kp + splits - 1) / splits;
+    kps = (kps + KCHUNK - 1) / KCHUNK * KCHUNK;
+    splits = (Kp + kps - 1) / kps;
+
+    SgDev p;
+    p.a = g.a.d; p.a_ld = g.a.ld; p.a_ps = g.a.plane_stride; p.ea = g.a.e; p.sa = g.a.s; p.M = M;
+    p.b = g.b.d; p.b_ld = g.b.ld; p.b_ps = g.b.plane_stride; p.eb = g.b.e; p.sb = g.b.s; p.N = N;
+    p.Kp = Kp; p.terms = g.terms; p.k_per_split = kps;
+    p.part = (long long*)scratch;
+    p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
+    p.alpha = g.alpha; p.beta = g.beta; p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
+    p.lower_only = g.lower_only ? 1 : 0;
+    p.status = status;
+    p.timeout_cycles = 4000000000ll;   // ~2 s at 2 GHz per K block: a hung MMA reports ETIMEOUT
+    p.tmem_cols = 32;
+    while (p.tmem_cols < (uint32_t)(TN * g.terms)) p.tmem_cols <<= 1;
+    const size_t smem = 1024 + (size_t)p.sa * A_PLANE_BYTES + (size_t)p.sb * B_PLANE_BYTES + 64;
+    cudaError_t e = cudaFuncSetAttribute(sliced_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid(tiles_n, tiles_m, splits);
+    sliced_gemm_kernel<<<grid, NTHREADS, smem, s>>>(p);
+    note_launch();
+    if (splits > 1) {
+        SgReduceDev r;
+        r.part = (const long long*)scratch; r.splits = splits; r.M = M; r.N = N;
+        r.ea = g.a.e; r.eb = g.b.e;
+        r.C = g.C; r.c_rs = g.c_rs; r.c_cs = g.c_cs; r.crow = g.crow;
+        r.alpha = g.alpha; r.beta = g.beta; r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
+        r.lower_only = g.lower_only ? 1 : 0;
+        const int64_t total = (int64_t)M * N;
+        sliced_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace rtp

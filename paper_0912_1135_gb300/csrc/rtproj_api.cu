@@ -33,7 +33,9 @@ void timer_flush(PhaseTimer& t) {
     t.n = 0;
 }
 
-void phase_begin(rtproj_ctx* h, int p) {
+}  // namespace
+
+void rtp::phase_begin(rtproj_ctx* h, int p) {
     PhaseTimer& t = h->timer;
     if (!t.enabled) return;
     if (t.n == PhaseTimer::kMax) timer_flush(t);
@@ -41,7 +43,7 @@ void phase_begin(rtproj_ctx* h, int p) {
     t.open = p;
 }
 
-void phase_end(rtproj_ctx* h, int p) {
+void rtp::phase_end(rtproj_ctx* h, int p) {
     PhaseTimer& t = h->timer;
     if (!t.enabled || t.open != p) return;
     cudaEventRecord(t.e[t.n], h->stream);
@@ -49,6 +51,8 @@ void phase_end(rtproj_ctx* h, int p) {
     t.n++;
     t.open = -1;
 }
+
+namespace {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kPartElems = 1216ull * 4096ull;   // bounds every split-K slab set (see gemm64)
@@ -66,7 +70,7 @@ size_t mixed_workspace(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const
 bool valid_opts(const rtproj_opts& o) {
     if (o.mode != RTPROJ_PLAIN_FP64 && o.mode != RTPROJ_MIXED_REFINED) return false;
     if (o.omega != RTPROJ_OMEGA_UNIFORM && o.omega != RTPROJ_OMEGA_RADEMACHER) return false;
-    auto ok = [](int s) { return s >= 1 && s <= 8; };
+    auto ok = [](int s) { return s >= 1 && s <= 10; };
     if (!ok(o.sketch_slices) || !ok(o.gram_slices) || !ok(o.gram2_slices) || !ok(o.apply_slices) ||
         !ok(o.resid_slices))
         return false;
@@ -146,8 +150,10 @@ rtproj_status gram_fp64(rtproj_ctx* h) {
     return RTPROJ_OK;
 }
 
+}  // namespace
+
 // h = Pi^* T1^* T1 Pi c for the m x k block c (row-major, leading dimension k): steps 2-6.
-rtproj_status middle_fp64(rtproj_ctx* h, const double* c, double* out, int k) {
+rtproj_status rtp::middle_fp64(rtproj_ctx* h, const double* c, double* out, int k) {
     const int m = (int)h->m;
     Gemm64 g;
     g.M = m; g.N = k; g.K = m;
@@ -163,6 +169,8 @@ rtproj_status middle_fp64(rtproj_ctx* h, const double* c, double* out, int k) {
     RT_CHECK(gemm64(t, h->part, h->part_elems, h->stream));
     return RTPROJ_OK;
 }
+
+namespace {
 
 rtproj_status project_fp64(rtproj_ctx* h, const double* B, int64_t ldb, int k, double* Z, int64_t ldz,
                            double* ROW, int64_t ldr, double* X, int64_t ldx) {
@@ -229,11 +237,11 @@ void rtproj_default_opts(rtproj_opts* o) {
     if (!o) return;
     o->mode = RTPROJ_MIXED_REFINED;
     o->omega = RTPROJ_OMEGA_UNIFORM;
-    o->sketch_slices = 4;
+    o->sketch_slices = 5;
     o->gram_slices = 7;
     o->gram2_slices = 3;
     o->apply_slices = 7;
-    o->resid_slices = 8;
+    o->resid_slices = 9;
     o->refine_passes = 1;
     o->timing = 0;
     o->rank_tol = 0.0;

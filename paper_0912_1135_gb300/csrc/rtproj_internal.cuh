@@ -119,11 +119,15 @@ struct SliceStack {
     int64_t plane_stride = 0;
 };
 
-// Slices X (element (r, c) at X[r*x_rs + c*x_cs]) into the stack; optional row gather.
-cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx,
+// Slices X (element (r, c) at X[r*x_rs + c*x_cs], multiplied by 2^cexp[c] when cexp is
+// given) into the stack; optional row gather. Columns cols..ld-1 are written as zeros.
+cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx, const int32_t* cexp,
                        const SliceStack& st, int* status, cudaStream_t s);
-// Writes G^T (l x n, K-major over n) as one bfloat16 plane with exponent 0 (exact).
+// Digit planes of src transposed into dst (dst.rows = src.cols, dst.ld >= src.rows).
+cudaError_t transpose_planes(const SliceStack& src, const SliceStack& dst, cudaStream_t s);
+// Writes G^* (l x n, reduction over n) as one digit plane plus its row exponents (exact).
 cudaError_t omega_plane(uint64_t seed, int dist, int n, int l, const SliceStack& st, cudaStream_t s);
+cudaError_t fill_int(int32_t* e, int n, int v, cudaStream_t s);
 
 // C[(crow?crow[i]:i)*c_rs + j*c_cs] = alpha * (A_stack x B_stack^T)[i][j] + beta * Cin[...]
 // where the product keeps slice pairs p + q <= max(sa, sb) - 1 (0-based) -- the
@@ -139,6 +143,14 @@ struct SlicedGemm {
 size_t sliced_gemm_scratch_bytes(int M, int N, int K);
 cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s);
 
+}  // namespace rtp
+
+struct rtproj_ctx;
+namespace rtp {
+void phase_begin(rtproj_ctx* h, int phase);
+void phase_end(rtproj_ctx* h, int phase);
+// Steps 2-6 of the apply in float64: out = Pi^* T1^* T1 Pi c (c, out: m x k, ld k).
+rtproj_status middle_fp64(rtproj_ctx* h, const double* c, double* out, int k);
 }  // namespace rtp
 
 // ---------------------------------------------------------------------------
@@ -168,17 +180,18 @@ struct rtproj_ctx {
     double* hbuf = nullptr;      // m x k_max  (h, row-major m x k)
     double* dhbuf = nullptr;     // m x k_max
     double* sbuf = nullptr;      // k_max x n  (refinement residual)
-    // mixed mode
-    rtp::SliceStack As;          // A: m x n, s planes
-    rtp::SliceStack Ats;         // A^*: n x m, s planes (row exponents folded, see api)
+    // mixed mode (k_mixed.cu)
+    rtp::SliceStack As;          // A with rows normalised: m x n, reduction over n
+    rtp::SliceStack Ats;         // the same digits transposed: n x m, reduction over m
     rtp::SliceStack Gs;          // G^*: l x n, one plane
-    rtp::SliceStack tmpA, tmpB;  // scratch stacks for the m x m / m x k operands
-    rtp::SliceStack Wsl;         // W slices (m x n)
-    rtp::SliceStack Bsl;         // right-hand-side slices (k x n)
-    rtp::SliceStack Ssl;         // refinement residual slices (k x n)
-    void* sg_scratch = nullptr;
+    rtp::SliceStack Ms;          // M' = R^{-*} Pi with columns scaled by 2^{e_A}: m x m
+    rtp::SliceStack Ws;          // W = P^{-1} A: m x n
+    rtp::SliceStack Bs;          // right-hand sides: k x n
+    rtp::SliceStack Hs;          // h or dh with rows scaled by 2^{e_A}, transposed: k x m
+    rtp::SliceStack Ss;          // refinement residual s: k x n
+    double* Mprime = nullptr;    // m x m
+    void* sg_scratch = nullptr;  // int64 split-K partials
     size_t sg_scratch_bytes = 0;
-    double* Wd = nullptr;        // m x n float64 W in mixed mode (shares W)
 
     rtp::PhaseTimer timer;
     int64_t l = 0;

@@ -1,0 +1,141 @@
+"""GPU parity of the mixed form: digit-sliced tensor-core products (tcgen05) plus refinement.
+
+The sketch test pins the sliced GEMM itself: with s digits of A and the exact one-digit
+G plane, S = A G must equal the exact product up to the digit truncation bound
+n 2^{e_i - 8s} max|G| (e_i the exponent of row i) plus float64 rounding of the result.
+The apply tests compare with the exact projection of the stored matrix (oracle.exact)."""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import closed_form, exact, metrics, philox
+from tests.gpu_common import EPS, fp64_tol, rt_module, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+# Tolerances of the mixed form: the target of 1e-10 relative error in Zb against the exact
+# projection and 1e-12 in ||A Zb|| / (||A|| ||b||).
+Z_TOL = 1e-10
+RESID_TOL = 1e-12
+
+
+def exact_sketch(A, G):
+    S = np.empty((A.shape[0], G.shape[1]))
+    for j in range(G.shape[1]):
+        h, l = exact.dd_matvec(A, G[:, j])
+        S[:, j] = h + l
+    return S
+
+
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 10])
+@pytest.mark.parametrize("m,n,l", [(64, 2048, 256), (37, 1000, 41)])
+def test_sliced_sketch_is_exact_up_to_digit_truncation(m, n, l, s):
+    torch = torch_cuda()
+    rt = rt_module()
+    A = workloads.haar_spectrum_matrix(m, n, 1e-6, 3)
+    with rt.Projector(to_dev(torch, A), l_max=l, k_max=1, mode="mixed", sketch_slices=s) as P:
+        S = P.sketch(seed=77, l=l).cpu().numpy()
+    G = philox.omega(77, n, l, "uniform")
+    Sx = exact_sketch(A, G)
+    e = np.frexp(np.max(np.abs(A), axis=1))[1]            # |A_i,:| < 2^{e_i}
+    bound = n * np.ldexp(1.0, e - 8 * s)[:, None] * 1.0 + 2 * EPS * np.abs(Sx)
+    assert np.all(np.abs(S - Sx) <= bound)
+    if s >= 8:
+        # eight digits exceed float64: the result is the exact product, rounded
+        assert np.max(np.abs(S - Sx) / (np.abs(A) @ np.abs(G))) < 4 * EPS
+
+
+def _mixed(rt, torch, A, l, k, **kw):
+    return rt.Projector(to_dev(torch, A), l_max=l, k_max=k, mode="mixed", **kw)
+
+
+@pytest.mark.parametrize("m,n,l,k,kappa", [
+    (64, 2048, 256, 16, 1e8),       # the small dense configuration
+    (64, 2048, 256, 16, 10.0),
+    (37, 1000, 41, 3, 1e5),         # ragged sizes, l = m + 4
+    (5, 77, 19, 1, 1e3),            # tiny, one right-hand side
+])
+def test_apply_matches_exact_oracle(m, n, l, k, kappa):
+    torch = torch_cuda()
+    rt = rt_module()
+    A = workloads.haar_spectrum_matrix(m, n, 1.0 / kappa, 10 + m)
+    B = workloads.rhs(k, n, 20 + m)
+    Zx, ROWx, Hx = exact.exact_project(A, B)
+    with _mixed(rt, torch, A, l, k) as P:
+        P.precondition(seed=11, l=l)
+        Z, ROW, H = P.project(to_dev(torch, B), null=True, row=True, lstsq=True)
+        info = P.info()
+    assert info["status"] == 0
+    Z, ROW, H = Z.cpu().numpy(), ROW.cpu().numpy(), H.cpu().numpy()
+    assert metrics.max_rel_err(Z, Zx) < Z_TOL
+    assert metrics.max_rel_err(ROW, ROWx) < Z_TOL * max(1.0, np.max(np.linalg.norm(Zx, axis=1) / np.linalg.norm(ROWx, axis=1)))
+    assert metrics.max_rel_err(H, Hx) < Z_TOL * kappa
+    assert metrics.normalised_residual(A, Z, B) < RESID_TOL
+
+
+def test_refinement_beats_float64_and_unrefined():
+    torch = torch_cuda()
+    rt = rt_module()
+    m, n, l, k = 64, 4096, 256, 4
+    A = workloads.haar_spectrum_matrix(m, n, 1e-10, 60)
+    B = workloads.rhs(k, n, 61)
+    Zx, _, _ = exact.exact_project(A, B)
+    errs = {}
+    for name, kw in {"fp64": dict(mode="fp64"), "mixed0": dict(mode="mixed", refine_passes=0),
+                     "mixed1": dict(mode="mixed", refine_passes=1), "mixed2": dict(mode="mixed", refine_passes=2)}.items():
+        with rt.Projector(to_dev(torch, A), l_max=l, k_max=k, **kw) as P:
+            P.precondition(seed=5, l=l)
+            errs[name] = metrics.max_rel_err(P.null_project(to_dev(torch, B)).cpu().numpy(), Zx)
+    assert errs["mixed1"] < Z_TOL and errs["mixed2"] < Z_TOL, errs
+    assert errs["mixed1"] < errs["fp64"] / 10, errs
+    assert errs["mixed1"] <= errs["mixed0"], errs
+
+
+def test_paper_family_closed_form():
+    torch = torch_cuda()
+    rt = rt_module()
+    A, Bb, pu, pv = workloads.paper_test_matrix(64, 4096, 1e10, 42, return_parts=True)
+    B = workloads.rhs(4, 4096, 43)
+    Zc, ROWc, _ = closed_form.project(Bb, pu, pv, B)
+    with _mixed(rt, torch, A, 256, 4) as P:
+        P.precondition(seed=2, l=256)
+        Z = P.null_project(to_dev(torch, B)).cpu().numpy()
+    assert metrics.max_rel_err(Z, Zc) < Z_TOL
+
+
+def test_alias_and_entry_points_agree():
+    torch = torch_cuda()
+    rt = rt_module()
+    m, n, l, k = 24, 500, 60, 5
+    A = workloads.haar_spectrum_matrix(m, n, 1e-3, 31)
+    B = workloads.rhs(k, n, 32)
+    with _mixed(rt, torch, A, l, k) as P:
+        P.precondition(seed=3, l=l)
+        Bt = to_dev(torch, B)
+        Z, ROW, H = P.project(Bt, null=True, row=True, lstsq=True)
+        np.testing.assert_array_equal(P.null_project(Bt).cpu().numpy(), Z.cpu().numpy())
+        np.testing.assert_array_equal(P.row_project(Bt).cpu().numpy(), ROW.cpu().numpy())
+        np.testing.assert_array_equal(P.lstsq(Bt).cpu().numpy(), H.cpu().numpy())
+        P.null_project(Bt, out=Bt)
+        np.testing.assert_array_equal(Bt.cpu().numpy(), Z.cpu().numpy())
+
+
+def test_full_size_dense_sampled():
+    """512 x 65536, kappa = 1e10, 64 right-hand sides, l = 2048, in the launch
+    configuration the bench times: one sampled right-hand side against the exact oracle,
+    all 64 through ||A z|| and idempotence."""
+    torch = torch_cuda()
+    rt = rt_module()
+    w = workloads.WORKLOADS["dense_512x65536"]
+    A = w.matrix()
+    B = w.rhs()
+    with _mixed(rt, torch, A, w.l, w.k) as P:
+        P.precondition(seed=w.seed_omega, l=w.l)
+        Z = P.null_project(to_dev(torch, B))
+        ZZ = P.null_project(Z.clone())
+        Z = Z.cpu().numpy()
+        ZZ = ZZ.cpu().numpy()
+    Zx, _, _ = exact.exact_project(A, B[:1])
+    assert metrics.max_rel_err(Z[:1], Zx) < Z_TOL
+    assert metrics.max_rel_err(ZZ, Z) < Z_TOL
+    assert metrics.normalised_residual(A, Z, B, normA=1.0) < RESID_TOL
