@@ -160,6 +160,23 @@ rtproj_status rtproj_project(rtproj_t h, const double* B, int64_t ldb, int64_t k
    Synchronizes. Used to test the sketch step on its own. */
 rtproj_status rtproj_sketch(rtproj_t h, uint64_t seed, int64_t l, double* S, int64_t lds);
 
+/* The float64 sketch S = A G of rtproj_sketch, for callers that cannot allocate device
+   memory: applications whose device memory is owned by a pooling allocator or a fixed
+   budget (a cudaMalloc would fail or fragment the pool), and loops that cannot afford the
+   device synchronization cudaMalloc implies. The paper has no counterpart; this is a
+   packaging of its sketch step (Eq. 12) that needs no workspace.
+   A (m x n, row-major, lda >= n) and S (m x l, row-major, lds >= l) are device pointers,
+   m <= l <= n; omega is an rtproj_omega value; stream is a cudaStream_t passed as void*.
+   The split-K scratch is a fixed array inside the library: 32 MiB of device memory
+   (4 Mi float64 entries), held on every GPU that loads the library until the process
+   exits. Nothing is allocated. Returns RTPROJ_ENOMEM when m * l exceeds 4 Mi entries and
+   RTPROJ_EINVAL for invalid sizes; asynchronous otherwise. The first call on a device
+   looks up the array's device address (with that device current): make it before any
+   stream capture. Every call shares the array and overwrites what it reads from it;
+   calls that overlap on the GPU race on it, so serialize them. */
+rtproj_status rtproj_sketch_noalloc(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed,
+                                    int64_t l, int omega, double* S, int64_t lds, void* stream);
+
 /* Copies the preconditioner state to HOST buffers (any may be NULL): R (m x m,
    row-major, upper triangular), perm (m entries: position j of the pivoted QR holds
    original column perm[j] of S^*, so (Pi x)[j] = x[perm[j]]), and Lc (m x m, the

@@ -73,6 +73,7 @@ EXPORTS = {
     "rtproj_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "rtproj_get_timings": (ctypes.c_int, [_P, _P, _P]),
     "rtproj_launch_count": (ctypes.c_uint64, []),
+    "rtproj_sketch_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, ctypes.c_uint64, _I64, ctypes.c_int, _P, _I64, _P]),
 }
 
 PHASES = ["sketch", "qr", "gram", "factor", "apply_a", "apply_m", "apply_at", "slice"]
