@@ -151,9 +151,218 @@ __global__ void qr_extract_r_kernel(const double* S, int m, int64_t lds, double*
     R[idx] = (i <= c) ? S[(int64_t)c * lds + i] : 0.0;
 }
 
+
+// ---------------------------------------------------------------------------------
+// Persistent form: one cooperative launch for all m steps. CTA b keeps columns
+// [b*cpc, b*cpc + cpc) of S^* (rows of S) in shared memory for the whole
+// factorization. Per step j: every CTA publishes the best remaining column norm it
+// owns and arrives on a grid-wide counter; after all have arrived each CTA picks the
+// global pivot (largest norm, lowest index on ties); the owner of the pivot builds the
+// reflector and publishes it (with a release flag); the others fetch it from L2 and
+// apply it to their active columns, downdating the norms. Columns never move: the
+// pivot column is retired and R[:, j] is the retired column's first j+1 entries.
+// Every wait has a clock deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all
+// CTAs leave their loops.
+// ---------------------------------------------------------------------------------
+constexpr int PQ_THREADS = 256;
+constexpr int PQ_WARPS = PQ_THREADS / 32;
+constexpr int PQ_MAXC = 32;
+
+struct PqrDev {
+    double* S; int m, l; int64_t lds;
+    double* R; int32_t* perm;
+    int cpc;
+    double* vbuf;            // 2 x l
+    double* scal;            // 2 x 2
+    double* bval;            // 2 x G
+    int* bidx;               // 2 x G
+    unsigned int* counter;   // arrivals (monotonic)
+    unsigned int* flags;     // m: reflector j published
+    int* abort_flag;
+    int* status;
+    long long timeout;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until *p >= target (or the abort flag is raised). Returns false on abort.
+__device__ bool wait_geq(const unsigned int* p, unsigned int target, int* abort_flag, int* status, long long timeout) {
+    const long long t0 = clock64();
+    while (ld_acquire(p) < target) {
+        if (*(volatile int*)abort_flag) return false;
+        if (clock64() - t0 > timeout) {
+            atomicExch(abort_flag, 1);
+            set_status(status, RTPROJ_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) {
+    extern __shared__ double smem_d[];
+    const int l = p.l, m = p.m, cpc = p.cpc;
+    double* cols = smem_d;                 // cpc x l
+    double* v = cols + (size_t)cpc * l;    // l
+    __shared__ double vn1[PQ_MAXC], vn2[PQ_MAXC];
+    __shared__ int posq[PQ_MAXC];
+    __shared__ double redv[PQ_WARPS];
+    __shared__ int redi[PQ_WARPS];
+    __shared__ int piv_s, ok_s;
+    __shared__ double beta_s;
+    const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int c0 = b * cpc;
+    const int nc = max(0, min(cpc, m - c0));
+
+    for (int q = 0; q < nc; ++q)
+        for (int i = t; i < l; i += PQ_THREADS) cols[(size_t)q * l + i] = p.S[(int64_t)(c0 + q) * p.lds + i];
+    __syncthreads();
+    for (int q = warp; q < nc; q += PQ_WARPS) {
+        const double* c = cols + (size_t)q * l;
+        double s = 0.0;
+        for (int i = lane; i < l; i += 32) s = fma(c[i], c[i], s);
+        s = warp_sum(s);
+        if (lane == 0) { vn1[q] = sqrt(s); vn2[q] = sqrt(s); posq[q] = -1; }
+    }
+    __syncthreads();
+
+    bool alive = true;
+    for (int j = 0; j < m && alive; ++j) {
+        const int par = j & 1;
+        // 1. publish the local best, arrive, wait for everyone
+        if (t == 0) {
+            double best = -1.0;
+            int bi = m;
+            for (int q = 0; q < nc; ++q)
+                if (posq[q] < 0 && (vn1[q] > best)) { best = vn1[q]; bi = c0 + q; }
+            p.bval[par * G + b] = best;
+            p.bidx[par * G + b] = bi;
+            __threadfence();
+            atomicAdd(p.counter, 1u);
+            ok_s = wait_geq(p.counter, (unsigned int)(j + 1) * (unsigned int)G, p.abort_flag, p.status, p.timeout);
+        }
+        __syncthreads();
+        if (!ok_s) { alive = false; break; }
+        // 2. global pivot: largest norm, lowest column index on ties
+        double best = -1.0;
+        int bi = m;
+        for (int g = t; g < G; g += PQ_THREADS) {
+            const double x = __ldcg(p.bval + par * G + g);
+            const int i = __ldcg(p.bidx + par * G + g);
+            if (x > best || (x == best && i < bi)) { best = x; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+        __syncthreads();
+        if (t == 0) {
+            double bb = redv[0];
+            int ii = redi[0];
+            for (int w = 1; w < PQ_WARPS; ++w)
+                if (redv[w] > bb || (redv[w] == bb && redi[w] < ii)) { bb = redv[w]; ii = redi[w]; }
+            piv_s = ii < m ? ii : -1;
+        }
+        __syncthreads();
+        const int piv = piv_s;
+        if (piv < 0) { alive = false; break; }     // cannot happen while columns remain
+        const int owner = piv / cpc;
+        double* vg = p.vbuf + (size_t)par * l;
+        if (owner == b) {
+            // 3a. the owner builds the reflector from its column
+            const int q = piv - c0;
+            double* c = cols + (size_t)q * l;
+            double s = 0.0;
+            for (int i = j + t; i < l; i += PQ_THREADS) s = fma(c[i], c[i], s);
+            s = warp_sum(s);
+            if (lane == 0) redv[warp] = s;
+            __syncthreads();
+            if (t == 0) {
+                double nx2 = 0.0;
+                for (int w = 0; w < PQ_WARPS; ++w) nx2 += redv[w];
+                const double nx = sqrt(nx2);
+                const double x0 = c[j];
+                double alpha = 0.0, beta = 0.0;
+                if (nx > 0.0) {
+                    alpha = x0 >= 0.0 ? -nx : nx;
+                    beta = 1.0 / (nx * (nx + fabs(x0)));
+                }
+                v[0] = x0 - alpha;
+                vg[0] = x0 - alpha;
+                p.scal[par * 2 + 1] = beta;
+                beta_s = beta;
+                c[j] = alpha;
+                posq[q] = j;
+                p.perm[j] = piv;
+            }
+            for (int i = j + 1 + t; i < l; i += PQ_THREADS) {
+                v[i - j] = c[i];
+                vg[i - j] = c[i];
+            }
+            __threadfence();
+            __syncthreads();
+            if (t == 0) st_release(p.flags + j, 1u);
+        } else {
+            // 3b. the others fetch it
+            if (t == 0) ok_s = wait_geq(p.flags + j, 1u, p.abort_flag, p.status, p.timeout);
+            __syncthreads();
+            if (!ok_s) { alive = false; break; }
+            for (int i = t; i < l - j; i += PQ_THREADS) v[i] = __ldcg(vg + i);
+            if (t == 0) beta_s = __ldcg(p.scal + par * 2 + 1);
+            __syncthreads();
+        }
+        // 4. apply I - beta v v^* to the active columns, downdate their norms
+        const double beta = beta_s;
+        for (int q = warp; q < nc; q += PQ_WARPS) {
+            if (posq[q] >= 0) continue;
+            double* c = cols + (size_t)q * l + j;
+            const int len = l - j;
+            double w = 0.0;
+            for (int i = lane; i < len; i += 32) w = fma(v[i], c[i], w);
+            w = warp_sum(w) * beta;
+            for (int i = lane; i < len; i += 32) c[i] = fma(-w, v[i], c[i]);
+            __syncwarp();
+            const double r = c[0];
+            const double n1 = vn1[q];
+            if (n1 != 0.0) {
+                double tmp = fabs(r) / n1;
+                tmp = fmax(0.0, (1.0 + tmp) * (1.0 - tmp));
+                const double ratio = n1 / vn2[q];
+                if (tmp * ratio * ratio <= 1.4901161193847656e-08) {
+                    double s2 = 0.0;
+                    for (int i = 1 + lane; i < len; i += 32) s2 = fma(c[i], c[i], s2);
+                    s2 = warp_sum(s2);
+                    if (lane == 0) { vn1[q] = sqrt(s2); vn2[q] = sqrt(s2); }
+                } else if (lane == 0) {
+                    vn1[q] = n1 * sqrt(tmp);
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    if (!alive) return;
+    // R[:, pos] = first pos+1 entries of the retired column
+    for (int q = 0; q < nc; ++q) {
+        const int pos = posq[q];
+        const double* c = cols + (size_t)q * l;
+        for (int i = t; i < m; i += PQ_THREADS) p.R[(int64_t)i * m + pos] = i <= pos ? c[i] : 0.0;
+    }
+}
+
 }  // namespace
 
-cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
+cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
                        double* work, int* status, cudaStream_t s) {
     (void)status;
     double* vn1 = work;
@@ -177,6 +386,52 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
     qr_extract_r_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(S, m, lds, R);
     note_launch();
     return cudaGetLastError();
+}
+
+size_t pivoted_qr_work_doubles(int m, int l) { return (size_t)3 * m + 3 * (size_t)l + 2048; }
+
+cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
+                       double* work, int* status, cudaStream_t s) {
+    // Persistent cooperative form when the columns fit in shared memory.
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (coop && sms > 0) {
+        int cpc = (m + sms - 1) / sms;
+        const size_t smem = ((size_t)cpc * l + l) * sizeof(double);
+        if (cpc <= PQ_MAXC && smem + 4096 <= (size_t)smem_optin) {
+            const int G = (m + cpc - 1) / cpc;
+            cudaFuncSetAttribute(qr_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            int per_sm = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_persistent_kernel, PQ_THREADS, smem);
+            if (per_sm >= 1 && G <= per_sm * sms) {
+                PqrDev p;
+                p.S = S; p.m = m; p.l = l; p.lds = lds; p.R = R; p.perm = perm; p.cpc = cpc;
+                double* w = work;
+                p.vbuf = w;                     w += 2 * (size_t)l;
+                p.scal = w;                     w += 4;
+                p.bval = w;                     w += 2 * (size_t)G;
+                p.bidx = (int*)w;               w += G;          // 2G ints
+                unsigned int* ctr = (unsigned int*)w;            // counter, abort, flags[m]
+                p.counter = ctr;
+                p.abort_flag = (int*)(ctr + 1);
+                p.flags = ctr + 2;
+                p.status = status;
+                p.timeout = 4000000000ll;
+                cudaError_t e = cudaMemsetAsync(ctr, 0, (size_t)(m + 2) * sizeof(unsigned int), s);
+                if (e != cudaSuccess) return e;
+                void* args[] = {&p};
+                e = cudaLaunchCooperativeKernel((const void*)qr_persistent_kernel, dim3(G), dim3(PQ_THREADS), args,
+                                                smem, s);
+                note_launch();
+                if (e == cudaSuccess) return cudaGetLastError();
+                cudaGetLastError();   // clear and fall back
+            }
+        }
+    }
+    return pivoted_qr_steps(S, m, l, lds, R, perm, work, status, s);
 }
 
 }  // namespace rtp

@@ -84,7 +84,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtp
     auto take = [&](size_t bytes) { const size_t at = off; off = align_up(off + bytes); return at; };
     L.status = take(64);
     L.S = take((size_t)m * l_max * 8);
-    L.qr_work = take((size_t)(3 * m + l_max + 8) * 8);
+    L.qr_work = take(pivoted_qr_work_doubles((int)m, (int)l_max) * 8);
     L.perm = take((size_t)m * 4);
     L.R = take((size_t)m * m * 8);
     L.RinvT = take((size_t)m * m * 8);

@@ -90,9 +90,14 @@ cudaError_t zero_upper(double* X, int m, cudaStream_t s);
 
 // Pivoted QR of S^* (k_qr.cu). S is m x l row-major (row i of S = column i of S^*),
 // overwritten. On exit R (m x m, upper) and perm (m) hold the factorization
-// S^*[:, perm] = Q R. work: 3*m + l doubles.
+// S^*[:, perm] = Q R. work: pivoted_qr_work_doubles(m, l) doubles. pivoted_qr uses the
+// persistent cooperative kernel when the columns fit in shared memory, else one pivot
+// kernel and one update kernel per step (pivoted_qr_steps).
+size_t pivoted_qr_work_doubles(int m, int l);
 cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
                        double* work, int* status, cudaStream_t s);
+cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
+                             double* work, int* status, cudaStream_t s);
 
 // Triangular solves and Cholesky (k_tri.cu).
 // Solves op(T) X = Bm in place; T (m x m) element (i,j) at T[i*t_rs + j*t_cs];
