@@ -218,23 +218,62 @@ def Zbuf_of(P, Bt):
     return _ZBUF[key]
 
 
-def roofline_entry(mode, phase_ms, phase_cnt, w, pk, opts):
-    """Dominant phase -> achieved vs peak (algorithmic work per launch / mean duration)."""
+def digit_pairs(sa, sb, terms):
+    """Digit pairs (p, q) with p < sa, q < sb, p + q < terms multiplied by the sliced GEMM."""
+    return sum(1 for p in range(sa) for q in range(sb) if p + q < terms)
+
+
+def phase_work(mode, w, o):
+    """Algorithmic work per step of each timed phase: (flops, unit, bound, kernel).
+
+    float64 form: float64 flops of each product. Mixed form: bf16 tensor flops of the
+    digit-pair products the Ozaki scheme performs (2 M N K per pair), since that is the
+    work the tensor pipe must do; QR and factor phases stay float64 (FP64 pipe)."""
     m, n, l, k = w.m, w.n, w.l, w.k
+    qr = 2.0 * l * m * m - 2.0 * m ** 3 / 3.0
     if mode == "fp64":
-        work = {
-            "sketch": 2.0 * m * n * l,
-            "gram": 2.0 * m * m * n + 2.0 * m * m * n,
-            "apply_a": 2.0 * m * n * k,
-            "apply_at": 2.0 * m * n * k,
+        return {
+            "sketch": (2.0 * m * n * l, "alu", "gemm64_kernel"),
+            "gram": (2.0 * m * m * n + m * m * n, "alu", "gemm64_kernel"),
+            "apply_a": (2.0 * m * n * k, "alu", "gemm64_kernel"),
+            "apply_at": (2.0 * m * n * k, "alu", "gemm64_kernel"),
+            "qr": (qr, "alu", "qr_persistent_kernel"),
         }
-        dom = max(work, key=lambda p: phase_ms.get(p, 0.0))
-        per_launch_ms = phase_ms[dom] / max(1, phase_cnt[dom])
-        achieved = work[dom] / (per_launch_ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": f"gemm64_kernel ({dom})", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)"}
-    return None
+    sk, g1, g2, ap, rs = o.sketch_slices, o.gram_slices, o.gram2_slices, o.apply_slices, o.resid_slices
+    passes = o.refine_passes
+    return {
+        "sketch": (2.0 * m * n * l * digit_pairs(1, sk, sk), "tensor", "sliced_gemm2_kernel"),
+        "gram": (2.0 * m * m * n * digit_pairs(g1, g1, g1) + 2.0 * m * m * n * digit_pairs(g2, g2, g2) * 0.5,
+                 "tensor", "sliced_gemm2_kernel"),
+        "apply_a": (2.0 * m * n * k * (digit_pairs(ap, ap, ap) + passes * digit_pairs(rs, rs, rs)), "tensor",
+                    "sliced_gemm2_kernel"),
+        "apply_at": (2.0 * m * n * k * (digit_pairs(rs, rs, rs) + passes * digit_pairs(ap, ap, ap)), "tensor",
+                     "sliced_gemm2_kernel"),
+        "qr": (qr, "alu", "qr_persistent_kernel"),
+    }
+
+
+def roofline_entry(mode, phase_ms, phase_cnt, steps, w, pk, opts):
+    """Per-phase achieved rate against its peak, and the entry for the dominant phase."""
+    work = phase_work(mode, w, opts)
+    tensor_peak = float(pk.get("bf16_tflops_sustained") or pk["bf16_tflops"])
+    phases = {}
+    for ph, (flops, bound, kernel) in work.items():
+        ms = phase_ms.get(ph, 0.0)
+        if ms <= 0:
+            continue
+        achieved = flops * steps / (ms * 1e-3) / 1e12
+        peak = tensor_peak if bound == "tensor" else FP64_PEAK_TFLOPS
+        phases[ph] = {"bound": bound, "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                      "frac": achieved / peak, "ms_per_step": ms / steps}
+    dom = max(phases, key=lambda p: phases[p]["ms_per_step"])
+    e = dict(phases[dom])
+    e.pop("ms_per_step")
+    e["phase"] = dom
+    e["traffic"] = None
+    e["peak_source"] = (f"{pk['_source']} bf16_tflops_sustained" if e["bound"] == "tensor"
+                        else "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)")
+    return e, phases
 
 
 def run_ours(args, w, world, rank, local):
@@ -297,9 +336,9 @@ def run_ours(args, w, world, rank, local):
         "clocks": clocks,
         "gpu_launches": int(launches),
     }
-    rl = roofline_entry(args.mode, phase_ms, phase_cnt, w, pk, P.opts)
-    if rl is not None:
-        line["roofline"] = rl
+    rl, rl_phases = roofline_entry(args.mode, phase_ms, phase_cnt, args.steps, w, pk, P.opts)
+    line["roofline"] = rl
+    line["roofline_phases"] = rl_phases
 
     if not args.no_e2e:
         line["e2e"] = e2e(torch, rt, A, B, w, args, dev)
@@ -354,10 +393,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     w = workloads.WORKLOADS[args.workload]
+    if args.l is not None:
+        import dataclasses
+        w = dataclasses.replace(w, l=args.l)
     world, rank, local = setup_dist() if args.impl == "ours" else (
         int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")))
     if args.impl == "reference":

@@ -11,47 +11,85 @@
 namespace rtp {
 namespace {
 
-constexpr int TRSM_NB = 4;
+constexpr int TRSM_NB = 4;        // right-hand-side columns per CTA
 constexpr int TRSM_THREADS = 256;
+constexpr int TRSM_BS = 32;       // rows per diagonal block
 
-// Solves op(T) X = B for TRSM_NB columns of B per CTA, B held in shared memory.
-__global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int64_t t_rs, int64_t t_cs, int lower,
-                                                            int m, double* B, int64_t b_rs, int ncols, int* status) {
+// Solves op(T) X = B for TRSM_NB columns of B per CTA, in blocks of 32 rows: warp 0
+// solves the 32 x 32 diagonal block with register shuffles, then all threads subtract
+// that block's contribution from the rows still to be solved. Two barriers per block.
+template <bool lower>
+__global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int64_t t_rs, int64_t t_cs, int m,
+                                                            double* B, int64_t b_rs, int ncols, int* status) {
     extern __shared__ double x[];   // m * TRSM_NB
     const int j0 = blockIdx.x * TRSM_NB;
     const int nc = min(TRSM_NB, ncols - j0);
-    const int t = threadIdx.x;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
         const int i = e / TRSM_NB, jj = e % TRSM_NB;
         x[e] = jj < nc ? B[(int64_t)i * b_rs + j0 + jj] : 0.0;
     }
     __syncthreads();
-    for (int step = 0; step < m; ++step) {
-        const int i = lower ? step : m - 1 - step;
-        if (t < TRSM_NB) {
-            double d = T[(int64_t)i * t_rs + (int64_t)i * t_cs];
-            if (!(d != 0.0) || !isfinite(d)) {
-                set_status(status, RTPROJ_ENONFINITE);
-                d = 1.0;
+    const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
+    for (int bi = 0; bi < nblk; ++bi) {
+        // block rows [r0, r0 + bs)
+        const int blk = lower ? bi : nblk - 1 - bi;
+        const int r0 = blk * TRSM_BS;
+        const int bs = min(TRSM_BS, m - r0);
+        if (warp == 0) {
+            // lane holds row r0 + lane of the block: its 4 right-hand-side values and its
+            // row of the diagonal block T(r0 + lane, r0 + 0..bs)
+            double xv[TRSM_NB];
+            double trow[TRSM_BS];
+            const bool in = lane < bs;
+#pragma unroll
+            for (int jj = 0; jj < TRSM_NB; ++jj) xv[jj] = in ? x[(r0 + lane) * TRSM_NB + jj] : 0.0;
+#pragma unroll
+            for (int k = 0; k < TRSM_BS; ++k)
+                trow[k] = (in && k < bs) ? T[(int64_t)(r0 + lane) * t_rs + (int64_t)(r0 + k) * t_cs] : 0.0;
+#pragma unroll
+            for (int step = 0; step < TRSM_BS; ++step) {
+                const int i = lower ? step : TRSM_BS - 1 - step;
+                if (i < bs) {
+                    if (lane == i) {
+                        double d = trow[i];
+                        if (!(d != 0.0) || !isfinite(d)) {
+                            set_status(status, RTPROJ_ENONFINITE);
+                            d = 1.0;
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < TRSM_NB; ++jj) xv[jj] /= d;
+                    }
+                    double xi[TRSM_NB];
+#pragma unroll
+                    for (int jj = 0; jj < TRSM_NB; ++jj) xi[jj] = __shfl_sync(0xffffffffu, xv[jj], i);
+                    const bool after = lower ? (lane > i) : (lane < i);
+                    if (after && in) {
+#pragma unroll
+                        for (int jj = 0; jj < TRSM_NB; ++jj) xv[jj] = fma(-trow[i], xi[jj], xv[jj]);
+                    }
+                }
             }
-            x[i * TRSM_NB + t] /= d;
+            if (in) {
+#pragma unroll
+                for (int jj = 0; jj < TRSM_NB; ++jj) x[(r0 + lane) * TRSM_NB + jj] = xv[jj];
+            }
         }
         __syncthreads();
-        double xi[TRSM_NB];
+        // rows not yet solved: below the block (lower) or above it (upper)
+        const int rbeg = lower ? r0 + bs : 0;
+        const int rend = lower ? m : r0;
+        for (int r = rbeg + t; r < rend; r += TRSM_THREADS) {
+            double acc[TRSM_NB];
 #pragma unroll
-        for (int jj = 0; jj < TRSM_NB; ++jj) xi[jj] = x[i * TRSM_NB + jj];
-        if (lower) {
-            for (int r = i + 1 + t; r < m; r += TRSM_THREADS) {
-                const double tv = T[(int64_t)r * t_rs + (int64_t)i * t_cs];
+            for (int jj = 0; jj < TRSM_NB; ++jj) acc[jj] = x[r * TRSM_NB + jj];
+            for (int k = 0; k < bs; ++k) {
+                const double tv = T[(int64_t)r * t_rs + (int64_t)(r0 + k) * t_cs];
 #pragma unroll
-                for (int jj = 0; jj < TRSM_NB; ++jj) x[r * TRSM_NB + jj] = fma(-tv, xi[jj], x[r * TRSM_NB + jj]);
+                for (int jj = 0; jj < TRSM_NB; ++jj) acc[jj] = fma(-tv, x[(r0 + k) * TRSM_NB + jj], acc[jj]);
             }
-        } else {
-            for (int r = t; r < i; r += TRSM_THREADS) {
-                const double tv = T[(int64_t)r * t_rs + (int64_t)i * t_cs];
 #pragma unroll
-                for (int jj = 0; jj < TRSM_NB; ++jj) x[r * TRSM_NB + jj] = fma(-tv, xi[jj], x[r * TRSM_NB + jj]);
-            }
+            for (int jj = 0; jj < TRSM_NB; ++jj) x[r * TRSM_NB + jj] = acc[jj];
         }
         __syncthreads();
     }
@@ -133,9 +171,16 @@ cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
     if (m <= 0 || ncols <= 0) return cudaSuccess;
     const size_t smem = (size_t)m * TRSM_NB * sizeof(double);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    trsm_kernel<<<(ncols + TRSM_NB - 1) / TRSM_NB, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, lower ? 1 : 0, m, Bm, b_rs,
-                                                                               ncols, status);
+    const unsigned grid = (unsigned)((ncols + TRSM_NB - 1) / TRSM_NB);
+    if (lower) {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(trsm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        trsm_kernel<true><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, status);
+    } else {
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(trsm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        trsm_kernel<false><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, status);
+    }
     note_launch();
     return cudaGetLastError();
 }

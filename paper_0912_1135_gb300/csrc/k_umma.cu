@@ -20,7 +20,11 @@
 // operands with cp.async into the SWIZZLE_128B K-major layout and read TMEM back.
 #include "rtproj_internal.cuh"
 
+#include <cuda.h>
+
 #include <algorithm>
+#include <cstdlib>
+#include <mutex>
 
 namespace rtp {
 namespace {
@@ -319,6 +323,297 @@ __global__ void sliced_reduce_kernel(SgReduceDev r) {
     r.C[row * r.c_rs + (int64_t)j * r.c_cs] = out;
 }
 
+
+// =====================================================================================
+// Pipelined form (sliced_gemm2_kernel): TMA loads, warp specialisation, windowed B.
+//
+// The digit planes of the B operand for one K block are loaded by a single 3-D TMA box
+// (64 k x 32 rows x sb planes) and lie back to back in shared memory, so that "B planes
+// q = 0..w-1" is one contiguous N = 32 w operand. One MMA per (A plane p, 16-k step)
+// then forms every pair (p, q), q < min(sb, terms - p), at once, writing level p + q to
+// TMEM columns (p + q) * 32: the D address is offset by p * 32 columns. The first MMA of
+// a 128-k chunk (p = 0) covers every level (terms <= sb is required), so it alone
+// carries accumulate = 0. Warp 0 issues the TMA loads into a ring of A-plane stages and
+// a ring of B-plane stages; warp 1 issues the MMAs and commits each stage back to its
+// producer; warps 2-5 read the level sums of each chunk from TMEM (double-buffered when
+// 2 * terms * 32 <= 512 columns) and fold them into int64 words exactly as the
+// synchronous form does. Every mbarrier wait is bounded; expiry raises RTPROJ_ETIMEOUT.
+// =====================================================================================
+constexpr int W_THREADS = 192;
+constexpr int W_MAX_A_STAGES = 16;
+constexpr int W_MAX_B_STAGES = 8;
+
+struct Sg2Dev {
+    int M, N, Kp, sa, sb, terms, k_per_split;
+    const int32_t* ea; const int32_t* eb;
+    long long* part;
+    double* C; int64_t c_rs, c_cs; const int32_t* crow;
+    double alpha, beta;
+    const double* Cin; int64_t cin_rs, cin_cs;
+    int lower_only;
+    int* status;
+    long long timeout;
+    uint32_t tmem_cols;
+    int acc_bufs, a_stages, b_stages;
+};
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait on an mbarrier phase; raises the CTA-wide abort flag on expiry.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int* abort_s, int* status,
+                                           long long timeout) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_s) return false;
+        if (clock64() - t0 > timeout) {
+            *abort_s = 1;
+            set_status(status, RTPROJ_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(W_THREADS, 1)
+    sliced_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Sg2Dev p) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int AS = p.a_stages;
+    const int BSN = p.b_stages;
+    const uint32_t b_stage_bytes = (uint32_t)p.sb * B_PLANE_BYTES;
+    unsigned char* sA = smem;
+    unsigned char* sB = sA + (size_t)AS * A_PLANE_BYTES;
+    uint64_t* bars = (uint64_t*)(sB + (size_t)BSN * b_stage_bytes);
+    uint64_t* fullA = bars;
+    uint64_t* emptyA = fullA + W_MAX_A_STAGES;
+    uint64_t* fullB = emptyA + W_MAX_A_STAGES;
+    uint64_t* emptyB = fullB + W_MAX_B_STAGES;
+    uint64_t* tfull = emptyB + W_MAX_B_STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+    __shared__ int abort_s;
+
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN, z = blockIdx.z;
+    if (p.lower_only && j0 > i0 + TM - 1) return;
+    const int kbeg = z * p.k_per_split;
+    const int kend = min(p.Kp, kbeg + p.k_per_split);
+    const int nkb = (kend - kbeg) / KB;
+    const int nchunks = (nkb + 1) / 2;
+    const uint32_t buf_cols = (uint32_t)(p.terms * TN);
+
+    if (t == 0) {
+        abort_s = 0;
+        for (int i = 0; i < AS; ++i) { mbar_init(fullA + i, 1); mbar_init(emptyA + i, 1); }
+        for (int i = 0; i < BSN; ++i) { mbar_init(fullB + i, 1); mbar_init(emptyB + i, 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(tfull + i, 1); mbar_init(tempty + i, 128); }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, p.tmem_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    volatile int* abort_v = &abort_s;
+
+    if (warp == 0) {
+        // ---------------- TMA producer
+        if (lane == 0) {
+            uint32_t a_it = 0, b_it = 0;
+            for (int kb = 0; kb < nkb && !*abort_v; ++kb) {
+                const int k0 = kbeg + kb * KB;
+                const int bs = b_it % BSN;
+                if (b_it >= (uint32_t)BSN &&
+                    !wait_phase(emptyB + bs, ((b_it / BSN) - 1) & 1, abort_v, p.status, p.timeout))
+                    break;
+                mbar_expect_tx(fullB + bs, b_stage_bytes);
+                tma_load_3d(smem_addr(sB + (size_t)bs * b_stage_bytes), &tmB, k0, j0, 0, fullB + bs);
+                ++b_it;
+                for (int pa = 0; pa < p.sa; ++pa) {
+                    const int as = a_it % AS;
+                    if (a_it >= (uint32_t)AS &&
+                        !wait_phase(emptyA + as, ((a_it / AS) - 1) & 1, abort_v, p.status, p.timeout))
+                        break;
+                    mbar_expect_tx(fullA + as, A_PLANE_BYTES);
+                    tma_load_3d(smem_addr(sA + (size_t)as * A_PLANE_BYTES), &tmA, k0, i0, pa, fullA + as);
+                    ++a_it;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer
+        if (lane == 0) {
+            uint32_t a_it = 0, b_it = 0;
+            int chunk = 0, buf = 0;
+            for (int kb = 0; kb < nkb && !*abort_v; ++kb) {
+                const bool chunk_start = (kb & 1) == 0;
+                if (chunk_start) {
+                    buf = chunk % p.acc_bufs;
+                    if (chunk >= p.acc_bufs &&
+                        !wait_phase(tempty + buf, ((chunk / p.acc_bufs) - 1) & 1, abort_v, p.status, p.timeout))
+                        break;
+                    tc_fence_after();
+                }
+                const int bs = b_it % BSN;
+                if (!wait_phase(fullB + bs, (b_it / BSN) & 1, abort_v, p.status, p.timeout)) break;
+                const uint32_t sB_addr = smem_addr(sB + (size_t)bs * b_stage_bytes);
+                bool ok = true;
+                for (int pa = 0; pa < p.sa; ++pa) {
+                    const int as = a_it % AS;
+                    if (!wait_phase(fullA + as, (a_it / AS) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sA_addr = smem_addr(sA + (size_t)as * A_PLANE_BYTES);
+                    const int nwin = min(p.sb, p.terms - pa);
+                    if (nwin > 0) {
+                        const uint32_t d0 = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * TN);
+#pragma unroll 1
+                        for (int kk = 0; kk < KB / 16; ++kk) {
+                            const uint64_t ad = sw128_desc(sA_addr + kk * 32);
+                            const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
+                            for (int w0 = 0; w0 < nwin; w0 += 8) {
+                                const int nw = min(8, nwin - w0);
+                                const uint64_t bd = sw128_desc(sB_addr + w0 * B_PLANE_BYTES + kk * 32);
+                                umma_bf16(d0 + (uint32_t)(w0 * TN), ad, bd, idesc_bf16(TM, nw * TN), acc);
+                            }
+                        }
+                    }
+                    umma_commit(emptyA + as);
+                    ++a_it;
+                }
+                if (!ok) break;
+                umma_commit(emptyB + bs);
+                ++b_it;
+                if ((kb & 1) == 1 || kb == nkb - 1) {
+                    umma_commit(tfull + buf);
+                    ++chunk;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5 read TMEM lanes 32 * (warp % 4) ...
+        const int quarter = warp & 3;
+        long long hi[TN], lo[TN];
+#pragma unroll
+        for (int j = 0; j < TN; ++j) { hi[j] = 0; lo[j] = 0; }
+        bool ok = true;
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c % p.acc_bufs;
+            if (!wait_phase(tfull + buf, (c / p.acc_bufs) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * buf_cols;
+            for (int g = 0; g < p.terms; ++g) {
+                uint32_t r[32];
+                tmem_ld32(base + (uint32_t)(g * TN), r);
+                tmem_ld_wait();
+                const long long mul = 1ll << (g <= 4 ? 8 * (4 - g) : 8 * (9 - g));
+                if (g <= 4) {
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) hi[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) lo[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const long long carry = lo[j] >> 40;
+                hi[j] += carry;
+                lo[j] -= carry * (1ll << 40);
+            }
+            tc_fence_before();
+            mbar_arrive(tempty + buf);
+        }
+        const int i = i0 + quarter * 32 + lane;
+        if (ok && !*abort_v && i < p.M) {
+            if (gridDim.z > 1) {
+                long long* dst = p.part + (((int64_t)z * p.M + i) * p.N + j0) * 2;
+#pragma unroll
+                for (int j = 0; j < TN; ++j)
+                    if (j0 + j < p.N) { dst[2 * j] = hi[j]; dst[2 * j + 1] = lo[j]; }
+            } else {
+                const int ea = p.ea ? p.ea[i] : 0;
+                const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
+#pragma unroll
+                for (int j = 0; j < TN; ++j) {
+                    const int gj = j0 + j;
+                    if (gj >= p.N || (p.lower_only && gj > i)) continue;
+                    const double v = ldexp(ldexp((double)hi[j], 40) + (double)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                    double out = p.alpha * v;
+                    if (p.beta != 0.0) out += p.beta * p.Cin[(int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs];
+                    p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = out;
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) tmem_dealloc(tmem, p.tmem_cols);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    });
+    return fn;
+}
+
+// 3-D map over a digit stack: (k, row, plane), box (64, box_rows, box_planes), 128-byte swizzle.
+bool make_stack_map(CUtensorMap* map, const SliceStack& st, int box_rows, int box_planes) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)st.ld, (cuuint64_t)st.rows, (cuuint64_t)st.s};
+    cuuint64_t strides[2] = {(cuuint64_t)st.ld * 2, (cuuint64_t)st.plane_stride * 2};
+    cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)box_rows, (cuuint32_t)box_planes};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)st.d, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+void launch_reduce(const SlicedGemm& g, int splits, void* scratch, cudaStream_t s) {
+    SgReduceDev r;
+    r.part = (const long long*)scratch; r.splits = splits; r.M = g.a.rows; r.N = g.b.rows;
+    r.ea = g.a.e; r.eb = g.b.e;
+    r.C = g.C; r.c_rs = g.c_rs; r.c_cs = g.c_cs; r.crow = g.crow;
+    r.alpha = g.alpha; r.beta = g.beta; r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
+    r.lower_only = g.lower_only ? 1 : 0;
+    const int64_t total = (int64_t)r.M * r.N;
+    sliced_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
+    note_launch();
+}
+
+bool pipelined_disabled() {
+    const char* e = std::getenv("RTPROJ_SYNC_GEMM");
+    return e && e[0] == '1';
+}
+
 }  // namespace
 
 size_t sliced_gemm_scratch_bytes(int M, int N, int K) {
@@ -330,7 +625,7 @@ size_t sliced_gemm_scratch_bytes(int M, int N, int K) {
     return splits * (size_t)M * N * 16;
 }
 
-cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
+static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
     const int M = g.a.rows, N = g.b.rows, K = g.a.cols;
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (g.a.s < 1 || g.a.s > MAXS || g.b.s < 1 || g.b.s > MAXS) return cudaErrorInvalidValue;
@@ -376,6 +671,79 @@ cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes
         sliced_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
         note_launch();
     }
+    return cudaGetLastError();
+}
+
+
+static int choose_splits(int M, int N, int Kp, size_t scratch_bytes, int* kps_out) {
+    const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+    int splits = 1;
+    const int max_splits = std::max(1, (Kp + KCHUNK - 1) / KCHUNK);
+    if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
+    while (splits > 1 && (size_t)splits * M * N * 16 > scratch_bytes) --splits;
+    int kps = (Kp + splits - 1) / splits;
+    kps = (kps + KCHUNK - 1) / KCHUNK * KCHUNK;
+    *kps_out = kps;
+    return (Kp + kps - 1) / kps;
+}
+
+cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
+    SlicedGemm g = g0;
+    // The pipelined kernel needs terms <= sb (the first MMA of a chunk covers every level).
+    // Put the operand with more digits on the B side: swap and write C transposed.
+    if (g.b.s < g.terms && g.a.s >= g.terms && !g.crow && !g.lower_only) {
+        std::swap(g.a, g.b);
+        std::swap(g.c_rs, g.c_cs);
+        std::swap(g.cin_rs, g.cin_cs);
+    }
+    const int M = g.a.rows, N = g.b.rows, K = g.a.cols;
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const bool shapes_ok = g.a.s >= 1 && g.a.s <= MAXS && g.b.s >= 1 && g.b.s <= MAXS && g.terms >= 1 &&
+                           g.terms <= 10 && g.terms <= g.b.s && g.b.cols == K && g.a.ld % 64 == 0 &&
+                           g.b.ld % 64 == 0 && g.a.ld >= K && g.b.ld >= K;
+    if (!shapes_ok || pipelined_disabled()) return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
+    CUtensorMap mapA, mapB;
+    if (!make_stack_map(&mapA, g.a, TM, 1) || !make_stack_map(&mapB, g.b, TN, g.b.s))
+        return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
+    const int Kp = (K + KB - 1) / KB * KB;
+    int kps = 0;
+    const int splits = choose_splits(M, N, Kp, scratch_bytes, &kps);
+    Sg2Dev p;
+    p.M = M; p.N = N; p.Kp = Kp; p.sa = g.a.s; p.sb = g.b.s; p.terms = g.terms; p.k_per_split = kps;
+    p.ea = g.a.e; p.eb = g.b.e;
+    p.part = (long long*)scratch;
+    p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
+    p.alpha = g.alpha; p.beta = g.beta; p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
+    p.lower_only = g.lower_only ? 1 : 0;
+    p.status = status;
+    p.timeout = 4000000000ll;
+    p.acc_bufs = (2 * g.terms * TN <= 512) ? 2 : 1;
+    p.tmem_cols = 32;
+    while (p.tmem_cols < (uint32_t)(p.acc_bufs * g.terms * TN)) p.tmem_cols <<= 1;
+    // Split shared memory between the A-plane ring (sa slots per K block) and the B-stage
+    // ring (one stage per K block) so that the producer can run as many K blocks ahead as
+    // possible: maximise min(b_stages, a_stages / sa).
+    const size_t b_stage = (size_t)g.b.s * B_PLANE_BYTES;
+    const size_t fixed = 1024 + (2 * W_MAX_A_STAGES + 2 * W_MAX_B_STAGES + 4) * 8 + 16;
+    const size_t budget = 220 * 1024 - fixed;
+    int best_bs = 0, best_as = 0;
+    double best_depth = -1.0;
+    for (int bsn = 2; bsn <= W_MAX_B_STAGES; ++bsn) {
+        if ((size_t)bsn * b_stage + 2 * A_PLANE_BYTES > budget) break;
+        const int asn = (int)std::min<size_t>(W_MAX_A_STAGES, (budget - (size_t)bsn * b_stage) / A_PLANE_BYTES);
+        const double depth = std::min<double>(bsn, (double)asn / g.a.s);
+        if (depth > best_depth + 1e-9) { best_depth = depth; best_bs = bsn; best_as = asn; }
+    }
+    if (best_as < 2 || best_bs < 2) return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
+    p.a_stages = best_as;
+    p.b_stages = best_bs;
+    const size_t smem = fixed + (size_t)best_bs * b_stage + (size_t)best_as * A_PLANE_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(sliced_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
+    sliced_gemm2_kernel<<<grid, W_THREADS, smem, s>>>(mapA, mapB, p);
+    note_launch();
+    if (splits > 1) launch_reduce(g, splits, scratch, s);
     return cudaGetLastError();
 }
 

@@ -139,3 +139,24 @@ def test_full_size_dense_sampled():
     assert metrics.max_rel_err(Z[:1], Zx) < Z_TOL
     assert metrics.max_rel_err(ZZ, Z) < Z_TOL
     assert metrics.normalised_residual(A, Z, B, normA=1.0) < RESID_TOL
+
+
+@pytest.mark.parametrize("m,n,l,k", [(64, 2048, 256, 16), (37, 1000, 41, 3)])
+def test_pipelined_and_synchronous_sliced_gemm_agree_bitwise(m, n, l, k, monkeypatch):
+    """Both tensor-core kernels form exact level sums, so their results are identical bit
+    for bit: the TMA-pipelined kernel (default) against the synchronous cp.async one
+    (RTPROJ_SYNC_GEMM=1)."""
+    torch = torch_cuda()
+    rt = rt_module()
+    A = workloads.haar_spectrum_matrix(m, n, 1e-9, 70)
+    B = workloads.rhs(k, n, 71)
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("RTPROJ_SYNC_GEMM", flag)
+        with _mixed(rt, torch, A, l, k) as P:
+            S = P.sketch(seed=5, l=l).cpu().numpy()
+            P.precondition(seed=5, l=l)
+            Z, ROW, H = P.project(to_dev(torch, B), null=True, row=True, lstsq=True)
+            out[flag] = (S, Z.cpu().numpy(), ROW.cpu().numpy(), H.cpu().numpy())
+    for a, b in zip(out["0"], out["1"]):
+        np.testing.assert_array_equal(a, b)
