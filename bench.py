@@ -127,14 +127,21 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """Largest value of x over the ranks (the slowest replica sets the job time)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(world: int, k: int, steps: int, ms_max: float) -> float:
+    """Whole-job projections/s: every rank projects k right-hand sides per step on its own
+    replica, and the job takes as long as the slowest rank."""
+    return world * k * steps / (ms_max * 1e-3)
 
 
 def cpu_oracle_step(A, B):
@@ -308,7 +315,7 @@ def run_ours(args, w, world, rank, local):
     launches = rt.launch_count() - launches0
     tim = P.timings()
     ms_max = max_over_ranks(ms, world)
-    value = world * w.k * args.steps / (ms_max * 1e-3)
+    value = job_throughput(world, w.k, args.steps, ms_max)
     phase_ms = {p: v[0] for p, v in tim.items()}
     phase_cnt = {p: v[1] for p, v in tim.items()}
 

@@ -21,6 +21,7 @@ struct Gemm64Dev {
     int omega_dist; uint32_t key0, key1;
     double* P;                     // partial slabs (split > 1)
     int lower_only;
+    int a_tri;
     // direct epilogue (one split)
     double* C; int64_t c_rs, c_cs; const int32_t* crow;
     double alpha, beta;
@@ -43,7 +44,11 @@ __global__ void __launch_bounds__(NT) gemm64_kernel(Gemm64Dev p) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
 
-    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    // triangular A: only k <= i (lower) or k >= i (upper) can be nonzero for this tile's rows
+    int klo = kbeg, khi = kend;
+    if (p.a_tri == 1) khi = min(khi, i0 + BM);
+    if (p.a_tri == 2) klo = max(klo, (i0 / BK) * BK);
+    for (int k0 = klo; k0 < khi; k0 += BK) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
             const int e = t + NT * r;
@@ -184,7 +189,7 @@ cudaError_t gemm64(const Gemm64& g, double* part, size_t part_elems, cudaStream_
     if (g.K > 0) {
         const int tiles = tiles_m * tiles_n;
         const int want = std::max(1, (4 * 152 + tiles - 1) / tiles);
-        const int maxk = std::max(1, (g.K + 255) / 256);
+        const int maxk = std::max(1, (g.K + 63) / 64);   // at least four 16-k steps per split
         splits = std::min(want, maxk);
         splits = (int)std::min<size_t>((size_t)splits, std::max<size_t>(1, part_elems / slab));
     }
@@ -200,6 +205,7 @@ cudaError_t gemm64(const Gemm64& g, double* part, size_t part_elems, cudaStream_
     p.key0 = (uint32_t)(g.seed & 0xFFFFFFFFull); p.key1 = (uint32_t)(g.seed >> 32);
     p.P = part;
     p.lower_only = g.lower_only ? 1 : 0;
+    p.a_tri = g.a_tri;
     p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
     p.alpha = g.alpha; p.beta = g.beta; p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
     if (g.K <= 0) return cudaErrorInvalidValue;

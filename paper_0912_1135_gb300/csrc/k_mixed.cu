@@ -179,6 +179,7 @@ rtproj_status mixed_prepare_a(rtproj_ctx* h) {
 
 rtproj_status mixed_sketch(rtproj_ctx* h, uint64_t seed, int64_t l, double* S, int64_t lds) {
     SliceStack G = rows_of(h->Gs, (int)l, 1);
+    G.max_digit = h->opts.omega == RTPROJ_OMEGA_RADEMACHER ? 1 : 255;
     MX_CHECK(omega_plane(seed, h->opts.omega, (int)h->n, (int)l, G, h->stream));
     return gemm(h, first(h->As, h->opts.sketch_slices), G, h->opts.sketch_slices, S, lds, 1);
 }

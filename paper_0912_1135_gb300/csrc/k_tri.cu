@@ -83,10 +83,26 @@ __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int
             double acc[TRSM_NB];
 #pragma unroll
             for (int jj = 0; jj < TRSM_NB; ++jj) acc[jj] = x[r * TRSM_NB + jj];
-            for (int k = 0; k < bs; ++k) {
-                const double tv = T[(int64_t)r * t_rs + (int64_t)(r0 + k) * t_cs];
+            const double* trow = T + (int64_t)r * t_rs + (int64_t)r0 * t_cs;
+            if (bs == TRSM_BS) {
+                // full block: issue the 32 loads of T's row segment before the FMAs
 #pragma unroll
-                for (int jj = 0; jj < TRSM_NB; ++jj) acc[jj] = fma(-tv, x[(r0 + k) * TRSM_NB + jj], acc[jj]);
+                for (int k0 = 0; k0 < TRSM_BS; k0 += 8) {
+                    double tv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) tv[q] = trow[(int64_t)(k0 + q) * t_cs];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+#pragma unroll
+                        for (int jj = 0; jj < TRSM_NB; ++jj)
+                            acc[jj] = fma(-tv[q], x[(r0 + k0 + q) * TRSM_NB + jj], acc[jj]);
+                }
+            } else {
+                for (int k = 0; k < bs; ++k) {
+                    const double tv = trow[(int64_t)k * t_cs];
+#pragma unroll
+                    for (int jj = 0; jj < TRSM_NB; ++jj) acc[jj] = fma(-tv, x[(r0 + k) * TRSM_NB + jj], acc[jj]);
+                }
             }
 #pragma unroll
             for (int jj = 0; jj < TRSM_NB; ++jj) x[r * TRSM_NB + jj] = acc[jj];

@@ -32,7 +32,6 @@ namespace {
 constexpr int TM = 128;
 constexpr int TN = 32;
 constexpr int KB = 64;
-constexpr int KCHUNK = 128;
 constexpr int NTHREADS = 128;
 constexpr int MAXS = 10;
 constexpr int A_PLANE_BYTES = TM * KB * 2;   // 16 KiB
@@ -43,7 +42,8 @@ struct SgDev {
     const __nv_bfloat16* b; int64_t b_ld, b_ps; const int32_t* eb; int sb; int N;
     int Kp;             // K rounded up to 64 (planes are zero padded to it)
     int terms;
-    int k_per_split;    // multiple of KCHUNK
+    int k_per_split;    // multiple of kchunk
+    int kchunk;         // K between TMEM readouts (128, 256 or 512: see chunk_for)
     long long* part;    // [split][M][N][2] when gridDim.z > 1
     double* C; int64_t c_rs, c_cs; const int32_t* crow;
     double alpha, beta;
@@ -122,6 +122,33 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Exact int32 value of an integer-valued float32 with |x| < 2^30, on the FMA/ALU pipes
+// (64-bit float-to-integer conversion would run on GB300's small FP64 pipe). x is split
+// into hi, a multiple of 256 (rounded by adding 1.5 * 2^31, whose ulp is 256), and the
+// exact remainder lo, |lo| <= 128; both are read off the bits of a float offset by
+// 1.5 * 2^23, which holds integers below 2^22 exactly in its mantissa.
+__device__ __forceinline__ int exact_f2i(float x) {
+    const float big = 3221225472.0f;               // 1.5 * 2^31
+    const float hi = __fsub_rn(__fadd_rn(x, big), big);
+    const float lo = __fsub_rn(x, hi);
+    const int ih = __float_as_int(__fadd_rn(__fmul_rn(hi, 0.00390625f), 12582912.0f)) - 0x4B400000;
+    const int il = __float_as_int(__fadd_rn(lo, 12582912.0f)) - 0x4B400000;
+    return ih * 256 + il;
+}
+
+// Adds the level-g sums of one 128-row x 32-column readout (r) into the int64 words.
+__device__ __forceinline__ void fold_level(int g, const uint32_t (&r)[32], long long (&hi)[32], long long (&lo)[32]) {
+    if (g <= 4) {
+        const int sh = 8 * (4 - g);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) hi[j] += (long long)exact_f2i(__uint_as_float(r[j])) << sh;
+    } else {
+        const int sh = 8 * (9 - g);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) lo[j] += (long long)exact_f2i(__uint_as_float(r[j])) << sh;
+    }
+}
 
 // Shared-memory matrix descriptor: K-major, SWIZZLE_128B (8-row atoms of 1024 bytes).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
@@ -236,21 +263,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gemm_kernel(SgDev p) {
         if (timed_out) break;
         kin_chunk += KB;
         // ---- fold the exact level sums into hi/lo every 128 K (and at the end)
-        if (kin_chunk >= KCHUNK || k0 + KB >= kend) {
+        if (kin_chunk >= p.kchunk || k0 + KB >= kend) {
             const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
             for (int g = 0; g < p.terms; ++g) {
                 uint32_t r[32];
                 tmem_ld32(lane_base + (uint32_t)(g * TN), r);
                 tmem_ld_wait();
-                const int shift = g <= 4 ? 8 * (4 - g) : 8 * (9 - g);
-                const long long mul = 1ll << shift;
-                if (g <= 4) {
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) hi[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) lo[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
-                }
+                fold_level(g, r, hi, lo);
             }
 #pragma unroll
             for (int j = 0; j < TN; ++j) {          // keep |lo| < 2^40
@@ -344,7 +363,7 @@ constexpr int W_MAX_A_STAGES = 16;
 constexpr int W_MAX_B_STAGES = 8;
 
 struct Sg2Dev {
-    int M, N, Kp, sa, sb, terms, k_per_split;
+    int M, N, Kp, sa, sb, terms, k_per_split, chunk_kb, splits;
     const int32_t* ea; const int32_t* eb;
     long long* part;
     double* C; int64_t c_rs, c_cs; const int32_t* crow;
@@ -387,6 +406,18 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
     return true;
 }
 
+// Tile t of the persistent loop -> (x = B-row tile, y = A-row tile, z = K split).
+struct TileCoord { int i0, j0, z; };
+__device__ __forceinline__ TileCoord tile_of(int t, int tiles_n, int tiles_m) {
+    TileCoord c;
+    const int per_z = tiles_n * tiles_m;
+    c.z = t / per_z;
+    const int r = t - c.z * per_z;
+    c.i0 = (r / tiles_n) * TM;
+    c.j0 = (r % tiles_n) * TN;
+    return c;
+}
+
 __global__ void __launch_bounds__(W_THREADS, 1)
     sliced_gemm2_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Sg2Dev p) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -407,12 +438,9 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     __shared__ int abort_s;
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN, z = blockIdx.z;
-    if (p.lower_only && j0 > i0 + TM - 1) return;
-    const int kbeg = z * p.k_per_split;
-    const int kend = min(p.Kp, kbeg + p.k_per_split);
-    const int nkb = (kend - kbeg) / KB;
-    const int nchunks = (nkb + 1) / 2;
+    const int tiles_n = (p.N + TN - 1) / TN, tiles_m = (p.M + TM - 1) / TM;
+    const int ntiles = tiles_n * tiles_m * p.splits;
+    const int cb = p.chunk_kb;
     const uint32_t buf_cols = (uint32_t)(p.terms * TN);
 
     if (t == 0) {
@@ -432,27 +460,35 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
     volatile int* abort_v = &abort_s;
 
+    // Every role walks the same tile sequence (blockIdx.x, + gridDim.x, ...), skipping the
+    // tiles strictly above the diagonal when only the lower triangle is wanted.
     if (warp == 0) {
         // ---------------- TMA producer
         if (lane == 0) {
             uint32_t a_it = 0, b_it = 0;
-            for (int kb = 0; kb < nkb && !*abort_v; ++kb) {
-                const int k0 = kbeg + kb * KB;
-                const int bs = b_it % BSN;
-                if (b_it >= (uint32_t)BSN &&
-                    !wait_phase(emptyB + bs, ((b_it / BSN) - 1) & 1, abort_v, p.status, p.timeout))
-                    break;
-                mbar_expect_tx(fullB + bs, b_stage_bytes);
-                tma_load_3d(smem_addr(sB + (size_t)bs * b_stage_bytes), &tmB, k0, j0, 0, fullB + bs);
-                ++b_it;
-                for (int pa = 0; pa < p.sa; ++pa) {
-                    const int as = a_it % AS;
-                    if (a_it >= (uint32_t)AS &&
-                        !wait_phase(emptyA + as, ((a_it / AS) - 1) & 1, abort_v, p.status, p.timeout))
+            for (int tile = blockIdx.x; tile < ntiles && !*abort_v; tile += gridDim.x) {
+                const TileCoord c = tile_of(tile, tiles_n, tiles_m);
+                if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+                const int kbeg = c.z * p.k_per_split;
+                const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
+                for (int kb = 0; kb < nkb && !*abort_v; ++kb) {
+                    const int k0 = kbeg + kb * KB;
+                    const int bs = b_it % BSN;
+                    if (b_it >= (uint32_t)BSN &&
+                        !wait_phase(emptyB + bs, ((b_it / BSN) - 1) & 1, abort_v, p.status, p.timeout))
                         break;
-                    mbar_expect_tx(fullA + as, A_PLANE_BYTES);
-                    tma_load_3d(smem_addr(sA + (size_t)as * A_PLANE_BYTES), &tmA, k0, i0, pa, fullA + as);
-                    ++a_it;
+                    mbar_expect_tx(fullB + bs, b_stage_bytes);
+                    tma_load_3d(smem_addr(sB + (size_t)bs * b_stage_bytes), &tmB, k0, c.j0, 0, fullB + bs);
+                    ++b_it;
+                    for (int pa = 0; pa < p.sa; ++pa) {
+                        const int as = a_it % AS;
+                        if (a_it >= (uint32_t)AS &&
+                            !wait_phase(emptyA + as, ((a_it / AS) - 1) & 1, abort_v, p.status, p.timeout))
+                            break;
+                        mbar_expect_tx(fullA + as, A_PLANE_BYTES);
+                        tma_load_3d(smem_addr(sA + (size_t)as * A_PLANE_BYTES), &tmA, k0, c.i0, pa, fullA + as);
+                        ++a_it;
+                    }
                 }
             }
         }
@@ -461,102 +497,124 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         if (lane == 0) {
             uint32_t a_it = 0, b_it = 0;
             int chunk = 0, buf = 0;
-            for (int kb = 0; kb < nkb && !*abort_v; ++kb) {
-                const bool chunk_start = (kb & 1) == 0;
-                if (chunk_start) {
-                    buf = chunk % p.acc_bufs;
-                    if (chunk >= p.acc_bufs &&
-                        !wait_phase(tempty + buf, ((chunk / p.acc_bufs) - 1) & 1, abort_v, p.status, p.timeout))
-                        break;
-                    tc_fence_after();
-                }
-                const int bs = b_it % BSN;
-                if (!wait_phase(fullB + bs, (b_it / BSN) & 1, abort_v, p.status, p.timeout)) break;
-                const uint32_t sB_addr = smem_addr(sB + (size_t)bs * b_stage_bytes);
-                bool ok = true;
-                for (int pa = 0; pa < p.sa; ++pa) {
-                    const int as = a_it % AS;
-                    if (!wait_phase(fullA + as, (a_it / AS) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t sA_addr = smem_addr(sA + (size_t)as * A_PLANE_BYTES);
-                    const int nwin = min(p.sb, p.terms - pa);
-                    if (nwin > 0) {
-                        const uint32_t d0 = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * TN);
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok && !*abort_v; tile += gridDim.x) {
+                const TileCoord c = tile_of(tile, tiles_n, tiles_m);
+                if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+                const int kbeg = c.z * p.k_per_split;
+                const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
+                for (int kb = 0; kb < nkb && ok; ++kb) {
+                    const bool chunk_start = (kb % cb) == 0;
+                    if (chunk_start) {
+                        buf = chunk % p.acc_bufs;
+                        if (chunk >= p.acc_bufs &&
+                            !wait_phase(tempty + buf, ((chunk / p.acc_bufs) - 1) & 1, abort_v, p.status, p.timeout)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    const int bs = b_it % BSN;
+                    if (!wait_phase(fullB + bs, (b_it / BSN) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
+                    const uint32_t sB_addr = smem_addr(sB + (size_t)bs * b_stage_bytes);
+                    for (int pa = 0; pa < p.sa; ++pa) {
+                        const int as = a_it % AS;
+                        if (!wait_phase(fullA + as, (a_it / AS) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t sA_addr = smem_addr(sA + (size_t)as * A_PLANE_BYTES);
+                        const int nwin = min(p.sb, p.terms - pa);
+                        if (nwin > 0) {
+                            const uint32_t d0 = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * TN);
 #pragma unroll 1
-                        for (int kk = 0; kk < KB / 16; ++kk) {
-                            const uint64_t ad = sw128_desc(sA_addr + kk * 32);
-                            const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
-                            for (int w0 = 0; w0 < nwin; w0 += 8) {
-                                const int nw = min(8, nwin - w0);
-                                const uint64_t bd = sw128_desc(sB_addr + w0 * B_PLANE_BYTES + kk * 32);
-                                umma_bf16(d0 + (uint32_t)(w0 * TN), ad, bd, idesc_bf16(TM, nw * TN), acc);
+                            for (int kk = 0; kk < KB / 16; ++kk) {
+                                const uint64_t ad = sw128_desc(sA_addr + kk * 32);
+                                const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
+                                for (int w0 = 0; w0 < nwin; w0 += 8) {
+                                    const int nw = min(8, nwin - w0);
+                                    const uint64_t bd = sw128_desc(sB_addr + w0 * B_PLANE_BYTES + kk * 32);
+                                    umma_bf16(d0 + (uint32_t)(w0 * TN), ad, bd, idesc_bf16(TM, nw * TN), acc);
+                                }
                             }
                         }
+                        umma_commit(emptyA + as);
+                        ++a_it;
                     }
-                    umma_commit(emptyA + as);
-                    ++a_it;
-                }
-                if (!ok) break;
-                umma_commit(emptyB + bs);
-                ++b_it;
-                if ((kb & 1) == 1 || kb == nkb - 1) {
-                    umma_commit(tfull + buf);
-                    ++chunk;
+                    if (!ok) break;
+                    umma_commit(emptyB + bs);
+                    ++b_it;
+                    if ((kb % cb) == cb - 1 || kb == nkb - 1) {
+                        umma_commit(tfull + buf);
+                        ++chunk;
+                    }
                 }
             }
         }
     } else {
         // ---------------- epilogue: warps 2..5 read TMEM lanes 32 * (warp % 4) ...
         const int quarter = warp & 3;
-        long long hi[TN], lo[TN];
-#pragma unroll
-        for (int j = 0; j < TN; ++j) { hi[j] = 0; lo[j] = 0; }
+        int chunk = 0;
         bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c % p.acc_bufs;
-            if (!wait_phase(tfull + buf, (c / p.acc_bufs) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * buf_cols;
-            for (int g = 0; g < p.terms; ++g) {
-                uint32_t r[32];
-                tmem_ld32(base + (uint32_t)(g * TN), r);
-                tmem_ld_wait();
-                const long long mul = 1ll << (g <= 4 ? 8 * (4 - g) : 8 * (9 - g));
-                if (g <= 4) {
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const TileCoord c = tile_of(tile, tiles_n, tiles_m);
+            if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+            const int kbeg = c.z * p.k_per_split;
+            const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
+            const int nchunks = (nkb + cb - 1) / cb;
+            long long hi[TN], lo[TN];
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) hi[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
-                } else {
-#pragma unroll
-                    for (int j = 0; j < TN; ++j) lo[j] += (long long)__float2ll_rn(__uint_as_float(r[j])) * mul;
+            for (int j = 0; j < TN; ++j) { hi[j] = 0; lo[j] = 0; }
+            for (int cc = 0; cc < nchunks; ++cc, ++chunk) {
+                const int buf = chunk % p.acc_bufs;
+                if (!wait_phase(tfull + buf, (chunk / p.acc_bufs) & 1, abort_v, p.status, p.timeout)) {
+                    ok = false;
+                    break;
                 }
-            }
-#pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                const long long carry = lo[j] >> 40;
-                hi[j] += carry;
-                lo[j] -= carry * (1ll << 40);
-            }
-            tc_fence_before();
-            mbar_arrive(tempty + buf);
-        }
-        const int i = i0 + quarter * 32 + lane;
-        if (ok && !*abort_v && i < p.M) {
-            if (gridDim.z > 1) {
-                long long* dst = p.part + (((int64_t)z * p.M + i) * p.N + j0) * 2;
-#pragma unroll
-                for (int j = 0; j < TN; ++j)
-                    if (j0 + j < p.N) { dst[2 * j] = hi[j]; dst[2 * j + 1] = lo[j]; }
-            } else {
-                const int ea = p.ea ? p.ea[i] : 0;
-                const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
+                tc_fence_after();
+                const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * buf_cols;
+                uint32_t ra[32], rb[32];
+                tmem_ld32(base, ra);
+                tmem_ld_wait();
+                for (int g = 0; g < p.terms; g += 2) {
+                    // load level g + 1 while level g is folded
+                    if (g + 1 < p.terms) tmem_ld32(base + (uint32_t)((g + 1) * TN), rb);
+                    fold_level(g, ra, hi, lo);
+                    tmem_ld_wait();
+                    if (g + 1 < p.terms) {
+                        if (g + 2 < p.terms) tmem_ld32(base + (uint32_t)((g + 2) * TN), ra);
+                        fold_level(g + 1, rb, hi, lo);
+                        tmem_ld_wait();
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < TN; ++j) {
-                    const int gj = j0 + j;
-                    if (gj >= p.N || (p.lower_only && gj > i)) continue;
-                    const double v = ldexp(ldexp((double)hi[j], 40) + (double)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
-                    double out = p.alpha * v;
-                    if (p.beta != 0.0) out += p.beta * p.Cin[(int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs];
-                    p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = out;
+                    const long long carry = lo[j] >> 40;
+                    hi[j] += carry;
+                    lo[j] -= carry * (1ll << 40);
+                }
+                tc_fence_before();
+                mbar_arrive(tempty + buf);
+            }
+            if (!ok) break;
+            const int i = c.i0 + quarter * 32 + lane;
+            if (!*abort_v && i < p.M) {
+                if (p.splits > 1) {
+                    long long* dst = p.part + (((int64_t)c.z * p.M + i) * p.N + c.j0) * 2;
+#pragma unroll
+                    for (int j = 0; j < TN; ++j)
+                        if (c.j0 + j < p.N) { dst[2 * j] = hi[j]; dst[2 * j + 1] = lo[j]; }
+                } else {
+                    const int ea = p.ea ? p.ea[i] : 0;
+                    const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) {
+                        const int gj = c.j0 + j;
+                        if (gj >= p.N || (p.lower_only && gj > i)) continue;
+                        const double v =
+                            ldexp(ldexp((double)hi[j], 40) + (double)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                        double out = p.alpha * v;
+                        if (p.beta != 0.0) out += p.beta * p.Cin[(int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs];
+                        p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = out;
+                    }
                 }
             }
         }
@@ -625,6 +683,8 @@ size_t sliced_gemm_scratch_bytes(int M, int N, int K) {
     return splits * (size_t)M * N * 16;
 }
 
+static int chunk_for(const SlicedGemm& g);
+
 static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
     const int M = g.a.rows, N = g.b.rows, K = g.a.cols;
     if (M <= 0 || N <= 0) return cudaSuccess;
@@ -634,18 +694,19 @@ static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t s
     const int Kp = (K + KB - 1) / KB * KB;
     const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN;
     const int tiles = tiles_m * tiles_n;
+    const int kchunk = chunk_for(g);
     int splits = 1;
-    const int max_splits = std::max(1, (Kp + KCHUNK - 1) / KCHUNK);
+    const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
     if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
     while (splits > 1 && (size_t)splits * M * N * 16 > scratch_bytes) --splits;
     int kps = (Kp + splits - 1) / splits;
-    kps = (kps + KCHUNK - 1) / KCHUNK * KCHUNK;
+    kps = (kps + kchunk - 1) / kchunk * kchunk;
     splits = (Kp + kps - 1) / kps;
 
     SgDev p;
     p.a = g.a.d; p.a_ld = g.a.ld; p.a_ps = g.a.plane_stride; p.ea = g.a.e; p.sa = g.a.s; p.M = M;
     p.b = g.b.d; p.b_ld = g.b.ld; p.b_ps = g.b.plane_stride; p.eb = g.b.e; p.sb = g.b.s; p.N = N;
-    p.Kp = Kp; p.terms = g.terms; p.k_per_split = kps;
+    p.Kp = Kp; p.terms = g.terms; p.k_per_split = kps; p.kchunk = kchunk;
     p.part = (long long*)scratch;
     p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
     p.alpha = g.alpha; p.beta = g.beta; p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
@@ -675,14 +736,25 @@ static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t s
 }
 
 
-static int choose_splits(int M, int N, int Kp, size_t scratch_bytes, int* kps_out) {
+// Largest readout interval (128, 256 or 512 k) that keeps every level g <= 7 exact: each
+// level holds at most min(sa, sb, terms) digit pairs per k, each product at most
+// max_digit_a * max_digit_b, and a float32 sum is exact while it stays within 2^24.
+static int chunk_for(const SlicedGemm& g) {
+    const long long pairs = std::max(1, std::min(std::min(g.a.s, g.b.s), std::min(g.terms, 8)));
+    const long long prod = (long long)g.a.max_digit * g.b.max_digit;
+    int kc = 128;
+    while (kc < 512 && pairs * (2 * kc) * prod <= (1ll << 24)) kc *= 2;
+    return kc;
+}
+
+static int choose_splits(int M, int N, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
     const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
     int splits = 1;
-    const int max_splits = std::max(1, (Kp + KCHUNK - 1) / KCHUNK);
+    const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
     if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
     while (splits > 1 && (size_t)splits * M * N * 16 > scratch_bytes) --splits;
     int kps = (Kp + splits - 1) / splits;
-    kps = (kps + KCHUNK - 1) / KCHUNK * KCHUNK;
+    kps = (kps + kchunk - 1) / kchunk * kchunk;
     *kps_out = kps;
     return (Kp + kps - 1) / kps;
 }
@@ -706,10 +778,12 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     if (!make_stack_map(&mapA, g.a, TM, 1) || !make_stack_map(&mapB, g.b, TN, g.b.s))
         return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
     const int Kp = (K + KB - 1) / KB * KB;
+    const int kchunk = chunk_for(g);
     int kps = 0;
-    const int splits = choose_splits(M, N, Kp, scratch_bytes, &kps);
+    const int splits = choose_splits(M, N, Kp, scratch_bytes, kchunk, &kps);
     Sg2Dev p;
     p.M = M; p.N = N; p.Kp = Kp; p.sa = g.a.s; p.sb = g.b.s; p.terms = g.terms; p.k_per_split = kps;
+    p.chunk_kb = kchunk / KB;
     p.ea = g.a.e; p.eb = g.b.e;
     p.part = (long long*)scratch;
     p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
@@ -740,7 +814,16 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     const size_t smem = fixed + (size_t)best_bs * b_stage + (size_t)best_as * A_PLANE_BYTES;
     cudaError_t e = cudaFuncSetAttribute(sliced_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM, splits);
+    p.splits = splits;
+    const int ntiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM) * splits;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 148;
+    }
+    const int grid = std::min(ntiles, sms);   // persistent: one CTA per SM walks the tiles
     sliced_gemm2_kernel<<<grid, W_THREADS, smem, s>>>(mapA, mapB, p);
     note_launch();
     if (splits > 1) launch_reduce(g, splits, scratch, s);

@@ -157,13 +157,13 @@ rtproj_status rtp::middle_fp64(rtproj_ctx* h, const double* c, double* out, int 
     const int m = (int)h->m;
     Gemm64 g;
     g.M = m; g.N = k; g.K = m;
-    g.A = h->T1; g.a_rs = m; g.a_cs = 1;
+    g.A = h->T1; g.a_rs = m; g.a_cs = 1; g.a_tri = 1;      // T1 is lower triangular
     g.B = c; g.b_rs = k; g.b_cs = 1; g.bk = h->perm;
     g.C = h->ebuf; g.c_rs = k; g.c_cs = 1;
     RT_CHECK(gemm64(g, h->part, h->part_elems, h->stream));
     Gemm64 t;
     t.M = m; t.N = k; t.K = m;
-    t.A = h->T1; t.a_rs = 1; t.a_cs = m;
+    t.A = h->T1; t.a_rs = 1; t.a_cs = m; t.a_tri = 2;      // T1^* is upper triangular
     t.B = h->ebuf; t.b_rs = k; t.b_cs = 1;
     t.C = out; t.c_rs = k; t.c_cs = 1; t.crow = h->perm;
     RT_CHECK(gemm64(t, h->part, h->part_elems, h->stream));

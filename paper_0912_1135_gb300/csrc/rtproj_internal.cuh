@@ -77,6 +77,7 @@ struct Gemm64 {
     double alpha = 1.0, beta = 0.0;
     const double* Cin = nullptr; int64_t cin_rs = 0, cin_cs = 0;
     bool lower_only = false;   // compute/write only entries with i >= j (tiles above skipped)
+    int a_tri = 0;             // 1: A(i,k) = 0 for k > i (lower); 2: A(i,k) = 0 for k < i (upper)
 };
 
 // Enqueues the GEMM + reduce. part/part_elems: scratch for the partial slabs.
@@ -122,6 +123,7 @@ struct SliceStack {
     int rows = 0, cols = 0, s = 0;
     int64_t ld = 0;
     int64_t plane_stride = 0;
+    int max_digit = 128;     // bound on |digit| (255 for the G plane)
 };
 
 // Slices X (element (r, c) at X[r*x_rs + c*x_cs], multiplied by 2^cexp[c] when cexp is
