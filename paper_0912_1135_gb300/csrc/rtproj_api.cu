@@ -60,7 +60,7 @@ constexpr size_t kPartElems = 1216ull * 4096ull;   // bounds every split-K slab 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t status, S, qr_work, perm, R, RinvT, Lc, T1, W, part, cbuf, ebuf, hbuf, dhbuf, sbuf;
+    size_t status, S, qr_work, perm, R, RinvT, Lc, T1, dinv, W, part, cbuf, ebuf, hbuf, dhbuf, sbuf;
     size_t mixed_base, mixed_bytes;
     size_t total;
 };
@@ -90,6 +90,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtp
     L.RinvT = take((size_t)m * m * 8);
     L.Lc = take((size_t)m * m * 8);
     L.T1 = take((size_t)m * m * 8);
+    L.dinv = take(trsm_work_doubles((int)m) * 8);
     L.W = take((size_t)m * n * 8);
     L.part = take(kPartElems * 8);
     L.cbuf = take((size_t)m * k_max * 8);
@@ -284,6 +285,7 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A
     h->RinvT = (double*)(b + L.RinvT);
     h->Lc = (double*)(b + L.Lc);
     h->T1 = (double*)(b + L.T1);
+    h->dinv = (double*)(b + L.dinv);
     h->W = (double*)(b + L.W);
     h->part = (double*)(b + L.part);
     h->part_elems = kPartElems;
@@ -355,7 +357,7 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     // R^{-*} (the transpose of P^- of Eq. 15, up to Pi)
     phase_begin(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(set_identity(h->RinvT, m, s));
-    RT_CHECK(trsm(h->R, 1, m, true, m, h->RinvT, m, m, h->status, s));
+    RT_CHECK(trsm(h->R, 1, m, true, m, h->RinvT, m, m, h->dinv, h->status, s));
     phase_end(h, RTPROJ_PHASE_FACTOR);
     // 3. X = P^{-1} A A^* P^{-*} (Eq. 14 via steps a-e, as W W^*)
     phase_begin(h, RTPROJ_PHASE_GRAM);
@@ -366,7 +368,7 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_begin(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(cholesky(h->Lc, m, h->part, h->part_elems, h->status, s));
     RT_CHECK(cudaMemcpyAsync(h->T1, h->RinvT, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
-    RT_CHECK(trsm(h->Lc, m, 1, true, m, h->T1, m, m, h->status, s));
+    RT_CHECK(trsm(h->Lc, m, 1, true, m, h->T1, m, m, h->dinv, h->status, s));
     phase_end(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(cudaEventRecord(h->ev1, s));
     RT_CHECK(cudaStreamSynchronize(s));

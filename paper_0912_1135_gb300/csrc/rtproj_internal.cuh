@@ -103,8 +103,10 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
 // Triangular solves and Cholesky (k_tri.cu).
 // Solves op(T) X = Bm in place; T (m x m) element (i,j) at T[i*t_rs + j*t_cs];
 // lower selects forward substitution. Bm element (i, j) at Bm[i*b_rs + j], j < ncols.
+// dinv_work: trsm_work_doubles(m) doubles (inverses of the 32 x 32 diagonal blocks).
 cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
-                 double* Bm, int64_t b_rs, int ncols, int* status, cudaStream_t s);
+                 double* Bm, int64_t b_rs, int ncols, double* dinv_work, int* status, cudaStream_t s);
+size_t trsm_work_doubles(int m);
 // In-place lower Cholesky of the m x m row-major X (strict upper part zeroed).
 cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s);
 
@@ -179,6 +181,7 @@ struct rtproj_ctx {
     double* RinvT = nullptr;     // m x m, R^{-*}
     double* Lc = nullptr;        // m x m, chol(X)
     double* T1 = nullptr;        // m x m, Lc^{-1} R^{-*}
+    double* dinv = nullptr;      // inverses of the 32 x 32 diagonal blocks (trsm)
     double* W = nullptr;         // m x n, P^{-1} A (float64 mode)
     double* part = nullptr;      // split-K partial slabs
     size_t part_elems = 0;
