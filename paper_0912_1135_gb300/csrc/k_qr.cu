@@ -157,9 +157,9 @@ __global__ void qr_extract_r_kernel(const double* S, int m, int64_t lds, double*
 // [b*cpc, b*cpc + cpc) of S^* (rows of S) in shared memory for the whole
 // factorization. Per step j: every CTA publishes the best remaining column norm it
 // owns and arrives on a grid-wide counter; after all have arrived each CTA picks the
-// global pivot (largest norm, lowest index on ties); the owner of the pivot builds the
-// reflector and publishes it (with a release flag); the others fetch it from L2 and
-// apply it to their active columns, downdating the norms. Columns never move: the
+// global pivot (largest norm, lowest index on ties), reads the pivot column from global
+// memory (every CTA writes its updated columns back after each step), forms the
+// reflector itself and applies it to its active columns, downdating the norms. Columns never move: the
 // pivot column is retired and R[:, j] is the retired column's first j+1 entries.
 // Every wait has a clock deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all
 // CTAs leave their loops.
@@ -276,14 +276,19 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         __syncthreads();
         const int piv = piv_s;
         if (piv < 0) { alive = false; break; }     // cannot happen while columns remain
+        // 3. every CTA forms the reflector itself from the pivot column, read from global
+        //    memory (each CTA writes its active columns back after every update), so the
+        //    reflector needs no second broadcast. All CTAs sum in the same order and get
+        //    bitwise the same alpha, beta and v.
         const int owner = piv / cpc;
-        double* vg = p.vbuf + (size_t)par * l;
-        if (owner == b) {
-            // 3a. the owner builds the reflector from its column
-            const int q = piv - c0;
-            double* c = cols + (size_t)q * l;
+        {
+            const double* pc = p.S + (int64_t)piv * p.lds;
             double s = 0.0;
-            for (int i = j + t; i < l; i += PQ_THREADS) s = fma(c[i], c[i], s);
+            for (int i = j + t; i < l; i += PQ_THREADS) {
+                const double x = __ldcg(pc + i);
+                v[i - j] = x;
+                s = fma(x, x, s);
+            }
             s = warp_sum(s);
             if (lane == 0) redv[warp] = s;
             __syncthreads();
@@ -291,34 +296,21 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
                 double nx2 = 0.0;
                 for (int w = 0; w < PQ_WARPS; ++w) nx2 += redv[w];
                 const double nx = sqrt(nx2);
-                const double x0 = c[j];
+                const double x0 = v[0];
                 double alpha = 0.0, beta = 0.0;
                 if (nx > 0.0) {
                     alpha = x0 >= 0.0 ? -nx : nx;
                     beta = 1.0 / (nx * (nx + fabs(x0)));
                 }
                 v[0] = x0 - alpha;
-                vg[0] = x0 - alpha;
-                p.scal[par * 2 + 1] = beta;
                 beta_s = beta;
-                c[j] = alpha;
-                posq[q] = j;
-                p.perm[j] = piv;
+                if (owner == b) {
+                    const int q = piv - c0;
+                    cols[(size_t)q * l + j] = alpha;
+                    posq[q] = j;
+                    p.perm[j] = piv;
+                }
             }
-            for (int i = j + 1 + t; i < l; i += PQ_THREADS) {
-                v[i - j] = c[i];
-                vg[i - j] = c[i];
-            }
-            __threadfence();
-            __syncthreads();
-            if (t == 0) st_release(p.flags + j, 1u);
-        } else {
-            // 3b. the others fetch it
-            if (t == 0) ok_s = wait_geq(p.flags + j, 1u, p.abort_flag, p.status, p.timeout);
-            __syncthreads();
-            if (!ok_s) { alive = false; break; }
-            for (int i = t; i < l - j; i += PQ_THREADS) v[i] = __ldcg(vg + i);
-            if (t == 0) beta_s = __ldcg(p.scal + par * 2 + 1);
             __syncthreads();
         }
         // 4. apply I - beta v v^* to the active columns, downdate their norms
@@ -348,6 +340,9 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
                 }
             }
             __syncwarp();
+            // write the updated tail back for the next pivot search
+            double* gcol = p.S + (int64_t)(c0 + q) * p.lds;
+            for (int i = lane; i < len; i += 32) gcol[j + i] = c[i];
         }
         __syncthreads();
     }
