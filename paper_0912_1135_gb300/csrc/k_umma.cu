@@ -138,16 +138,48 @@ __device__ __forceinline__ int exact_f2i(float x) {
 }
 
 // Adds the level-g sums of one 128-row x 32-column readout (r) into the int64 words.
+// When every value of the warp's readout is below 2^22 in magnitude (the usual case) one
+// magic-offset add converts each; otherwise the two-part exact_f2i is used.
 __device__ __forceinline__ void fold_level(int g, const uint32_t (&r)[32], long long (&hi)[32], long long (&lo)[32]) {
-    if (g <= 4) {
-        const int sh = 8 * (4 - g);
+    bool small = true;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) hi[j] += (long long)exact_f2i(__uint_as_float(r[j])) << sh;
+    for (int j = 0; j < 32; ++j) small &= fabsf(__uint_as_float(r[j])) < 4194304.0f;
+    const bool fast = __all_sync(0xffffffffu, small);
+    const int sh = g <= 4 ? 8 * (4 - g) : 8 * (9 - g);
+    long long* acc = g <= 4 ? hi : lo;
+    if (fast) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int v = __float_as_int(__fadd_rn(__uint_as_float(r[j]), 12582912.0f)) - 0x4B400000;
+            if (g <= 4) hi[j] += (long long)v << sh; else lo[j] += (long long)v << sh;
+        }
     } else {
-        const int sh = 8 * (9 - g);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) lo[j] += (long long)exact_f2i(__uint_as_float(r[j])) << sh;
+        for (int j = 0; j < 32; ++j) {
+            const int v = exact_f2i(__uint_as_float(r[j]));
+            if (g <= 4) hi[j] += (long long)v << sh; else lo[j] += (long long)v << sh;
+        }
     }
+    (void)acc;
+}
+
+// (hi * 2^40 + lo) * 2^e as a double: one fused multiply-add of the two words (rounded
+// once, or twice when |hi| >= 2^53), then the power of two is added to the exponent
+// field; ldexp only when the result would leave the normal range.
+__device__ __forceinline__ double words_to_double(long long hi, long long lo, int e) {
+    const double d = fma((double)hi, 1099511627776.0, (double)lo);
+    const long long bits = __double_as_longlong(d);
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (d == 0.0 || ex + e <= 0 || ex + e >= 2047) return ldexp(d, e);
+    return __longlong_as_double(bits + ((long long)e << 52));
+}
+
+// alpha * v + beta * cin for the common alpha = +-1, beta in {0, 1} without FP64 multiplies.
+__device__ __forceinline__ double epilogue_value(double v, double alpha, double beta, const double* cin) {
+    double out = alpha == 1.0 ? v : (alpha == -1.0 ? -v : alpha * v);
+    if (beta == 1.0) out += *cin;
+    else if (beta != 0.0) out = fma(beta, *cin, out);
+    return out;
 }
 
 // Shared-memory matrix descriptor: K-major, SWIZZLE_128B (8-row atoms of 1024 bytes).
@@ -300,10 +332,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gemm_kernel(SgDev p) {
             for (int j = 0; j < TN; ++j) {
                 const int gj = j0 + j;
                 if (gj >= p.N || (p.lower_only && gj > i)) continue;
-                const double v = ldexp(ldexp((double)hi[j], 40) + (double)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
-                double out = p.alpha * v;
-                if (p.beta != 0.0) out += p.beta * p.Cin[(int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs];
-                p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = out;
+                const double v = words_to_double(hi[j], lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                p.C[row * p.c_rs + (int64_t)gj * p.c_cs] =
+                    epilogue_value(v, p.alpha, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
             }
         }
     }
@@ -335,11 +366,10 @@ __global__ void sliced_reduce_kernel(SgReduceDev r) {
     const long long h = (long long)(acc >> 40);
     const long long l = (long long)(acc - ((__int128)h << 40));   // in [0, 2^40)
     const int e = (r.ea ? r.ea[i] : 0) + (r.eb ? r.eb[j] : 0) - 86;
-    const double v = ldexp(ldexp((double)h, 40) + (double)l, e);
-    double out = r.alpha * v;
-    if (r.beta != 0.0) out += r.beta * r.Cin[(int64_t)i * r.cin_rs + (int64_t)j * r.cin_cs];
+    const double v = words_to_double(h, l, e);
     const int64_t row = r.crow ? (int64_t)r.crow[i] : (int64_t)i;
-    r.C[row * r.c_rs + (int64_t)j * r.c_cs] = out;
+    r.C[row * r.c_rs + (int64_t)j * r.c_cs] =
+        epilogue_value(v, r.alpha, r.beta, r.Cin + (int64_t)i * r.cin_rs + (int64_t)j * r.cin_cs);
 }
 
 
@@ -609,11 +639,9 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     for (int j = 0; j < TN; ++j) {
                         const int gj = c.j0 + j;
                         if (gj >= p.N || (p.lower_only && gj > i)) continue;
-                        const double v =
-                            ldexp(ldexp((double)hi[j], 40) + (double)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
-                        double out = p.alpha * v;
-                        if (p.beta != 0.0) out += p.beta * p.Cin[(int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs];
-                        p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = out;
+                        const double v = words_to_double(hi[j], lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                        p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = epilogue_value(
+                            v, p.alpha, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
                     }
                 }
             }
