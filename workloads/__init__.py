@@ -137,8 +137,9 @@ class Workload:
         return rhs(self.k if k is None else k, self.n, self.seed_b)
 
 
-# Small dense configuration (oracle-sized) and the headline dense configuration.
+# Small dense configuration (oracle-sized, l = 4m) and the headline dense configuration
+# (l = m + 4, the sketch size Section 4 suggests).
 WORKLOADS = {
     "dense_64x2048": Workload("dense_64x2048_kappa1e8_k16", 64, 2048, 1e-8, 16, 256, 1, 11, 21),
-    "dense_512x65536": Workload("dense_512x65536_kappa1e10_k64", 512, 65536, 1e-10, 64, 2048, 2, 12, 22),
+    "dense_512x65536": Workload("dense_512x65536_kappa1e10_k64", 512, 65536, 1e-10, 64, 516, 2, 12, 22),
 }
