@@ -20,6 +20,8 @@
 // operands with cp.async into the SWIZZLE_128B K-major layout and read TMEM back.
 #include "rtproj_internal.cuh"
 
+#include <utility>
+
 #include <cuda.h>
 
 #include <algorithm>
@@ -180,6 +182,130 @@ __device__ __forceinline__ double epilogue_value(double v, double alpha, double 
     if (beta == 1.0) out += *cin;
     else if (beta != 0.0) out = fma(beta, *cin, out);
     return out;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// Level g of the 10-level fixed point goes to word hi (g <= 4) or lo (g >= 5), scaled by
+// 2^level_shift(g).
+__host__ __device__ constexpr int level_shift(int g) { return g <= 4 ? 8 * (4 - g) : 8 * (9 - g); }
+
+// acc += v * 2^SH modulo 2^64: one wide multiply-add (SH < 32) or one add to the upper word.
+template <int SH>
+__device__ __forceinline__ void add_shifted(unsigned long long& acc, int v) {
+    if constexpr (SH == 32) {
+        acc += (unsigned long long)(unsigned)v << 32;
+    } else {
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(v), "r"(1 << SH));
+    }
+}
+
+// Sum over levels [G0, G1) that land in word `hi_word` of 0x4B400000 * 2^level_shift, modulo
+// 2^64: the offset that the magic-number conversion adds to every value.
+__host__ __device__ constexpr unsigned long long magic_bias(int G0, int G1, bool hi_word) {
+    unsigned long long b = 0;
+    for (int g = G0; g < G1; ++g)
+        if ((g <= 4) == hi_word) b += 0x4B400000ull << level_shift(g);
+    return b;
+}
+
+// Adds level L of a readout into its word: raw bits of x + 1.5 * 2^23 (FAST) or the exact
+// integer value.
+template <int L, bool FAST>
+__device__ __forceinline__ void fold_one(const uint32_t (&r)[16], unsigned long long (&hi)[16],
+                                         unsigned long long (&lo)[16]) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const int v = FAST ? __float_as_int(__fadd_rn(__uint_as_float(r[j]), 12582912.0f))
+                           : exact_f2i(__uint_as_float(r[j]));
+        if constexpr (L <= 4) add_shifted<level_shift(L)>(hi[j], v);
+        else add_shifted<level_shift(L)>(lo[j], v);
+    }
+}
+template <int G0, bool FAST, int... I>
+__device__ __forceinline__ void fold_levels(const uint32_t (&r)[sizeof...(I)][16], unsigned long long (&hi)[16],
+                                            unsigned long long (&lo)[16], std::integer_sequence<int, I...>) {
+    (fold_one<G0 + I, FAST>(r[I], hi, lo), ...);
+}
+
+// Folds levels [G0, G1) of one readout (16 columns of this warp's 32 TMEM lanes) into the
+// words. All levels are loaded, then checked: when every value is below 2^22 in magnitude
+// (the usual case) one add of 1.5 * 2^23 puts the integer in the low mantissa bits and the
+// raw bits are accumulated, the constant offset being removed once per word; otherwise
+// each value goes through the two-part exact_f2i. With `release`, the TMEM buffer is
+// handed back to the MMA warp as soon as the values are in registers.
+template <int G0, int G1>
+__device__ __forceinline__ void fold_group16(uint32_t base, unsigned long long (&hi)[16],
+                                             unsigned long long (&lo)[16], bool release, uint64_t* empty_bar) {
+    constexpr int NG = G1 - G0;
+    uint32_t r[NG][16];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) tmem_ld16(base + (uint32_t)((G0 + g) * TN), r[g]);
+    tmem_ld_wait();
+    if (release) {
+        tc_fence_before();
+        mbar_arrive(empty_bar);
+    }
+    float mx = 0.0f;
+#pragma unroll
+    for (int g = 0; g < NG; ++g)
+#pragma unroll
+        for (int j = 0; j < 16; ++j) mx = fmaxf(mx, fabsf(__uint_as_float(r[g][j])));
+    if (__all_sync(0xffffffffu, mx < 4194304.0f)) {
+        fold_levels<G0, true>(r, hi, lo, std::make_integer_sequence<int, NG>{});
+        constexpr unsigned long long bh = magic_bias(G0, G1, true), bl = magic_bias(G0, G1, false);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if constexpr (bh != 0) hi[j] -= bh;
+            if constexpr (bl != 0) lo[j] -= bl;
+        }
+    } else {
+        fold_levels<G0, false>(r, hi, lo, std::make_integer_sequence<int, NG>{});
+    }
+}
+
+// One chunk readout for TERMS levels: levels 0-4 then 5-9, the buffer released after the
+// last load. Afterwards |lo| < 2^40 (carry moved into hi).
+template <int TERMS>
+__device__ __forceinline__ void readout16(uint32_t base, unsigned long long (&hi)[16], unsigned long long (&lo)[16],
+                                          uint64_t* empty_bar) {
+    constexpr int A1 = TERMS < 5 ? TERMS : 5;
+    fold_group16<0, A1>(base, hi, lo, TERMS <= 5, empty_bar);
+    if constexpr (TERMS > 5) fold_group16<5, TERMS>(base, hi, lo, true, empty_bar);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        const long long carry = (long long)lo[j] >> 40;
+        hi[j] += (unsigned long long)carry;
+        lo[j] -= (unsigned long long)carry << 40;
+    }
+}
+
+__device__ __forceinline__ void readout16_terms(int terms, uint32_t base, unsigned long long (&hi)[16],
+                                                unsigned long long (&lo)[16], uint64_t* empty_bar) {
+    switch (terms) {
+        case 1: readout16<1>(base, hi, lo, empty_bar); break;
+        case 2: readout16<2>(base, hi, lo, empty_bar); break;
+        case 3: readout16<3>(base, hi, lo, empty_bar); break;
+        case 4: readout16<4>(base, hi, lo, empty_bar); break;
+        case 5: readout16<5>(base, hi, lo, empty_bar); break;
+        case 6: readout16<6>(base, hi, lo, empty_bar); break;
+        case 7: readout16<7>(base, hi, lo, empty_bar); break;
+        case 8: readout16<8>(base, hi, lo, empty_bar); break;
+        case 9: readout16<9>(base, hi, lo, empty_bar); break;
+        default: readout16<10>(base, hi, lo, empty_bar); break;
+    }
 }
 
 // Shared-memory matrix descriptor: K-major, SWIZZLE_128B (8-row atoms of 1024 bytes).
@@ -384,11 +510,13 @@ __global__ void sliced_reduce_kernel(SgReduceDev r) {
 // a 128-k chunk (p = 0) covers every level (terms <= sb is required), so it alone
 // carries accumulate = 0. Warp 0 issues the TMA loads into a ring of A-plane stages and
 // a ring of B-plane stages; warp 1 issues the MMAs and commits each stage back to its
-// producer; warps 2-5 read the level sums of each chunk from TMEM (double-buffered when
-// 2 * terms * 32 <= 512 columns) and fold them into int64 words exactly as the
-// synchronous form does. Every mbarrier wait is bounded; expiry raises RTPROJ_ETIMEOUT.
+// producer; warps 2-9 (two per TMEM lane quarter, 16 columns each) read the level sums of
+// each chunk from TMEM (double-buffered when 2 * terms * 32 <= 512 columns), hand the
+// buffer back as soon as the values are in registers, and fold them into the same int64
+// words as the synchronous form. Every mbarrier wait is bounded; expiry raises RTPROJ_ETIMEOUT.
 // =====================================================================================
-constexpr int W_THREADS = 192;
+constexpr int W_EPI_WARPS = 8;                  // two per TMEM lane quarter, 16 columns each
+constexpr int W_THREADS = 64 + 32 * W_EPI_WARPS;
 constexpr int W_MAX_A_STAGES = 16;
 constexpr int W_MAX_B_STAGES = 8;
 
@@ -409,9 +537,6 @@ struct Sg2Dev {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
     asm volatile(
@@ -477,7 +602,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         abort_s = 0;
         for (int i = 0; i < AS; ++i) { mbar_init(fullA + i, 1); mbar_init(emptyA + i, 1); }
         for (int i = 0; i < BSN; ++i) { mbar_init(fullB + i, 1); mbar_init(emptyB + i, 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(tfull + i, 1); mbar_init(tempty + i, 128); }
+        for (int i = 0; i < 2; ++i) { mbar_init(tfull + i, 1); mbar_init(tempty + i, 32 * W_EPI_WARPS); }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
@@ -580,8 +705,9 @@ __global__ void __launch_bounds__(W_THREADS, 1)
             }
         }
     } else {
-        // ---------------- epilogue: warps 2..5 read TMEM lanes 32 * (warp % 4) ...
-        const int quarter = warp & 3;
+        // ---------------- epilogue: warps 2..9; warp w reads TMEM lanes 32 * (w % 4) ... + 31
+        // (the lane quarter it may access) and columns 16 * half ... + 15 of each level.
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
         int chunk = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
@@ -590,9 +716,9 @@ __global__ void __launch_bounds__(W_THREADS, 1)
             const int kbeg = c.z * p.k_per_split;
             const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
             const int nchunks = (nkb + cb - 1) / cb;
-            long long hi[TN], lo[TN];
+            unsigned long long hi[16], lo[16];
 #pragma unroll
-            for (int j = 0; j < TN; ++j) { hi[j] = 0; lo[j] = 0; }
+            for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
             for (int cc = 0; cc < nchunks; ++cc, ++chunk) {
                 const int buf = chunk % p.acc_bufs;
                 if (!wait_phase(tfull + buf, (chunk / p.acc_bufs) & 1, abort_v, p.status, p.timeout)) {
@@ -600,46 +726,28 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * buf_cols;
-                uint32_t ra[32], rb[32];
-                tmem_ld32(base, ra);
-                tmem_ld_wait();
-                for (int g = 0; g < p.terms; g += 2) {
-                    // load level g + 1 while level g is folded
-                    if (g + 1 < p.terms) tmem_ld32(base + (uint32_t)((g + 1) * TN), rb);
-                    fold_level(g, ra, hi, lo);
-                    tmem_ld_wait();
-                    if (g + 1 < p.terms) {
-                        if (g + 2 < p.terms) tmem_ld32(base + (uint32_t)((g + 2) * TN), ra);
-                        fold_level(g + 1, rb, hi, lo);
-                        tmem_ld_wait();
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < TN; ++j) {
-                    const long long carry = lo[j] >> 40;
-                    hi[j] += carry;
-                    lo[j] -= carry * (1ll << 40);
-                }
-                tc_fence_before();
-                mbar_arrive(tempty + buf);
+                const uint32_t base =
+                    tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * buf_cols + (uint32_t)(half * 16);
+                readout16_terms(p.terms, base, hi, lo, tempty + buf);
             }
             if (!ok) break;
             const int i = c.i0 + quarter * 32 + lane;
+            const int jb = c.j0 + half * 16;
             if (!*abort_v && i < p.M) {
                 if (p.splits > 1) {
-                    long long* dst = p.part + (((int64_t)c.z * p.M + i) * p.N + c.j0) * 2;
+                    long long* dst = p.part + (((int64_t)c.z * p.M + i) * p.N + jb) * 2;
 #pragma unroll
-                    for (int j = 0; j < TN; ++j)
-                        if (c.j0 + j < p.N) { dst[2 * j] = hi[j]; dst[2 * j + 1] = lo[j]; }
+                    for (int j = 0; j < 16; ++j)
+                        if (jb + j < p.N) { dst[2 * j] = (long long)hi[j]; dst[2 * j + 1] = (long long)lo[j]; }
                 } else {
                     const int ea = p.ea ? p.ea[i] : 0;
                     const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
 #pragma unroll
-                    for (int j = 0; j < TN; ++j) {
-                        const int gj = c.j0 + j;
+                    for (int j = 0; j < 16; ++j) {
+                        const int gj = jb + j;
                         if (gj >= p.N || (p.lower_only && gj > i)) continue;
-                        const double v = words_to_double(hi[j], lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                        const double v = words_to_double((long long)hi[j], (long long)lo[j],
+                                                         ea + (p.eb ? p.eb[gj] : 0) - 86);
                         p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = epilogue_value(
                             v, p.alpha, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
                     }
