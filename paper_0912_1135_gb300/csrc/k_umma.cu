@@ -314,6 +314,9 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Descriptor from its two 32-bit words.
+__device__ __forceinline__ uint64_t make_desc(uint32_t lo, uint32_t hi) { return ((uint64_t)hi << 32) | lo; }
+
 // Instruction descriptor, kind::f16: F32 accumulator, BF16 A and B, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -534,15 +537,38 @@ struct Sg2Dev {
     int acc_bufs, a_stages, b_stages;
 };
 
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+
+// Warp-converged forms of the single-thread operations: every lane executes the
+// instruction sequence with the same (warp-uniform) operands and lane 0 alone issues it,
+// through a predicate rather than a branch, so that the issuing warp never diverges.
+__device__ __forceinline__ void tma_load_3d_lane0(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                                  uint64_t* bar, uint32_t bytes) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
-            dst),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        "{\n\t.reg .pred e;\n\t.reg .u32 l;\n\t"
+        "mov.u32 l, %%laneid;\n\t"
+        "setp.eq.u32 e, l, 0;\n\t"
+        "@e mbarrier.arrive.expect_tx.shared::cta.b64 _, [%5], %6;\n\t"
+        "@e cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n\t}\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar)), "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ void umma_bf16_lane0(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                                uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t.reg .u32 l;\n\t"
+        "mov.u32 l, %%laneid;\n\t"
+        "setp.eq.u32 e, l, 0;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit_lane0(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t.reg .u32 l;\n\t"
+        "mov.u32 l, %%laneid;\n\t"
+        "setp.eq.u32 e, l, 0;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}\n" ::"r"(smem_addr(bar))
         : "memory");
 }
 
@@ -559,6 +585,27 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
         }
     }
     return true;
+}
+
+// The same bounded wait for a whole converged warp: every lane polls, the exit decision is
+// warp-uniform (lane 0 owns the timeout and the abort flag).
+__device__ __forceinline__ bool wait_phase_warp(uint64_t* bar, uint32_t parity, volatile int* abort_s, int* status,
+                                                long long timeout) {
+    const long long t0 = clock64();
+    while (true) {
+        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        int bad = 0;
+        if ((threadIdx.x & 31) == 0) {
+            if (*abort_s) {
+                bad = 1;
+            } else if (clock64() - t0 > timeout) {
+                *abort_s = 1;
+                set_status(status, RTPROJ_ETIMEOUT);
+                bad = 1;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+    }
 }
 
 // Tile t of the persistent loop -> (x = B-row tile, y = A-row tile, z = K split).
@@ -618,89 +665,103 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     // Every role walks the same tile sequence (blockIdx.x, + gridDim.x, ...), skipping the
     // tiles strictly above the diagonal when only the lower triangle is wanted.
     if (warp == 0) {
-        // ---------------- TMA producer
-        if (lane == 0) {
-            uint32_t a_it = 0, b_it = 0;
-            for (int tile = blockIdx.x; tile < ntiles && !*abort_v; tile += gridDim.x) {
-                const TileCoord c = tile_of(tile, tiles_n, tiles_m);
-                if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
-                const int kbeg = c.z * p.k_per_split;
-                const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
-                for (int kb = 0; kb < nkb && !*abort_v; ++kb) {
-                    const int k0 = kbeg + kb * KB;
-                    const int bs = b_it % BSN;
-                    if (b_it >= (uint32_t)BSN &&
-                        !wait_phase(emptyB + bs, ((b_it / BSN) - 1) & 1, abort_v, p.status, p.timeout))
+        // ---------------- TMA producer (whole warp, lane 0 issues)
+        uint32_t a_it = 0, b_it = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const TileCoord c = tile_of(tile, tiles_n, tiles_m);
+            if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+            const int kbeg = c.z * p.k_per_split;
+            const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const int k0 = kbeg + kb * KB;
+                const int bs = b_it % BSN;
+                if (b_it >= (uint32_t)BSN &&
+                    !wait_phase_warp(emptyB + bs, ((b_it / BSN) - 1) & 1, abort_v, p.status, p.timeout)) {
+                    ok = false;
+                    break;
+                }
+                tma_load_3d_lane0(smem_addr(sB + (size_t)bs * b_stage_bytes), &tmB, k0, c.j0, 0, fullB + bs,
+                                  b_stage_bytes);
+                ++b_it;
+                for (int pa = 0; pa < p.sa; ++pa) {
+                    const int as = a_it % AS;
+                    if (a_it >= (uint32_t)AS &&
+                        !wait_phase_warp(emptyA + as, ((a_it / AS) - 1) & 1, abort_v, p.status, p.timeout)) {
+                        ok = false;
                         break;
-                    mbar_expect_tx(fullB + bs, b_stage_bytes);
-                    tma_load_3d(smem_addr(sB + (size_t)bs * b_stage_bytes), &tmB, k0, c.j0, 0, fullB + bs);
-                    ++b_it;
-                    for (int pa = 0; pa < p.sa; ++pa) {
-                        const int as = a_it % AS;
-                        if (a_it >= (uint32_t)AS &&
-                            !wait_phase(emptyA + as, ((a_it / AS) - 1) & 1, abort_v, p.status, p.timeout))
-                            break;
-                        mbar_expect_tx(fullA + as, A_PLANE_BYTES);
-                        tma_load_3d(smem_addr(sA + (size_t)as * A_PLANE_BYTES), &tmA, k0, c.i0, pa, fullA + as);
-                        ++a_it;
                     }
+                    tma_load_3d_lane0(smem_addr(sA + (size_t)as * A_PLANE_BYTES), &tmA, k0, c.i0, pa, fullA + as,
+                                      A_PLANE_BYTES);
+                    ++a_it;
                 }
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer
-        if (lane == 0) {
-            uint32_t a_it = 0, b_it = 0;
-            int chunk = 0, buf = 0;
-            bool ok = true;
-            for (int tile = blockIdx.x; tile < ntiles && ok && !*abort_v; tile += gridDim.x) {
-                const TileCoord c = tile_of(tile, tiles_n, tiles_m);
-                if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
-                const int kbeg = c.z * p.k_per_split;
-                const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
-                for (int kb = 0; kb < nkb && ok; ++kb) {
-                    const bool chunk_start = (kb % cb) == 0;
-                    if (chunk_start) {
-                        buf = chunk % p.acc_bufs;
-                        if (chunk >= p.acc_bufs &&
-                            !wait_phase(tempty + buf, ((chunk / p.acc_bufs) - 1) & 1, abort_v, p.status, p.timeout)) {
-                            ok = false;
-                            break;
+        // ---------------- MMA issuer (whole warp, lane 0 issues)
+        const uint64_t d0desc = sw128_desc(smem_addr(sA));
+        const uint32_t a_lo0 = (uint32_t)d0desc, desc_hi = (uint32_t)(d0desc >> 32);
+        const uint32_t b_lo0 = (uint32_t)sw128_desc(smem_addr(sB));
+        uint32_t a_it = 0, b_it = 0;
+        int chunk = 0, buf = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            const TileCoord c = tile_of(tile, tiles_n, tiles_m);
+            if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+            const int kbeg = c.z * p.k_per_split;
+            const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
+            for (int kb = 0; kb < nkb && ok; ++kb) {
+                const bool chunk_start = (kb % cb) == 0;
+                if (chunk_start) {
+                    buf = chunk % p.acc_bufs;
+                    if (chunk >= p.acc_bufs &&
+                        !wait_phase_warp(tempty + buf, ((chunk / p.acc_bufs) - 1) & 1, abort_v, p.status, p.timeout)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                }
+                const int bs = b_it % BSN;
+                if (!wait_phase_warp(fullB + bs, (b_it / BSN) & 1, abort_v, p.status, p.timeout)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t b_lo = b_lo0 + (uint32_t)bs * (b_stage_bytes >> 4);
+                for (int pa = 0; pa < p.sa; ++pa) {
+                    const int as = a_it % AS;
+                    if (!wait_phase_warp(fullA + as, (a_it / AS) & 1, abort_v, p.status, p.timeout)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    // Plane pa against B levels 0 .. nwin-1: one MMA for the first eight levels
+                    // (N = 32 per level), a second for levels 8 and 9. Descriptors are built from
+                    // precomputed words: the K step adds 32 bytes (2 units) to the start address.
+                    const int nwin = min(p.sb, p.terms - pa);
+                    if (nwin > 0) {
+                        const int n1 = min(8, nwin), n2 = nwin - n1;
+                        const uint32_t a_lo = a_lo0 + (uint32_t)as * (A_PLANE_BYTES >> 4);
+                        const uint32_t d = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * TN);
+                        const uint32_t id1 = idesc_bf16(TM, n1 * TN), id2 = idesc_bf16(TM, (n2 > 0 ? n2 : 1) * TN);
+#pragma unroll
+                        for (int kk = 0; kk < KB / 16; ++kk) {
+                            const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
+                            const uint64_t ad = make_desc(a_lo + 2 * kk, desc_hi);
+                            umma_bf16_lane0(d, ad, make_desc(b_lo + 2 * kk, desc_hi), id1, acc);
+                            if (n2 > 0)
+                                umma_bf16_lane0(d + 8 * TN, ad, make_desc(b_lo + 8 * (B_PLANE_BYTES >> 4) + 2 * kk, desc_hi),
+                                                id2, acc);
                         }
-                        tc_fence_after();
                     }
-                    const int bs = b_it % BSN;
-                    if (!wait_phase(fullB + bs, (b_it / BSN) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
-                    const uint32_t sB_addr = smem_addr(sB + (size_t)bs * b_stage_bytes);
-                    for (int pa = 0; pa < p.sa; ++pa) {
-                        const int as = a_it % AS;
-                        if (!wait_phase(fullA + as, (a_it / AS) & 1, abort_v, p.status, p.timeout)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t sA_addr = smem_addr(sA + (size_t)as * A_PLANE_BYTES);
-                        const int nwin = min(p.sb, p.terms - pa);
-                        if (nwin > 0) {
-                            const uint32_t d0 = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * TN);
-#pragma unroll 1
-                            for (int kk = 0; kk < KB / 16; ++kk) {
-                                const uint64_t ad = sw128_desc(sA_addr + kk * 32);
-                                const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
-                                for (int w0 = 0; w0 < nwin; w0 += 8) {
-                                    const int nw = min(8, nwin - w0);
-                                    const uint64_t bd = sw128_desc(sB_addr + w0 * B_PLANE_BYTES + kk * 32);
-                                    umma_bf16(d0 + (uint32_t)(w0 * TN), ad, bd, idesc_bf16(TM, nw * TN), acc);
-                                }
-                            }
-                        }
-                        umma_commit(emptyA + as);
-                        ++a_it;
-                    }
-                    if (!ok) break;
-                    umma_commit(emptyB + bs);
-                    ++b_it;
-                    if ((kb % cb) == cb - 1 || kb == nkb - 1) {
-                        umma_commit(tfull + buf);
-                        ++chunk;
-                    }
+                    umma_commit_lane0(emptyA + as);
+                    ++a_it;
+                }
+                if (!ok) break;
+                umma_commit_lane0(emptyB + bs);
+                ++b_it;
+                if ((kb % cb) == cb - 1 || kb == nkb - 1) {
+                    umma_commit_lane0(tfull + buf);
+                    ++chunk;
                 }
             }
         }
