@@ -148,7 +148,6 @@ __device__ __forceinline__ void fold_level(int g, const uint32_t (&r)[32], long 
     for (int j = 0; j < 32; ++j) small &= fabsf(__uint_as_float(r[j])) < 4194304.0f;
     const bool fast = __all_sync(0xffffffffu, small);
     const int sh = g <= 4 ? 8 * (4 - g) : 8 * (9 - g);
-    long long* acc = g <= 4 ? hi : lo;
     if (fast) {
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
@@ -162,7 +161,6 @@ __device__ __forceinline__ void fold_level(int g, const uint32_t (&r)[32], long 
             if (g <= 4) hi[j] += (long long)v << sh; else lo[j] += (long long)v << sh;
         }
     }
-    (void)acc;
 }
 
 // (hi * 2^40 + lo) * 2^e as a double: one fused multiply-add of the two words (rounded
@@ -221,38 +219,36 @@ __host__ __device__ constexpr unsigned long long magic_bias(int G0, int G1, bool
     return b;
 }
 
-// Adds level L of a readout into its word: raw bits of x + 1.5 * 2^23 (FAST) or the exact
-// integer value.
-template <int L, bool FAST>
-__device__ __forceinline__ void fold_one(const uint32_t (&r)[16], unsigned long long (&hi)[16],
-                                         unsigned long long (&lo)[16]) {
+// Adds level L of one 16-column unit (columns CB*16 .. CB*16+15 of the warp's NCOL) into
+// its word. Every value enters with the same offset 0x4B400000: the raw bits of
+// x + 1.5 * 2^23 (FAST, exact when |x| < 2^22) or the exact integer plus that offset; the
+// sum of the offsets is removed once per chunk.
+template <int L, bool FAST, int CB, int NCOL>
+__device__ __forceinline__ void fold_one(const uint32_t (&r)[16], unsigned long long (&hi)[NCOL],
+                                         unsigned long long (&lo)[NCOL]) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         const int v = FAST ? __float_as_int(__fadd_rn(__uint_as_float(r[j]), 12582912.0f))
-                           : exact_f2i(__uint_as_float(r[j]));
-        if constexpr (L <= 4) add_shifted<level_shift(L)>(hi[j], v);
-        else add_shifted<level_shift(L)>(lo[j], v);
+                           : exact_f2i(__uint_as_float(r[j])) + 0x4B400000;
+        if constexpr (L <= 4) add_shifted<level_shift(L)>(hi[CB * 16 + j], v);
+        else add_shifted<level_shift(L)>(lo[CB * 16 + j], v);
     }
 }
-template <int G0, bool FAST, int... I>
-__device__ __forceinline__ void fold_levels(const uint32_t (&r)[sizeof...(I)][16], unsigned long long (&hi)[16],
-                                            unsigned long long (&lo)[16], std::integer_sequence<int, I...>) {
-    (fold_one<G0 + I, FAST>(r[I], hi, lo), ...);
+template <int L0, bool FAST, int CB, int NCOL, int... I>
+__device__ __forceinline__ void fold_levels(const uint32_t (&r)[sizeof...(I)][16], unsigned long long (&hi)[NCOL],
+                                            unsigned long long (&lo)[NCOL], std::integer_sequence<int, I...>) {
+    (fold_one<L0 + I, FAST, CB, NCOL>(r[I], hi, lo), ...);
 }
 
-// Folds levels [G0, G1) of one readout (16 columns of this warp's 32 TMEM lanes) into the
-// words. All levels are loaded, then checked: when every value is below 2^22 in magnitude
-// (the usual case) one add of 1.5 * 2^23 puts the integer in the low mantissa bits and the
-// raw bits are accumulated, the constant offset being removed once per word; otherwise
-// each value goes through the two-part exact_f2i. With `release`, the TMEM buffer is
-// handed back to the MMA warp as soon as the values are in registers.
-template <int G0, int G1>
-__device__ __forceinline__ void fold_group16(uint32_t base, unsigned long long (&hi)[16],
-                                             unsigned long long (&lo)[16], bool release, uint64_t* empty_bar) {
-    constexpr int NG = G1 - G0;
+// Loads levels L0 .. L0+NG-1 of one 16-column unit (TMEM address `addr` + level * tn),
+// checks them, and folds them in; with `release` the TMEM buffer is handed back to the
+// MMA warp as soon as the values are in registers.
+template <int L0, int NG, int CB, int NCOL>
+__device__ __forceinline__ void fold_group(uint32_t addr, uint32_t tn, unsigned long long (&hi)[NCOL],
+                                           unsigned long long (&lo)[NCOL], bool release, uint64_t* empty_bar) {
     uint32_t r[NG][16];
 #pragma unroll
-    for (int g = 0; g < NG; ++g) tmem_ld16(base + (uint32_t)((G0 + g) * TN), r[g]);
+    for (int g = 0; g < NG; ++g) tmem_ld16(addr + (uint32_t)(L0 + g) * tn, r[g]);
     tmem_ld_wait();
     if (release) {
         tc_fence_before();
@@ -263,48 +259,55 @@ __device__ __forceinline__ void fold_group16(uint32_t base, unsigned long long (
     for (int g = 0; g < NG; ++g)
 #pragma unroll
         for (int j = 0; j < 16; ++j) mx = fmaxf(mx, fabsf(__uint_as_float(r[g][j])));
-    if (__all_sync(0xffffffffu, mx < 4194304.0f)) {
-        fold_levels<G0, true>(r, hi, lo, std::make_integer_sequence<int, NG>{});
-        constexpr unsigned long long bh = magic_bias(G0, G1, true), bl = magic_bias(G0, G1, false);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if constexpr (bh != 0) hi[j] -= bh;
-            if constexpr (bl != 0) lo[j] -= bl;
-        }
-    } else {
-        fold_levels<G0, false>(r, hi, lo, std::make_integer_sequence<int, NG>{});
-    }
+    if (__all_sync(0xffffffffu, mx < 4194304.0f))
+        fold_levels<L0, true, CB, NCOL>(r, hi, lo, std::make_integer_sequence<int, NG>{});
+    else
+        fold_levels<L0, false, CB, NCOL>(r, hi, lo, std::make_integer_sequence<int, NG>{});
 }
 
-// One chunk readout for TERMS levels: levels 0-4 then 5-9, the buffer released after the
-// last load. Afterwards |lo| < 2^40 (carry moved into hi).
-template <int TERMS>
-__device__ __forceinline__ void readout16(uint32_t base, unsigned long long (&hi)[16], unsigned long long (&lo)[16],
-                                          uint64_t* empty_bar) {
-    constexpr int A1 = TERMS < 5 ? TERMS : 5;
-    fold_group16<0, A1>(base, hi, lo, TERMS <= 5, empty_bar);
-    if constexpr (TERMS > 5) fold_group16<5, TERMS>(base, hi, lo, true, empty_bar);
+// Level groups of one chunk readout: 16-column units in order, levels in groups of GS.
+template <int TERMS, int NCOL, int CB, int L0>
+__device__ __forceinline__ void readout_rec(uint32_t addr0, uint32_t tn, unsigned long long (&hi)[NCOL],
+                                            unsigned long long (&lo)[NCOL], uint64_t* empty_bar) {
+    constexpr int GS = NCOL == 16 ? 5 : 1;
+    constexpr int NG = (TERMS - L0) < GS ? (TERMS - L0) : GS;
+    constexpr bool last = (CB == NCOL / 16 - 1) && (L0 + NG >= TERMS);
+    fold_group<L0, NG, CB, NCOL>(addr0 + CB * 16, tn, hi, lo, last, empty_bar);
+    if constexpr (L0 + NG < TERMS) readout_rec<TERMS, NCOL, CB, L0 + NG>(addr0, tn, hi, lo, empty_bar);
+    else if constexpr (CB + 1 < NCOL / 16) readout_rec<TERMS, NCOL, CB + 1, 0>(addr0, tn, hi, lo, empty_bar);
+}
+
+// One chunk readout of TERMS levels for the warp's NCOL columns, then the offsets are
+// removed and the carry of lo moved into hi (afterwards |lo| < 2^40).
+template <int TERMS, int NCOL>
+__device__ __forceinline__ void readout(uint32_t addr0, uint32_t tn, unsigned long long (&hi)[NCOL],
+                                        unsigned long long (&lo)[NCOL], uint64_t* empty_bar) {
+    readout_rec<TERMS, NCOL, 0, 0>(addr0, tn, hi, lo, empty_bar);
+    constexpr unsigned long long bh = magic_bias(0, TERMS, true), bl = magic_bias(0, TERMS, false);
 #pragma unroll
-    for (int j = 0; j < 16; ++j) {
+    for (int j = 0; j < NCOL; ++j) {
+        hi[j] -= bh;
+        lo[j] -= bl;
         const long long carry = (long long)lo[j] >> 40;
         hi[j] += (unsigned long long)carry;
         lo[j] -= (unsigned long long)carry << 40;
     }
 }
 
-__device__ __forceinline__ void readout16_terms(int terms, uint32_t base, unsigned long long (&hi)[16],
-                                                unsigned long long (&lo)[16], uint64_t* empty_bar) {
+template <int NCOL>
+__device__ __forceinline__ void readout_terms(int terms, uint32_t addr0, uint32_t tn, unsigned long long (&hi)[NCOL],
+                                              unsigned long long (&lo)[NCOL], uint64_t* empty_bar) {
     switch (terms) {
-        case 1: readout16<1>(base, hi, lo, empty_bar); break;
-        case 2: readout16<2>(base, hi, lo, empty_bar); break;
-        case 3: readout16<3>(base, hi, lo, empty_bar); break;
-        case 4: readout16<4>(base, hi, lo, empty_bar); break;
-        case 5: readout16<5>(base, hi, lo, empty_bar); break;
-        case 6: readout16<6>(base, hi, lo, empty_bar); break;
-        case 7: readout16<7>(base, hi, lo, empty_bar); break;
-        case 8: readout16<8>(base, hi, lo, empty_bar); break;
-        case 9: readout16<9>(base, hi, lo, empty_bar); break;
-        default: readout16<10>(base, hi, lo, empty_bar); break;
+        case 1: readout<1, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 2: readout<2, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 3: readout<3, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 4: readout<4, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 5: readout<5, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 6: readout<6, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 7: readout<7, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 8: readout<8, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        case 9: readout<9, NCOL>(addr0, tn, hi, lo, empty_bar); break;
+        default: readout<10, NCOL>(addr0, tn, hi, lo, empty_bar); break;
     }
 }
 
@@ -535,6 +538,7 @@ struct Sg2Dev {
     long long timeout;
     uint32_t tmem_cols;
     int acc_bufs, a_stages, b_stages;
+    int tn;                       // B rows per tile: 32 or 64
 };
 
 
@@ -591,6 +595,7 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity, volat
 // warp-uniform (lane 0 owns the timeout and the abort flag).
 __device__ __forceinline__ bool wait_phase_warp(uint64_t* bar, uint32_t parity, volatile int* abort_s, int* status,
                                                 long long timeout) {
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
     const long long t0 = clock64();
     while (true) {
         if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
@@ -610,14 +615,71 @@ __device__ __forceinline__ bool wait_phase_warp(uint64_t* bar, uint32_t parity, 
 
 // Tile t of the persistent loop -> (x = B-row tile, y = A-row tile, z = K split).
 struct TileCoord { int i0, j0, z; };
-__device__ __forceinline__ TileCoord tile_of(int t, int tiles_n, int tiles_m) {
+__device__ __forceinline__ TileCoord tile_of(int t, int tiles_n, int tiles_m, int tn) {
     TileCoord c;
     const int per_z = tiles_n * tiles_m;
     c.z = t / per_z;
     const int r = t - c.z * per_z;
     c.i0 = (r / tiles_n) * TM;
-    c.j0 = (r % tiles_n) * TN;
+    c.j0 = (r % tiles_n) * tn;
     return c;
+}
+
+// Epilogue role of one warp: NCOL = tn / 2 columns of each tile, for TMEM lanes
+// 32 * quarter ... + 31 (tile rows), chunk by chunk, then the tile's partial words or its
+// final values.
+template <int NCOL>
+__device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, uint64_t* tfull, uint64_t* tempty,
+                                              volatile int* abort_v, int quarter, int half, int lane) {
+    const int tn = 2 * NCOL;
+    const int tiles_n = (p.N + tn - 1) / tn, tiles_m = (p.M + TM - 1) / TM;
+    const int ntiles = tiles_n * tiles_m * p.splits;
+    const int cb = p.chunk_kb;
+    const uint32_t buf_cols = (uint32_t)(p.terms * tn);
+    int chunk = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+        const TileCoord c = tile_of(tile, tiles_n, tiles_m, tn);
+        if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+        const int kbeg = c.z * p.k_per_split;
+        const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
+        const int nchunks = (nkb + cb - 1) / cb;
+        unsigned long long hi[NCOL], lo[NCOL];
+#pragma unroll
+        for (int j = 0; j < NCOL; ++j) { hi[j] = 0; lo[j] = 0; }
+        for (int cc = 0; cc < nchunks; ++cc, ++chunk) {
+            const int buf = chunk % p.acc_bufs;
+            if (!wait_phase(tfull + buf, (chunk / p.acc_bufs) & 1, abort_v, p.status, p.timeout)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t base =
+                tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * buf_cols + (uint32_t)(half * NCOL);
+            readout_terms<NCOL>(p.terms, base, (uint32_t)tn, hi, lo, tempty + buf);
+        }
+        if (!ok) break;
+        const int i = c.i0 + quarter * 32 + lane;
+        const int jb = c.j0 + half * NCOL;
+        if (*abort_v || i >= p.M) continue;
+        if (p.splits > 1) {
+            long long* dst = p.part + (((int64_t)c.z * p.M + i) * p.N + jb) * 2;
+#pragma unroll
+            for (int j = 0; j < NCOL; ++j)
+                if (jb + j < p.N) { dst[2 * j] = (long long)hi[j]; dst[2 * j + 1] = (long long)lo[j]; }
+        } else {
+            const int ea = p.ea ? p.ea[i] : 0;
+            const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
+#pragma unroll
+            for (int j = 0; j < NCOL; ++j) {
+                const int gj = jb + j;
+                if (gj >= p.N || (p.lower_only && gj > i)) continue;
+                const double v = words_to_double((long long)hi[j], (long long)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                p.C[row * p.c_rs + (int64_t)gj * p.c_cs] =
+                    epilogue_value(v, p.alpha, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
+            }
+        }
+    }
 }
 
 __global__ void __launch_bounds__(W_THREADS, 1)
@@ -626,7 +688,9 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int AS = p.a_stages;
     const int BSN = p.b_stages;
-    const uint32_t b_stage_bytes = (uint32_t)p.sb * B_PLANE_BYTES;
+    const int tn = p.tn;
+    const uint32_t b_plane_bytes = (uint32_t)tn * KB * 2;
+    const uint32_t b_stage_bytes = (uint32_t)p.sb * b_plane_bytes;
     unsigned char* sA = smem;
     unsigned char* sB = sA + (size_t)AS * A_PLANE_BYTES;
     uint64_t* bars = (uint64_t*)(sB + (size_t)BSN * b_stage_bytes);
@@ -640,10 +704,10 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     __shared__ int abort_s;
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int tiles_n = (p.N + TN - 1) / TN, tiles_m = (p.M + TM - 1) / TM;
+    const int tiles_n = (p.N + tn - 1) / tn, tiles_m = (p.M + TM - 1) / TM;
     const int ntiles = tiles_n * tiles_m * p.splits;
     const int cb = p.chunk_kb;
-    const uint32_t buf_cols = (uint32_t)(p.terms * TN);
+    const uint32_t buf_cols = (uint32_t)(p.terms * tn);
 
     if (t == 0) {
         abort_s = 0;
@@ -669,7 +733,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         uint32_t a_it = 0, b_it = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const TileCoord c = tile_of(tile, tiles_n, tiles_m);
+            const TileCoord c = tile_of(tile, tiles_n, tiles_m, tn);
             if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
             const int kbeg = c.z * p.k_per_split;
             const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
@@ -702,11 +766,13 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         const uint64_t d0desc = sw128_desc(smem_addr(sA));
         const uint32_t a_lo0 = (uint32_t)d0desc, desc_hi = (uint32_t)(d0desc >> 32);
         const uint32_t b_lo0 = (uint32_t)sw128_desc(smem_addr(sB));
+        const int wmax = 256 / tn;                                     // levels per MMA window
+        const uint32_t b_win = (uint32_t)wmax * (b_plane_bytes >> 4);  // second window's B offset
         uint32_t a_it = 0, b_it = 0;
         int chunk = 0, buf = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const TileCoord c = tile_of(tile, tiles_n, tiles_m);
+            const TileCoord c = tile_of(tile, tiles_n, tiles_m, tn);
             if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
             const int kbeg = c.z * p.k_per_split;
             const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
@@ -734,23 +800,22 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                         break;
                     }
                     tc_fence_after();
-                    // Plane pa against B levels 0 .. nwin-1: one MMA for the first eight levels
-                    // (N = 32 per level), a second for levels 8 and 9. Descriptors are built from
+                    // Plane pa against B levels 0 .. nwin-1: one MMA per window of up to 256 / tn
+                    // levels (N = tn per level), at most two windows. Descriptors are built from
                     // precomputed words: the K step adds 32 bytes (2 units) to the start address.
                     const int nwin = min(p.sb, p.terms - pa);
                     if (nwin > 0) {
-                        const int n1 = min(8, nwin), n2 = nwin - n1;
+                        const int n1 = min(wmax, nwin), n2 = nwin - n1;
                         const uint32_t a_lo = a_lo0 + (uint32_t)as * (A_PLANE_BYTES >> 4);
-                        const uint32_t d = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * TN);
-                        const uint32_t id1 = idesc_bf16(TM, n1 * TN), id2 = idesc_bf16(TM, (n2 > 0 ? n2 : 1) * TN);
+                        const uint32_t d = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * tn);
+                        const uint32_t id1 = idesc_bf16(TM, n1 * tn), id2 = idesc_bf16(TM, (n2 > 0 ? n2 : 1) * tn);
 #pragma unroll
                         for (int kk = 0; kk < KB / 16; ++kk) {
                             const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
                             const uint64_t ad = make_desc(a_lo + 2 * kk, desc_hi);
                             umma_bf16_lane0(d, ad, make_desc(b_lo + 2 * kk, desc_hi), id1, acc);
                             if (n2 > 0)
-                                umma_bf16_lane0(d + 8 * TN, ad, make_desc(b_lo + 8 * (B_PLANE_BYTES >> 4) + 2 * kk, desc_hi),
-                                                id2, acc);
+                                umma_bf16_lane0(d + 256, ad, make_desc(b_lo + b_win + 2 * kk, desc_hi), id2, acc);
                         }
                     }
                     umma_commit_lane0(emptyA + as);
@@ -767,54 +832,10 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         }
     } else {
         // ---------------- epilogue: warps 2..9; warp w reads TMEM lanes 32 * (w % 4) ... + 31
-        // (the lane quarter it may access) and columns 16 * half ... + 15 of each level.
+        // (the lane quarter it may access) and columns tn/2 * half ... of each level.
         const int quarter = warp & 3, half = (warp - 2) >> 2;
-        int chunk = 0;
-        bool ok = true;
-        for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const TileCoord c = tile_of(tile, tiles_n, tiles_m);
-            if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
-            const int kbeg = c.z * p.k_per_split;
-            const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
-            const int nchunks = (nkb + cb - 1) / cb;
-            unsigned long long hi[16], lo[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
-            for (int cc = 0; cc < nchunks; ++cc, ++chunk) {
-                const int buf = chunk % p.acc_bufs;
-                if (!wait_phase(tfull + buf, (chunk / p.acc_bufs) & 1, abort_v, p.status, p.timeout)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t base =
-                    tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * buf_cols + (uint32_t)(half * 16);
-                readout16_terms(p.terms, base, hi, lo, tempty + buf);
-            }
-            if (!ok) break;
-            const int i = c.i0 + quarter * 32 + lane;
-            const int jb = c.j0 + half * 16;
-            if (!*abort_v && i < p.M) {
-                if (p.splits > 1) {
-                    long long* dst = p.part + (((int64_t)c.z * p.M + i) * p.N + jb) * 2;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (jb + j < p.N) { dst[2 * j] = (long long)hi[j]; dst[2 * j + 1] = (long long)lo[j]; }
-                } else {
-                    const int ea = p.ea ? p.ea[i] : 0;
-                    const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int gj = jb + j;
-                        if (gj >= p.N || (p.lower_only && gj > i)) continue;
-                        const double v = words_to_double((long long)hi[j], (long long)lo[j],
-                                                         ea + (p.eb ? p.eb[gj] : 0) - 86);
-                        p.C[row * p.c_rs + (int64_t)gj * p.c_cs] = epilogue_value(
-                            v, p.alpha, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
-                    }
-                }
-            }
-        }
+        if (tn == 64) epilogue_role<32>(p, tmem, tfull, tempty, abort_v, quarter, half, lane);
+        else epilogue_role<16>(p, tmem, tfull, tempty, abort_v, quarter, half, lane);
     }
     tc_fence_before();
     __syncthreads();
@@ -944,8 +965,8 @@ static int chunk_for(const SlicedGemm& g) {
     return kc;
 }
 
-static int choose_splits(int M, int N, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
-    const int tiles = ((M + TM - 1) / TM) * ((N + TN - 1) / TN);
+static int choose_splits(int M, int N, int tn, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
+    const int tiles = ((M + TM - 1) / TM) * ((N + tn - 1) / tn);
     int splits = 1;
     const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
     if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
@@ -971,13 +992,17 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
                            g.terms <= 10 && g.terms <= g.b.s && g.b.cols == K && g.a.ld % 64 == 0 &&
                            g.b.ld % 64 == 0 && g.a.ld >= K && g.b.ld >= K;
     if (!shapes_ok || pipelined_disabled()) return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
+    // 64 B rows per tile when the levels of one accumulator set fit TMEM at that width
+    // (terms * 64 <= 512 columns): half the A-plane reads per flop and twice the MMA work
+    // per pipeline stage; 32 otherwise.
+    const int tn = (g.terms * 64 <= 512 && N > 32) ? 64 : 32;
     CUtensorMap mapA, mapB;
-    if (!make_stack_map(&mapA, g.a, TM, 1) || !make_stack_map(&mapB, g.b, TN, g.b.s))
+    if (!make_stack_map(&mapA, g.a, TM, 1) || !make_stack_map(&mapB, g.b, tn, g.b.s))
         return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
     const int Kp = (K + KB - 1) / KB * KB;
     const int kchunk = chunk_for(g);
     int kps = 0;
-    const int splits = choose_splits(M, N, Kp, scratch_bytes, kchunk, &kps);
+    const int splits = choose_splits(M, N, tn, Kp, scratch_bytes, kchunk, &kps);
     Sg2Dev p;
     p.M = M; p.N = N; p.Kp = Kp; p.sa = g.a.s; p.sb = g.b.s; p.terms = g.terms; p.k_per_split = kps;
     p.chunk_kb = kchunk / KB;
@@ -988,13 +1013,14 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     p.lower_only = g.lower_only ? 1 : 0;
     p.status = status;
     p.timeout = 4000000000ll;
-    p.acc_bufs = (2 * g.terms * TN <= 512) ? 2 : 1;
+    p.tn = tn;
+    p.acc_bufs = (2 * g.terms * tn <= 512) ? 2 : 1;
     p.tmem_cols = 32;
-    while (p.tmem_cols < (uint32_t)(p.acc_bufs * g.terms * TN)) p.tmem_cols <<= 1;
+    while (p.tmem_cols < (uint32_t)(p.acc_bufs * g.terms * tn)) p.tmem_cols <<= 1;
     // Split shared memory between the A-plane ring (sa slots per K block) and the B-stage
     // ring (one stage per K block) so that the producer can run as many K blocks ahead as
     // possible: maximise min(b_stages, a_stages / sa).
-    const size_t b_stage = (size_t)g.b.s * B_PLANE_BYTES;
+    const size_t b_stage = (size_t)g.b.s * tn * KB * 2;
     const size_t fixed = 1024 + (2 * W_MAX_A_STAGES + 2 * W_MAX_B_STAGES + 4) * 8 + 16;
     const size_t budget = 220 * 1024 - fixed;
     int best_bs = 0, best_as = 0;
@@ -1012,7 +1038,7 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     cudaError_t e = cudaFuncSetAttribute(sliced_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     p.splits = splits;
-    const int ntiles = ((N + TN - 1) / TN) * ((M + TM - 1) / TM) * splits;
+    const int ntiles = ((N + tn - 1) / tn) * ((M + TM - 1) / TM) * splits;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
