@@ -154,30 +154,33 @@ __global__ void qr_extract_r_kernel(const double* S, int m, int64_t lds, double*
 
 // ---------------------------------------------------------------------------------
 // Persistent form: one cooperative launch for all m steps. CTA b keeps columns
-// [b*cpc, b*cpc + cpc) of S^* (rows of S) in shared memory for the whole
-// factorization. Per step j: every CTA publishes the best remaining column norm it
-// owns and arrives on a grid-wide counter; after all have arrived each CTA picks the
-// global pivot (largest norm, lowest index on ties), reads the pivot column from global
-// memory (every CTA writes its updated columns back after each step), forms the
-// reflector itself and applies it to its active columns, downdating the norms. Columns never move: the
-// pivot column is retired and R[:, j] is the retired column's first j+1 entries.
-// Every wait has a clock deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all
-// CTAs leave their loops.
-// ---------------------------------------------------------------------------------
-constexpr int PQ_THREADS = 256;
+// [b*cpc, b*cpc + cpc) of S^* (rows of S) in shared memory for the whole factorization,
+// one warp per column. A step costs one grid-wide exchange. Before arriving for step j,
+// each CTA publishes its candidate: its remaining column with the largest downdated norm
+// (lowest index on ties), fully updated through step j-1, copied to the CTA's slot in
+// global memory together with its exactly recomputed tail norm. After everyone has
+// arrived, each CTA picks the global pivot among the candidates (largest norm, lowest
+// column index on ties), reads that column from its owner's slot, forms the reflector
+// itself (all CTAs compute bitwise the same alpha, beta and v) and applies it: first the
+// row-j entry of each active column, so that the norms are downdated (LAPACK-style) and
+// the next candidate is known early; the candidate's full update, slot copy and arrival
+// follow, and the other columns' updates overlap the wait. Columns never move: the pivot
+// column is retired and R[:, j] is the retired column's first j+1 entries. Slots and
+// candidates alternate between two buffers by step parity. Every wait has a clock
+// deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all CTAs leave their loops.
+constexpr int PQ_THREADS = 128;
 constexpr int PQ_WARPS = PQ_THREADS / 32;
 constexpr int PQ_MAXC = 32;
+constexpr int PQ_MAX_G = 256;
 
 struct PqrDev {
     double* S; int m, l; int64_t lds;
     double* R; int32_t* perm;
     int cpc;
-    double* vbuf;            // 2 x l
-    double* scal;            // 2 x 2
-    double* bval;            // 2 x G
-    int* bidx;               // 2 x G
+    double* slots;           // 2 x G x l: candidate columns by step parity
+    double* bval;            // 2 x G: candidate tail norms
+    int* bidx;               // 2 x G: candidate column indices (m = none)
     unsigned int* counter;   // arrivals (monotonic)
-    unsigned int* flags;     // m: reflector j published
     int* abort_flag;
     int* status;
     long long timeout;
@@ -188,22 +191,52 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
 }
 
 // Bounded wait until *p >= target (or the abort flag is raised). Returns false on abort.
+// The counter is polled back to back; the abort flag and the deadline every 64 polls.
 __device__ bool wait_geq(const unsigned int* p, unsigned int target, int* abort_flag, int* status, long long timeout) {
     const long long t0 = clock64();
-    while (ld_acquire(p) < target) {
-        if (*(volatile int*)abort_flag) return false;
-        if (clock64() - t0 > timeout) {
-            atomicExch(abort_flag, 1);
-            set_status(status, RTPROJ_ETIMEOUT);
-            return false;
+    for (unsigned int it = 1;; ++it) {
+        if (ld_acquire(p) >= target) return true;
+        if ((it & 63) == 0) {
+            if (*(volatile int*)abort_flag) return false;
+            if (clock64() - t0 > timeout) {
+                atomicExch(abort_flag, 1);
+                set_status(status, RTPROJ_ETIMEOUT);
+                return false;
+            }
         }
     }
-    return true;
+}
+
+// Candidate of this CTA for step j + 1 (parity par1): the column owned by warp `warp`
+// at local index q (or none when q < 0). The warp copies rows j+1 .. l-1 to the slot,
+// recomputes the tail norm exactly, publishes (norm, index) and arrives.
+__device__ __forceinline__ void publish_candidate(const PqrDev& p, int b, int G, int par1, int j, int q,
+                                                  const double* col, double* vn1, double* vn2, int lane) {
+    double nrm = -1.0;
+    if (q >= 0) {
+        double* slot = p.slots + ((int64_t)par1 * G + b) * p.l;
+        double s = 0.0;
+        for (int i = j + 1 + lane; i < p.l; i += 32) {
+            const double x = col[i];
+            slot[i] = x;
+            s = fma(x, x, s);
+        }
+        s = warp_sum(s);
+        nrm = sqrt(s);
+        if (lane == 0) { vn1[q] = nrm; vn2[q] = nrm; }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        p.bval[par1 * G + b] = nrm;
+        p.bidx[par1 * G + b] = q >= 0 ? b * p.cpc + q : p.m;
+        red_release_add(p.counter, 1u);
+    }
 }
 
 __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) {
@@ -211,12 +244,13 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     const int l = p.l, m = p.m, cpc = p.cpc;
     double* cols = smem_d;                 // cpc x l
     double* v = cols + (size_t)cpc * l;    // l
-    __shared__ double vn1[PQ_MAXC], vn2[PQ_MAXC];
+    __shared__ double vn1[PQ_MAXC], vn2[PQ_MAXC], wq[PQ_MAXC];
     __shared__ int posq[PQ_MAXC];
+    __shared__ unsigned char doneq[PQ_MAXC];
     __shared__ double redv[PQ_WARPS];
     __shared__ int redi[PQ_WARPS];
-    __shared__ int piv_s, ok_s;
-    __shared__ double beta_s;
+    __shared__ int piv_s, owner_s, ok_s, cand_s;
+    __shared__ double norm_s;
     const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int c0 = b * cpc;
     const int nc = max(0, min(cpc, m - c0));
@@ -232,22 +266,24 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         if (lane == 0) { vn1[q] = sqrt(s); vn2[q] = sqrt(s); posq[q] = -1; }
     }
     __syncthreads();
+    // candidate for step 0: whole columns (rows 0 .. l-1)
+    if (t == 0) {
+        double best = -1.0;
+        int bq = -1;
+        for (int q = 0; q < nc; ++q)
+            if (vn1[q] > best) { best = vn1[q]; bq = q; }
+        cand_s = bq;
+    }
+    __syncthreads();
+    if (warp == 0) publish_candidate(p, b, G, 0, -1, cand_s, cand_s >= 0 ? cols + (size_t)cand_s * l : nullptr,
+                                     vn1, vn2, lane);
 
     bool alive = true;
     for (int j = 0; j < m && alive; ++j) {
         const int par = j & 1;
-        // 1. publish the local best, arrive, wait for everyone
-        if (t == 0) {
-            double best = -1.0;
-            int bi = m;
-            for (int q = 0; q < nc; ++q)
-                if (posq[q] < 0 && (vn1[q] > best)) { best = vn1[q]; bi = c0 + q; }
-            p.bval[par * G + b] = best;
-            p.bidx[par * G + b] = bi;
-            __threadfence();
-            atomicAdd(p.counter, 1u);
-            ok_s = wait_geq(p.counter, (unsigned int)(j + 1) * (unsigned int)G, p.abort_flag, p.status, p.timeout);
-        }
+        // 1. wait for every candidate of step j
+        if (t == 0) ok_s = wait_geq(p.counter, (unsigned int)(j + 1) * (unsigned int)G, p.abort_flag, p.status,
+                                     p.timeout);
         __syncthreads();
         if (!ok_s) { alive = false; break; }
         // 2. global pivot: largest norm, lowest column index on ties
@@ -272,77 +308,95 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             for (int w = 1; w < PQ_WARPS; ++w)
                 if (redv[w] > bb || (redv[w] == bb && redi[w] < ii)) { bb = redv[w]; ii = redi[w]; }
             piv_s = ii < m ? ii : -1;
+            owner_s = ii < m ? ii / cpc : -1;
+            norm_s = bb;                                   // the pivot column's tail norm
         }
         __syncthreads();
         const int piv = piv_s;
-        if (piv < 0) { alive = false; break; }     // cannot happen while columns remain
-        // 3. every CTA forms the reflector itself from the pivot column, read from global
-        //    memory (each CTA writes its active columns back after every update), so the
-        //    reflector needs no second broadcast. All CTAs sum in the same order and get
-        //    bitwise the same alpha, beta and v.
-        const int owner = piv / cpc;
-        {
-            const double* pc = p.S + (int64_t)piv * p.lds;
-            double s = 0.0;
-            for (int i = j + t; i < l; i += PQ_THREADS) {
-                const double x = __ldcg(pc + i);
-                v[i - j] = x;
-                s = fma(x, x, s);
-            }
-            s = warp_sum(s);
-            if (lane == 0) redv[warp] = s;
-            __syncthreads();
-            if (t == 0) {
-                double nx2 = 0.0;
-                for (int w = 0; w < PQ_WARPS; ++w) nx2 += redv[w];
-                const double nx = sqrt(nx2);
-                const double x0 = v[0];
-                double alpha = 0.0, beta = 0.0;
-                if (nx > 0.0) {
-                    alpha = x0 >= 0.0 ? -nx : nx;
-                    beta = 1.0 / (nx * (nx + fabs(x0)));
-                }
-                v[0] = x0 - alpha;
-                beta_s = beta;
-                if (owner == b) {
-                    const int q = piv - c0;
-                    cols[(size_t)q * l + j] = alpha;
-                    posq[q] = j;
-                    p.perm[j] = piv;
-                }
-            }
-            __syncthreads();
+        if (piv < 0) { alive = false; break; }             // cannot happen while columns remain
+        const int owner = owner_s;
+        const double nx = norm_s;
+        // 3. the reflector from the owner's slot (rows j .. l-1); every thread derives alpha
+        //    and beta from the published norm and the slot's first entry
+        const double* slot = p.slots + ((int64_t)par * G + owner) * l;
+        const double x0 = __ldcg(slot + j);
+        double alpha = 0.0, beta = 0.0;
+        if (nx > 0.0) {
+            alpha = x0 >= 0.0 ? -nx : nx;
+            beta = 1.0 / (nx * (nx + fabs(x0)));
         }
-        // 4. apply I - beta v v^* to the active columns, downdate their norms
-        const double beta = beta_s;
+        for (int i = j + t; i < l; i += PQ_THREADS) v[i - j] = i == j ? x0 - alpha : __ldcg(slot + i);
+        if (t == 0 && owner == b) {
+            const int q = piv - c0;
+            cols[(size_t)q * l + j] = alpha;
+            posq[q] = j;
+            p.perm[j] = piv;
+        }
+        __syncthreads();
+        const int len = l - j;
+        // 4a. row j of each active column and its downdated norm; a column whose downdate
+        //     would lose more than half the digits is updated in full here and its norm
+        //     recomputed, so that every norm is current when the next candidate is chosen
         for (int q = warp; q < nc; q += PQ_WARPS) {
             if (posq[q] >= 0) continue;
             double* c = cols + (size_t)q * l + j;
-            const int len = l - j;
+            const double cj = c[0];
             double w = 0.0;
             for (int i = lane; i < len; i += 32) w = fma(v[i], c[i], w);
             w = warp_sum(w) * beta;
-            for (int i = lane; i < len; i += 32) c[i] = fma(-w, v[i], c[i]);
-            __syncwarp();
-            const double r = c[0];
+            const double r = fma(-w, v[0], cj);
             const double n1 = vn1[q];
+            bool recompute = false;
+            double tmp = 0.0;
             if (n1 != 0.0) {
-                double tmp = fabs(r) / n1;
+                tmp = fabs(r) / n1;
                 tmp = fmax(0.0, (1.0 + tmp) * (1.0 - tmp));
                 const double ratio = n1 / vn2[q];
-                if (tmp * ratio * ratio <= 1.4901161193847656e-08) {
-                    double s2 = 0.0;
-                    for (int i = 1 + lane; i < len; i += 32) s2 = fma(c[i], c[i], s2);
-                    s2 = warp_sum(s2);
-                    if (lane == 0) { vn1[q] = sqrt(s2); vn2[q] = sqrt(s2); }
-                } else if (lane == 0) {
-                    vn1[q] = n1 * sqrt(tmp);
-                }
+                recompute = tmp * ratio * ratio <= 1.4901161193847656e-08;
             }
-            __syncwarp();
-            // write the updated tail back for the next pivot search
-            double* gcol = p.S + (int64_t)(c0 + q) * p.lds;
-            for (int i = lane; i < len; i += 32) gcol[j + i] = c[i];
+            if (recompute) {
+                double s2 = 0.0;
+                for (int i = 1 + lane; i < len; i += 32) {
+                    const double x = fma(-w, v[i], c[i]);
+                    c[i] = x;
+                    s2 = fma(x, x, s2);
+                }
+                s2 = warp_sum(s2);
+                if (lane == 0) { vn1[q] = sqrt(s2); vn2[q] = sqrt(s2); }
+            } else if (lane == 0 && n1 != 0.0) {
+                vn1[q] = n1 * sqrt(tmp);
+            }
+            if (lane == 0) { c[0] = r; wq[q] = w; doneq[q] = recompute ? 1 : 0; }
+        }
+        __syncthreads();
+        // 4b. the next candidate (largest downdated norm, lowest index on ties); its warp
+        //     finishes its update first, publishes it and arrives
+        if (t == 0) {
+            double bestn = -1.0;
+            int bq = -1;
+            for (int q = 0; q < nc; ++q)
+                if (posq[q] < 0 && vn1[q] > bestn) { bestn = vn1[q]; bq = q; }
+            cand_s = bq;
+        }
+        __syncthreads();
+        const int cand = cand_s;
+        const int cand_warp = cand >= 0 ? cand % PQ_WARPS : 0;
+        if (warp == cand_warp) {
+            if (cand >= 0 && !doneq[cand]) {
+                double* c = cols + (size_t)cand * l + j;
+                const double w = wq[cand];
+                for (int i = 1 + lane; i < len; i += 32) c[i] = fma(-w, v[i], c[i]);
+                __syncwarp();
+            }
+            publish_candidate(p, b, G, par ^ 1, j, cand, cand >= 0 ? cols + (size_t)cand * l : nullptr, vn1, vn2,
+                              lane);
+        }
+        // 4c. the remaining columns (overlapping the other CTAs' arrivals)
+        for (int q = warp; q < nc; q += PQ_WARPS) {
+            if (posq[q] >= 0 || q == cand || doneq[q]) continue;
+            double* c = cols + (size_t)q * l + j;
+            const double w = wq[q];
+            for (int i = 1 + lane; i < len; i += 32) c[i] = fma(-w, v[i], c[i]);
         }
         __syncthreads();
     }
@@ -383,7 +437,11 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
     return cudaGetLastError();
 }
 
-size_t pivoted_qr_work_doubles(int m, int l) { return (size_t)3 * m + 3 * (size_t)l + 2048; }
+size_t pivoted_qr_work_doubles(int m, int l) {
+    const size_t steps = (size_t)3 * m + 3 * (size_t)l + 2048;                       // per-step form
+    const size_t persistent = (size_t)2 * PQ_MAX_G * l + 4 * (size_t)PQ_MAX_G + 64;   // slots, candidates
+    return steps > persistent ? steps : persistent;
+}
 
 cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
                        double* work, int* status, cudaStream_t s) {
@@ -396,8 +454,8 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
     if (coop && sms > 0) {
         int cpc = (m + sms - 1) / sms;
         const size_t smem = ((size_t)cpc * l + l) * sizeof(double);
-        if (cpc <= PQ_MAXC && smem + 4096 <= (size_t)smem_optin) {
-            const int G = (m + cpc - 1) / cpc;
+        const int G = (m + cpc - 1) / cpc;
+        if (cpc <= PQ_MAXC && G <= PQ_MAX_G && smem + 4096 <= (size_t)smem_optin) {
             cudaFuncSetAttribute(qr_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int per_sm = 0;
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_persistent_kernel, PQ_THREADS, smem);
@@ -405,17 +463,15 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 PqrDev p;
                 p.S = S; p.m = m; p.l = l; p.lds = lds; p.R = R; p.perm = perm; p.cpc = cpc;
                 double* w = work;
-                p.vbuf = w;                     w += 2 * (size_t)l;
-                p.scal = w;                     w += 4;
+                p.slots = w;                    w += (size_t)2 * G * l;
                 p.bval = w;                     w += 2 * (size_t)G;
                 p.bidx = (int*)w;               w += G;          // 2G ints
-                unsigned int* ctr = (unsigned int*)w;            // counter, abort, flags[m]
+                unsigned int* ctr = (unsigned int*)w;            // counter, abort
                 p.counter = ctr;
                 p.abort_flag = (int*)(ctr + 1);
-                p.flags = ctr + 2;
                 p.status = status;
                 p.timeout = 4000000000ll;
-                cudaError_t e = cudaMemsetAsync(ctr, 0, (size_t)(m + 2) * sizeof(unsigned int), s);
+                cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
                 if (e != cudaSuccess) return e;
                 void* args[] = {&p};
                 e = cudaLaunchCooperativeKernel((const void*)qr_persistent_kernel, dim3(G), dim3(PQ_THREADS), args,
