@@ -174,6 +174,10 @@ rtproj_status mixed_prepare_a(rtproj_ctx* h) {
     MX_CHECK(transpose_planes(h->As, h->Ats, h->stream));
     MX_CHECK(fill_int(h->Ats.e, (int)h->n, 0, h->stream));
     phase_end(h, RTPROJ_PHASE_SLICE);
+    // A is read only here in this form: remember whether it held non-finite entries, so
+    // that precondition reports it without reading A again
+    MX_CHECK(cudaMemcpyAsync(&h->a_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    MX_CHECK(cudaStreamSynchronize(h->stream));
     return RTPROJ_OK;
 }
 

@@ -10,6 +10,8 @@
 // The digits come from integer operations on the float64 bit pattern (no FP64 pipe).
 #include "rtproj_internal.cuh"
 
+#include <type_traits>
+
 namespace rtp {
 namespace {
 
@@ -157,6 +159,117 @@ __global__ void fill_int_kernel(int32_t* e, int n, int v) {
     if (i < n) e[i] = v;
 }
 
+// ---------------------------------------------------------------------------------
+// Contiguous rows (x_cs = 1, no row index, no column exponents): the same digits, from
+// integer operations only. One CTA of SLF_THREADS per row: the row maximum of |x| is the
+// maximum of the bit patterns with the sign cleared (their order is that of the values),
+// non-finite entries are those with an all-ones exponent field; then every thread turns
+// eight consecutive entries into eight digits per plane and stores them as one 16-byte
+// vector per plane. S is a template parameter so the digits stay in registers; F fits
+// 64 bits for S <= 8.
+constexpr int SLF_THREADS = 512;
+
+__device__ __forceinline__ unsigned long long u64_max(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+// Bits of the bfloat16 holding the integer d, |d| <= 256: d is exact in float32 (one add
+// of 1.5 * 2^23 and one subtract), and the float's upper half is the bfloat16.
+__device__ __forceinline__ uint32_t bf16_bits_of_int(int d) {
+    const float f = __fsub_rn(__int_as_float(0x4B400000 + d), 12582912.0f);
+    return __float_as_uint(f) >> 16;
+}
+
+// Digits of one entry (bit pattern `bits`) for the shift base of its row.
+template <int S>
+__device__ __forceinline__ void entry_digits(unsigned long long bits, int shift_base, int (&dig)[S]) {
+    using U = typename std::conditional<(S <= 8), unsigned long long, unsigned __int128>::type;
+    constexpr int kMaxShift = S <= 8 ? 63 : 127;
+    const bool neg = (bits >> 63) != 0;
+    int E = (int)((bits >> 52) & 0x7FFull);
+    unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+    if (E == 0) E = 1; else M |= 1ull << 52;
+    if (E == 0x7FF) M = 0;                        // non-finite: flagged by the caller, digits 0
+    const int sh = E - 1075 + shift_base;
+    U F = 0;
+    if (M != 0) {
+        if (sh >= 0) {
+            F = sh < kMaxShift - 52 ? ((U)M << sh) : (U)0;
+        } else if (sh > -64) {
+            const int rs = -sh;
+            unsigned long long f = M >> rs;
+            if ((M >> (rs - 1)) & 1ull) f += 1ull;
+            F = (U)f;
+        }
+    }
+    int carry = 0;
+#pragma unroll
+    for (int p = S - 1; p >= 1; --p) {
+        int b = (int)(unsigned)(F & 0xFFu) + carry;
+        F >>= 8;
+        carry = b >= 128 ? 1 : 0;
+        b -= carry * 256;
+        dig[p] = neg ? -b : b;
+    }
+    const int b0 = (int)(unsigned)F + carry;
+    dig[0] = neg ? -b0 : b0;
+}
+
+template <int S>
+__global__ void __launch_bounds__(SLF_THREADS) slice_rows_fast_kernel(SliceDev a) {
+    __shared__ unsigned long long smax[SLF_THREADS / 32];
+    __shared__ int sbad[SLF_THREADS / 32];
+    __shared__ int base_s;
+    const int r = blockIdx.x, t = threadIdx.x;
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.X + (int64_t)r * a.x_rs);
+    unsigned long long mx = 0;
+    int bad = 0;
+    for (int c = t; c < a.cols; c += SLF_THREADS) {
+        const unsigned long long u = __ldg(row + c) & 0x7FFFFFFFFFFFFFFFull;
+        if (u >= 0x7FF0000000000000ull) bad = 1;
+        else mx = u64_max(mx, u);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = u64_max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((t & 31) == 0) { smax[t >> 5] = mx; sbad[t >> 5] = bad; }
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long m2 = 0;
+        int b2 = 0;
+        for (int w = 0; w < SLF_THREADS / 32; ++w) { m2 = u64_max(m2, smax[w]); b2 |= sbad[w]; }
+        // e with max < 2^e <= 2 max (the frexp exponent): E - 1022 for a normal maximum,
+        // from the leading bit of the mantissa for a subnormal one, 0 for a zero row
+        int ex = 0;
+        const int E = (int)(m2 >> 52);
+        if (E > 0) ex = E - 1022;
+        else if (m2 != 0) ex = (64 - __clzll((long long)m2)) - 1074;
+        a.e[r] = ex;
+        base_s = 7 + 8 * (S - 1) - ex;
+        if (b2) set_status(a.status, RTPROJ_ENONFINITE);
+    }
+    __syncthreads();
+    const int base = base_s;
+    __nv_bfloat16* drow = a.d + (int64_t)r * a.ld;
+    for (int c0 = 8 * t; c0 < a.ld; c0 += 8 * SLF_THREADS) {
+        uint32_t w[S][4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            int d0[S], d1[S];
+            const int c = c0 + 2 * h;
+            entry_digits<S>(c < a.cols ? __ldg(row + c) : 0ull, base, d0);
+            entry_digits<S>(c + 1 < a.cols ? __ldg(row + c + 1) : 0ull, base, d1);
+#pragma unroll
+            for (int p = 0; p < S; ++p) w[p][h] = bf16_bits_of_int(d0[p]) | (bf16_bits_of_int(d1[p]) << 16);
+        }
+#pragma unroll
+        for (int p = 0; p < S; ++p)
+            *reinterpret_cast<uint4*>(drow + (int64_t)p * a.ps + c0) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+    }
+}
+
 }  // namespace
 
 cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx, const int32_t* cexp,
@@ -167,7 +280,25 @@ cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_
     a.X = X; a.x_rs = x_rs; a.x_cs = x_cs; a.rowidx = rowidx; a.cexp = cexp;
     a.rows = st.rows; a.cols = st.cols; a.s = st.s;
     a.d = st.d; a.ld = st.ld; a.ps = st.plane_stride; a.e = st.e; a.status = status;
-    slice_rows_kernel<<<st.rows, SL_THREADS, 0, s>>>(a);
+    // 16-byte vector stores need 8-entry aligned planes and rows
+    const bool fast = x_cs == 1 && !rowidx && !cexp && st.ld % 8 == 0 && st.plane_stride % 8 == 0 &&
+                      ((uintptr_t)st.d & 15) == 0 && ((uintptr_t)X & 7) == 0;
+    if (fast) {
+        switch (st.s) {
+            case 1: slice_rows_fast_kernel<1><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 2: slice_rows_fast_kernel<2><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 3: slice_rows_fast_kernel<3><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 4: slice_rows_fast_kernel<4><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 5: slice_rows_fast_kernel<5><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 6: slice_rows_fast_kernel<6><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 7: slice_rows_fast_kernel<7><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 8: slice_rows_fast_kernel<8><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            case 9: slice_rows_fast_kernel<9><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+            default: slice_rows_fast_kernel<10><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
+        }
+    } else {
+        slice_rows_kernel<<<st.rows, SL_THREADS, 0, s>>>(a);
+    }
     note_launch();
     return cudaGetLastError();
 }

@@ -340,7 +340,11 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     h->l = l;
     RT_CHECK(cudaEventRecord(h->ev0, s));
     RT_CHECK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
-    RT_CHECK(check_finite(h->A, h->lda, m, (int)h->n, h->status, s));
+    if (h->opts.mode == RTPROJ_MIXED_REFINED) {
+        if (h->a_status != RTPROJ_OK) return (rtproj_status)h->a_status;   // found when A was sliced
+    } else {
+        RT_CHECK(check_finite(h->A, h->lda, m, (int)h->n, h->status, s));
+    }
     // 1. S = A G (Eq. 12)
     phase_begin(h, RTPROJ_PHASE_SKETCH);
     rtproj_status st = h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_sketch(h, seed, l, h->S, l)

@@ -206,6 +206,7 @@ struct rtproj_ctx {
     rtp::PhaseTimer timer;
     int64_t l = 0;
     int preconditioned = 0;
+    int a_status = 0;            // mixed form: status of slicing A at create (non-finite entries)
     float ms_pre = 0.f;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };

@@ -160,3 +160,16 @@ def test_pipelined_and_synchronous_sliced_gemm_agree_bitwise(m, n, l, k, monkeyp
             out[flag] = (S, Z.cpu().numpy(), ROW.cpu().numpy(), H.cpu().numpy())
     for a, b in zip(out["0"], out["1"]):
         np.testing.assert_array_equal(a, b)
+
+
+def test_nonfinite_entry_of_a_is_reported_by_precondition():
+    """A is sliced once, at create; a non-finite entry found there makes precondition
+    return RTPROJ_ENONFINITE without reading A again."""
+    torch = torch_cuda()
+    rt = rt_module()
+    A = workloads.haar_spectrum_matrix(37, 1000, 1e-3, 5)
+    A[11, 503] = np.inf
+    with _mixed(rt, torch, A, 41, 2) as P:
+        with pytest.raises(rt.RtprojError) as e:
+            P.precondition(seed=1, l=41)
+        assert e.value.code == 5
