@@ -65,7 +65,8 @@ __global__ void tri_diag_inv_kernel(const double* T, int64_t t_rs, int64_t t_cs,
 // contribution from the rows still to be solved. Three barriers per block.
 template <bool lower>
 __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int64_t t_rs, int64_t t_cs, int m,
-                                                            double* B, int64_t b_rs, int ncols, const double* Dinv) {
+                                                            double* B, int64_t b_rs, int ncols, const double* Dinv,
+                                                            int rhs_lower) {
     extern __shared__ double x[];   // m * TRSM_NB
     const int j0 = blockIdx.x * TRSM_NB;
     const int nc = min(TRSM_NB, ncols - j0);
@@ -76,7 +77,10 @@ __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int
     }
     __syncthreads();
     const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
-    for (int bi = 0; bi < nblk; ++bi) {
+    // A lower-triangular right-hand side (zero above its diagonal) gives a lower-triangular
+    // solution of a lower system: rows above this CTA's first column stay zero.
+    const int bi0 = (lower && rhs_lower) ? min(j0, m) / TRSM_BS : 0;
+    for (int bi = bi0; bi < nblk; ++bi) {
         const int blk = lower ? bi : nblk - 1 - bi;
         const int r0 = blk * TRSM_BS;
         const int bs = min(TRSM_BS, m - r0);
@@ -234,10 +238,177 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double* X, int m, int 
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Persistent blocked Cholesky: one cooperative launch for all panels of 32 columns.
+// Per panel p0: (A) CTA 0 factors the diagonal block in shared memory and forms its
+// inverse Z = L_pp^{-1} in the same right-looking sweep (Gauss-Jordan on the identity);
+// (B) every warp of the grid solves panel rows: L[r][p0..] = X[r][p0..] Z^*; (C) all CTAs
+// update the trailing lower triangle on 16 x 16 tiles. A grid-wide counter separates the
+// phases; every wait is bounded (RTPROJ_ETIMEOUT). The reciprocal square root of each
+// pivot starts from the float32 estimate and takes two Newton steps in float64
+// (y <- y (3 - d y^2) / 2), which doubles the correct bits each time.
+constexpr int CHP_THREADS = 256;
+constexpr int CHP_NB = 32;
+constexpr int CHP_TILE = 16;
+
+struct CholPDev {
+    double* X; int m;
+    double* zbuf;            // 32 x 32: Z of the current panel
+    unsigned int* counter;
+    int* abort_flag;
+    int* status;
+    long long timeout;
+};
+
+__device__ __forceinline__ unsigned int chp_ld_acquire(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier number `k` (1, 2, ...): returns false when a wait expired or another CTA
+// aborted; then every CTA leaves.
+__device__ bool chp_grid_sync(const CholPDev& p, unsigned int k, int* ok_s) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(p.counter, 1u);
+        const unsigned int target = k * gridDim.x;
+        const long long t0 = clock64();
+        int ok = 1;
+        for (unsigned int it = 1;; ++it) {
+            if (chp_ld_acquire(p.counter) >= target) break;
+            if ((it & 63) == 0) {
+                if (*(volatile int*)p.abort_flag) { ok = 0; break; }
+                if (clock64() - t0 > p.timeout) {
+                    atomicExch(p.abort_flag, 1);
+                    set_status(p.status, RTPROJ_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        *ok_s = ok;
+    }
+    __syncthreads();
+    return *ok_s != 0;
+}
+
+// 1 / sqrt(d) for d > 0 in the float range: float32 estimate, two Newton steps in float64.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+    double y = (double)rsqrtf((float)d);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    return y;
+}
+
+__global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDev p) {
+    __shared__ double a[CHP_NB][CHP_NB + 1];
+    __shared__ double z[CHP_NB][CHP_NB + 1];
+    __shared__ double pr[CHP_TILE][CHP_NB + 1];
+    __shared__ double pq[CHP_TILE][CHP_NB + 1];
+    __shared__ double inv_s;
+    __shared__ int ok_s;
+    const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int G = gridDim.x;
+    unsigned int nsync = 0;
+    for (int p0 = 0; p0 < m; p0 += CHP_NB) {
+        const int nb = min(CHP_NB, m - p0);
+        const int base = p0 + nb, rest = m - base;
+        // (A) diagonal block and its inverse
+        if (blockIdx.x == 0) {
+            for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
+                const int i = e / CHP_NB, j = e % CHP_NB;
+                a[i][j] = (i < nb && j <= i) ? __ldcg(p.X + (int64_t)(p0 + i) * m + p0 + j) : 0.0;
+                z[i][j] = (i == j) ? 1.0 : 0.0;
+            }
+            __syncthreads();
+            for (int c = 0; c < nb; ++c) {
+                if (t == 0) {
+                    double d = a[c][c];
+                    if (!(d > 0.0) || !isfinite(d)) {
+                        set_status(p.status, RTPROJ_ENOTSPD);
+                        d = 1.0;
+                    }
+                    const float df = (float)d;
+                    const double y = (df > 1e-30f && df < 1e30f) ? rsqrt_newton(d) : 1.0 / sqrt(d);
+                    inv_s = y;
+                    a[c][c] = d * y;                       // sqrt(d)
+                }
+                __syncthreads();
+                const double y = inv_s;
+                // column c of L and row c of Z scaled by 1 / L_cc
+                if (t > c && t < nb) a[t][c] *= y;
+                else if (t >= CHP_NB && t - CHP_NB <= c) z[c][t - CHP_NB] *= y;
+                __syncthreads();
+                // trailing update of the block and elimination in Z
+                const int w = nb - c - 1;
+                for (int e = t; e < w * CHP_NB * 2; e += CHP_THREADS) {
+                    const int r = c + 1 + e / (2 * CHP_NB), q = e % (2 * CHP_NB);
+                    if (q < CHP_NB) {
+                        if (q > c && q <= r) a[r][q] = fma(-a[r][c], a[q][c], a[r][q]);
+                    } else {
+                        const int k = q - CHP_NB;
+                        if (k <= c) z[r][k] = fma(-a[r][c], z[c][k], z[r][k]);
+                    }
+                }
+                __syncthreads();
+            }
+            for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
+                const int i = e / CHP_NB, j = e % CHP_NB;
+                if (i < nb && j < nb) p.X[(int64_t)(p0 + i) * m + p0 + j] = j <= i ? a[i][j] : 0.0;
+                p.zbuf[e] = z[i][j];
+            }
+        }
+        if (rest <= 0) break;
+        if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
+        // (B) panel rows: x_c = sum_{k <= c} b_k Z[c][k], one warp per row
+        for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) z[e / CHP_NB][e % CHP_NB] = __ldcg(p.zbuf + e);
+        __syncthreads();
+        for (int r = base + blockIdx.x * (CHP_THREADS / 32) + warp; r < m; r += G * (CHP_THREADS / 32)) {
+            double* row = p.X + (int64_t)r * m + p0;
+            const double b = lane < nb ? __ldcg(row + lane) : 0.0;
+            double x = 0.0;
+#pragma unroll
+            for (int k = 0; k < CHP_NB; ++k) {
+                const double bk = __shfl_sync(0xffffffffu, b, k);
+                if (k <= lane) x = fma(bk, z[lane][k], x);
+            }
+            if (lane < nb) row[lane] = x;
+        }
+        if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
+        // (C) trailing lower triangle on 16 x 16 tiles: X[r][q] -= sum_c L[r][c] L[q][c]
+        const int nt = (rest + CHP_TILE - 1) / CHP_TILE;
+        const int ntiles = nt * (nt + 1) / 2;
+        for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+            int u = tile, tr = 0;
+            while (u > tr) { u -= tr + 1; ++tr; }
+            const int r0 = base + tr * CHP_TILE, q0 = base + u * CHP_TILE;
+            for (int e = t; e < CHP_TILE * CHP_NB; e += CHP_THREADS) {
+                const int i = e / CHP_NB, c = e % CHP_NB;
+                pr[i][c] = (r0 + i < m && c < nb) ? __ldcg(p.X + (int64_t)(r0 + i) * m + p0 + c) : 0.0;
+                pq[i][c] = (q0 + i < m && c < nb) ? __ldcg(p.X + (int64_t)(q0 + i) * m + p0 + c) : 0.0;
+            }
+            __syncthreads();
+            const int i = t / CHP_TILE, j = t % CHP_TILE;
+            const int r = r0 + i, q = q0 + j;
+            if (r < m && q <= r) {
+                double acc = 0.0;
+#pragma unroll
+                for (int c = 0; c < CHP_NB; ++c) acc = fma(pr[i][c], pq[j][c], acc);
+                double* xp = p.X + (int64_t)r * m + q;
+                *xp = __ldcg(xp) - acc;
+            }
+            __syncthreads();
+        }
+        if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
+    }
+}
+
 }  // namespace
 
 cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
-                 double* Bm, int64_t b_rs, int ncols, double* dinv_work, int* status, cudaStream_t s) {
+                 double* Bm, int64_t b_rs, int ncols, double* dinv_work, int* status, cudaStream_t s, bool rhs_lower) {
     if (m <= 0 || ncols <= 0) return cudaSuccess;
     const size_t smem = (size_t)m * TRSM_NB * sizeof(double);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
@@ -247,12 +418,13 @@ cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
         tri_diag_inv_kernel<true><<<nblk, TRSM_BS, 0, s>>>(T, t_rs, t_cs, m, dinv_work, status);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(trsm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        trsm_kernel<true><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, dinv_work);
+        trsm_kernel<true><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, dinv_work,
+                                                             rhs_lower ? 1 : 0);
     } else {
         tri_diag_inv_kernel<false><<<nblk, TRSM_BS, 0, s>>>(T, t_rs, t_cs, m, dinv_work, status);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(trsm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        trsm_kernel<false><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, dinv_work);
+        trsm_kernel<false><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, dinv_work, 0);
     }
     note_launch(2);
     return cudaGetLastError();
@@ -261,6 +433,30 @@ cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
 size_t trsm_work_doubles(int m) { return (size_t)((m + TRSM_BS - 1) / TRSM_BS) * TRSM_BS * TRSM_BS; }
 
 cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s) {
+    // Persistent cooperative form; the per-panel launches below when it cannot run.
+    int dev = 0, sms = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (coop && sms > 0 && part_elems >= CHP_NB * CHP_NB + 2) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_persistent_kernel, CHP_THREADS, 0);
+        if (per_sm >= 1) {
+            CholPDev p;
+            p.X = X; p.m = m; p.zbuf = part;
+            p.counter = (unsigned int*)(part + CHP_NB * CHP_NB);
+            p.abort_flag = (int*)(p.counter + 1);
+            p.status = status;
+            p.timeout = 4000000000ll;
+            cudaError_t e = cudaMemsetAsync(p.counter, 0, 2 * sizeof(unsigned int), s);
+            if (e != cudaSuccess) return e;
+            void* args[] = {&p};
+            e = cudaLaunchCooperativeKernel((const void*)chol_persistent_kernel, dim3(sms), dim3(CHP_THREADS), args, 0, s);
+            note_launch();
+            if (e == cudaSuccess) return zero_upper(X, m, s);
+            cudaGetLastError();   // clear and fall back
+        }
+    }
     for (int p0 = 0; p0 < m; p0 += CH_NB) {
         const int nb = std::min(CH_NB, m - p0);
         chol_diag_kernel<<<1, 256, 0, s>>>(X, m, p0, nb, status);
@@ -273,8 +469,6 @@ cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* sta
         chol_update_kernel<<<nt * (nt + 1) / 2, 256, 0, s>>>(X, m, p0, nb);
         note_launch();
     }
-    (void)part;
-    (void)part_elems;
     return zero_upper(X, m, s);
 }
 

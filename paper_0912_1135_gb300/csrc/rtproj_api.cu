@@ -361,7 +361,7 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     // R^{-*} (the transpose of P^- of Eq. 15, up to Pi)
     phase_begin(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(set_identity(h->RinvT, m, s));
-    RT_CHECK(trsm(h->R, 1, m, true, m, h->RinvT, m, m, h->dinv, h->status, s));
+    RT_CHECK(trsm(h->R, 1, m, true, m, h->RinvT, m, m, h->dinv, h->status, s, true));   // R^* X = I
     phase_end(h, RTPROJ_PHASE_FACTOR);
     // 3. X = P^{-1} A A^* P^{-*} (Eq. 14 via steps a-e, as W W^*)
     phase_begin(h, RTPROJ_PHASE_GRAM);
@@ -372,7 +372,7 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_begin(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(cholesky(h->Lc, m, h->part, h->part_elems, h->status, s));
     RT_CHECK(cudaMemcpyAsync(h->T1, h->RinvT, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
-    RT_CHECK(trsm(h->Lc, m, 1, true, m, h->T1, m, m, h->dinv, h->status, s));
+    RT_CHECK(trsm(h->Lc, m, 1, true, m, h->T1, m, m, h->dinv, h->status, s, true));     // R^{-*} is lower
     phase_end(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(cudaEventRecord(h->ev1, s));
     RT_CHECK(cudaStreamSynchronize(s));

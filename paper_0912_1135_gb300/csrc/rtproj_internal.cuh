@@ -104,8 +104,11 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
 // Solves op(T) X = Bm in place; T (m x m) element (i,j) at T[i*t_rs + j*t_cs];
 // lower selects forward substitution. Bm element (i, j) at Bm[i*b_rs + j], j < ncols.
 // dinv_work: trsm_work_doubles(m) doubles (inverses of the 32 x 32 diagonal blocks).
+// rhs_lower (lower solves only): Bm is zero above its diagonal, so the solution is too and
+// the rows above each column are skipped.
 cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
-                 double* Bm, int64_t b_rs, int ncols, double* dinv_work, int* status, cudaStream_t s);
+                 double* Bm, int64_t b_rs, int ncols, double* dinv_work, int* status, cudaStream_t s,
+                 bool rhs_lower = false);
 size_t trsm_work_doubles(int m);
 // In-place lower Cholesky of the m x m row-major X (strict upper part zeroed).
 cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s);
