@@ -156,18 +156,21 @@ __global__ void qr_extract_r_kernel(const double* S, int m, int64_t lds, double*
 // Persistent form: one cooperative launch for all m steps. CTA b keeps columns
 // [b*cpc, b*cpc + cpc) of S^* (rows of S) in shared memory for the whole factorization,
 // one warp per column. A step costs one grid-wide exchange. Before arriving for step j,
-// each CTA publishes its candidate: its remaining column with the largest downdated norm
-// (lowest index on ties), fully updated through step j-1, copied to the CTA's slot in
-// global memory together with its exactly recomputed tail norm. After everyone has
-// arrived, each CTA picks the global pivot among the candidates (largest norm, lowest
-// column index on ties), reads that column from its owner's slot, forms the reflector
-// itself (all CTAs compute bitwise the same alpha, beta and v) and applies it: first the
-// row-j entry of each active column, so that the norms are downdated (LAPACK-style) and
-// the next candidate is known early; the candidate's full update, slot copy and arrival
-// follow, and the other columns' updates overlap the wait. Columns never move: the pivot
-// column is retired and R[:, j] is the retired column's first j+1 entries. Slots and
-// candidates alternate between two buffers by step parity. Every wait has a clock
-// deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all CTAs leave their loops.
+// each CTA publishes its candidate: its remaining column with the largest downdated
+// squared norm (lowest index on ties), fully updated through step j-1 by all its warps,
+// copied to the CTA's slot in global memory together with its exactly recomputed squared
+// tail norm. After everyone has arrived, each CTA picks the global pivot among the
+// candidates (largest squared norm, lowest column index on ties), reads that column from
+// its owner's slot, forms the reflector itself (all CTAs compute bitwise the same alpha,
+// beta and v) and applies it: first the row-j entry of each active column, so that the
+// squared norms are downdated (LAPACK's rule, in squares: no division, no square root)
+// and the next candidate is known early; the candidate's full update, slot copy and
+// arrival follow, and the other columns' updates overlap the wait. Columns never move:
+// the pivot column is retired and R[:, j] is the retired column's first j+1 entries.
+// Slots and candidates alternate between two buffers by step parity. Every wait has a
+// clock deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all CTAs leave their
+// loops. (GB300's FP64 pipe takes 64 cycles per warp instruction, active lanes or not,
+// so the step is arranged to keep float64 instructions off its critical path.)
 constexpr int PQ_THREADS = 128;
 constexpr int PQ_WARPS = PQ_THREADS / 32;
 constexpr int PQ_MAXC = 32;
@@ -178,7 +181,7 @@ struct PqrDev {
     double* R; int32_t* perm;
     int cpc;
     double* slots;           // 2 x G x l: candidate columns by step parity
-    double* bval;            // 2 x G: candidate tail norms
+    double* bval;            // 2 x G: candidate squared tail norms
     int* bidx;               // 2 x G: candidate column indices (m = none)
     unsigned int* counter;   // arrivals (monotonic)
     int* abort_flag;
@@ -212,28 +215,43 @@ __device__ bool wait_geq(const unsigned int* p, unsigned int target, int* abort_
     }
 }
 
-// Candidate of this CTA for step j + 1 (parity par1): the column owned by warp `warp`
-// at local index q (or none when q < 0). The warp copies rows j+1 .. l-1 to the slot,
-// recomputes the tail norm exactly, publishes (norm, index) and arrives.
-__device__ __forceinline__ void publish_candidate(const PqrDev& p, int b, int G, int par1, int j, int q,
-                                                  const double* col, double* vn1, double* vn2, int lane) {
-    double nrm = -1.0;
+// Squared norms are compared through their bit patterns: for non-negative doubles the
+// integer order is the numeric order, and integer compares stay off the FP64 pipe.
+__device__ __forceinline__ unsigned long long sq_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// Candidate of this CTA for step j + 1 (parity par1): local column q (or none when q < 0),
+// finishing its update with w (unless `done`) and copying rows j+1 .. l-1 to the slot;
+// all warps share the rows. Its squared tail norm is recomputed exactly and published.
+// Called by every thread of the CTA.
+__device__ __forceinline__ void publish_candidate(const PqrDev& p, int b, int G, int par1, int j, int q, double* col,
+                                                  const double* v, double w, bool done, double* s1, double* s2,
+                                                  double* redv) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    double ssq = 0.0;
     if (q >= 0) {
         double* slot = p.slots + ((int64_t)par1 * G + b) * p.l;
-        double s = 0.0;
-        for (int i = j + 1 + lane; i < p.l; i += 32) {
-            const double x = col[i];
+        const int first = j + 1, len1 = p.l - first;
+        const int per = (len1 + PQ_WARPS - 1) / PQ_WARPS;
+        const int lo = first + warp * per, hi = min(p.l, lo + per);
+        for (int i = lo + lane; i < hi; i += 32) {
+            double x = col[i];
+            if (!done) {
+                x = fma(-w, v[i - j], x);
+                col[i] = x;
+            }
             slot[i] = x;
-            s = fma(x, x, s);
+            ssq = fma(x, x, ssq);
         }
-        s = warp_sum(s);
-        nrm = sqrt(s);
-        if (lane == 0) { vn1[q] = nrm; vn2[q] = nrm; }
+        ssq = warp_sum(ssq);
     }
     __threadfence();
-    __syncwarp();
-    if (lane == 0) {
-        p.bval[par1 * G + b] = nrm;
+    if (lane == 0) redv[warp] = ssq;
+    __syncthreads();
+    if (t == 0) {
+        double nsq = 0.0;
+        for (int k = 0; k < PQ_WARPS; ++k) nsq += redv[k];
+        if (q >= 0) { s1[q] = nsq; s2[q] = nsq; }
+        p.bval[par1 * G + b] = q >= 0 ? nsq : 0.0;
         p.bidx[par1 * G + b] = q >= 0 ? b * p.cpc + q : p.m;
         red_release_add(p.counter, 1u);
     }
@@ -244,16 +262,18 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     const int l = p.l, m = p.m, cpc = p.cpc;
     double* cols = smem_d;                 // cpc x l
     double* v = cols + (size_t)cpc * l;    // l
-    __shared__ double vn1[PQ_MAXC], vn2[PQ_MAXC], wq[PQ_MAXC];
+    __shared__ double s1[PQ_MAXC], s2[PQ_MAXC], wq[PQ_MAXC];   // squared norms: downdated, at last recompute
     __shared__ int posq[PQ_MAXC];
     __shared__ unsigned char doneq[PQ_MAXC];
+    __shared__ unsigned long long redb[PQ_WARPS];
     __shared__ double redv[PQ_WARPS];
     __shared__ int redi[PQ_WARPS];
     __shared__ int piv_s, owner_s, ok_s, cand_s;
-    __shared__ double norm_s;
+    __shared__ double nsq_s;
     const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int c0 = b * cpc;
     const int nc = max(0, min(cpc, m - c0));
+    const double tol3z = 1.4901161193847656e-08;   // sqrt(eps): LAPACK's recompute threshold
 
     for (int q = 0; q < nc; ++q)
         for (int i = t; i < l; i += PQ_THREADS) cols[(size_t)q * l + i] = p.S[(int64_t)(c0 + q) * p.lds + i];
@@ -263,20 +283,21 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         double s = 0.0;
         for (int i = lane; i < l; i += 32) s = fma(c[i], c[i], s);
         s = warp_sum(s);
-        if (lane == 0) { vn1[q] = sqrt(s); vn2[q] = sqrt(s); posq[q] = -1; }
+        if (lane == 0) { s1[q] = s; s2[q] = s; posq[q] = -1; }
     }
     __syncthreads();
-    // candidate for step 0: whole columns (rows 0 .. l-1)
     if (t == 0) {
-        double best = -1.0;
+        unsigned long long best = 0;
         int bq = -1;
         for (int q = 0; q < nc; ++q)
-            if (vn1[q] > best) { best = vn1[q]; bq = q; }
+            if (bq < 0 || sq_bits(s1[q]) > best) { best = sq_bits(s1[q]); bq = q; }
         cand_s = bq;
     }
     __syncthreads();
-    if (warp == 0) publish_candidate(p, b, G, 0, -1, cand_s, cand_s >= 0 ? cols + (size_t)cand_s * l : nullptr,
-                                     vn1, vn2, lane);
+    {
+        const int q = cand_s;
+        publish_candidate(p, b, G, 0, -1, q, q >= 0 ? cols + (size_t)q * l : nullptr, v, 0.0, true, s1, s2, redv);
+    }
 
     bool alive = true;
     for (int j = 0; j < m && alive; ++j) {
@@ -286,40 +307,43 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
                                      p.timeout);
         __syncthreads();
         if (!ok_s) { alive = false; break; }
-        // 2. global pivot: largest norm, lowest column index on ties
-        double best = -1.0;
+        // 2. global pivot: largest squared norm, lowest column index on ties
+        unsigned long long best = 0;
         int bi = m;
         for (int g = t; g < G; g += PQ_THREADS) {
-            const double x = __ldcg(p.bval + par * G + g);
+            const unsigned long long x = sq_bits(__ldcg(p.bval + par * G + g));
             const int i = __ldcg(p.bidx + par * G + g);
-            if (x > best || (x == best && i < bi)) { best = x; bi = i; }
+            if (i < m && (bi == m || x > best || (x == best && i < bi))) { best = x; bi = i; }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+            if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
         }
-        if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+        if (lane == 0) { redb[warp] = best; redi[warp] = bi; }
         __syncthreads();
         if (t == 0) {
-            double bb = redv[0];
+            unsigned long long bb = redb[0];
             int ii = redi[0];
             for (int w = 1; w < PQ_WARPS; ++w)
-                if (redv[w] > bb || (redv[w] == bb && redi[w] < ii)) { bb = redv[w]; ii = redi[w]; }
+                if (redi[w] < m && (ii == m || redb[w] > bb || (redb[w] == bb && redi[w] < ii))) {
+                    bb = redb[w];
+                    ii = redi[w];
+                }
             piv_s = ii < m ? ii : -1;
             owner_s = ii < m ? ii / cpc : -1;
-            norm_s = bb;                                   // the pivot column's tail norm
+            nsq_s = __longlong_as_double((long long)bb);
         }
         __syncthreads();
         const int piv = piv_s;
         if (piv < 0) { alive = false; break; }             // cannot happen while columns remain
         const int owner = owner_s;
-        const double nx = norm_s;
         // 3. the reflector from the owner's slot (rows j .. l-1); every thread derives alpha
-        //    and beta from the published norm and the slot's first entry
+        //    and beta from the published squared norm and the slot's first entry
         const double* slot = p.slots + ((int64_t)par * G + owner) * l;
         const double x0 = __ldcg(slot + j);
+        const double nx = sqrt(nsq_s);
         double alpha = 0.0, beta = 0.0;
         if (nx > 0.0) {
             alpha = x0 >= 0.0 ? -nx : nx;
@@ -334,9 +358,9 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         }
         __syncthreads();
         const int len = l - j;
-        // 4a. row j of each active column and its downdated norm; a column whose downdate
-        //     would lose more than half the digits is updated in full here and its norm
-        //     recomputed, so that every norm is current when the next candidate is chosen
+        // 4a. row j of each active column and its downdated squared norm s1 - r^2; when the
+        //     downdate falls to tol3z times the norm at the last recompute (LAPACK's test on
+        //     the ratio), the column is updated in full here and its norm recomputed
         for (int q = warp; q < nc; q += PQ_WARPS) {
             if (posq[q] >= 0) continue;
             double* c = cols + (size_t)q * l + j;
@@ -345,52 +369,37 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             for (int i = lane; i < len; i += 32) w = fma(v[i], c[i], w);
             w = warp_sum(w) * beta;
             const double r = fma(-w, v[0], cj);
-            const double n1 = vn1[q];
-            bool recompute = false;
-            double tmp = 0.0;
-            if (n1 != 0.0) {
-                tmp = fabs(r) / n1;
-                tmp = fmax(0.0, (1.0 + tmp) * (1.0 - tmp));
-                const double ratio = n1 / vn2[q];
-                recompute = tmp * ratio * ratio <= 1.4901161193847656e-08;
-            }
+            const double sq = s1[q];
+            const double sq_new = fma(-r, r, sq);
+            const bool recompute = sq != 0.0 && sq_new <= tol3z * s2[q];
             if (recompute) {
-                double s2 = 0.0;
+                double ss = 0.0;
                 for (int i = 1 + lane; i < len; i += 32) {
                     const double x = fma(-w, v[i], c[i]);
                     c[i] = x;
-                    s2 = fma(x, x, s2);
+                    ss = fma(x, x, ss);
                 }
-                s2 = warp_sum(s2);
-                if (lane == 0) { vn1[q] = sqrt(s2); vn2[q] = sqrt(s2); }
-            } else if (lane == 0 && n1 != 0.0) {
-                vn1[q] = n1 * sqrt(tmp);
+                ss = warp_sum(ss);
+                if (lane == 0) { s1[q] = ss; s2[q] = ss; }
+            } else if (lane == 0 && sq != 0.0) {
+                s1[q] = sq_new;
             }
             if (lane == 0) { c[0] = r; wq[q] = w; doneq[q] = recompute ? 1 : 0; }
         }
         __syncthreads();
-        // 4b. the next candidate (largest downdated norm, lowest index on ties); its warp
-        //     finishes its update first, publishes it and arrives
+        // 4b. the next candidate (largest downdated squared norm, lowest index on ties): all
+        //     warps finish its update, copy it to the slot and the CTA arrives
         if (t == 0) {
-            double bestn = -1.0;
+            unsigned long long bestn = 0;
             int bq = -1;
             for (int q = 0; q < nc; ++q)
-                if (posq[q] < 0 && vn1[q] > bestn) { bestn = vn1[q]; bq = q; }
+                if (posq[q] < 0 && (bq < 0 || sq_bits(s1[q]) > bestn)) { bestn = sq_bits(s1[q]); bq = q; }
             cand_s = bq;
         }
         __syncthreads();
         const int cand = cand_s;
-        const int cand_warp = cand >= 0 ? cand % PQ_WARPS : 0;
-        if (warp == cand_warp) {
-            if (cand >= 0 && !doneq[cand]) {
-                double* c = cols + (size_t)cand * l + j;
-                const double w = wq[cand];
-                for (int i = 1 + lane; i < len; i += 32) c[i] = fma(-w, v[i], c[i]);
-                __syncwarp();
-            }
-            publish_candidate(p, b, G, par ^ 1, j, cand, cand >= 0 ? cols + (size_t)cand * l : nullptr, vn1, vn2,
-                              lane);
-        }
+        publish_candidate(p, b, G, par ^ 1, j, cand, cand >= 0 ? cols + (size_t)cand * l : nullptr, v,
+                          cand >= 0 ? wq[cand] : 0.0, cand >= 0 && doneq[cand], s1, s2, redv);
         // 4c. the remaining columns (overlapping the other CTAs' arrivals)
         for (int q = warp; q < nc; q += PQ_WARPS) {
             if (posq[q] >= 0 || q == cand || doneq[q]) continue;
