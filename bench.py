@@ -7,8 +7,10 @@ refinement pass in the mixed form). value = k * steps / (device time of the time
 steps), all ranks together; each rank runs an independent replica (one GPU each).
 
 Workload (synthetic, seeded): A = U diag(sigma) V^T, 512 x 65536 float64, U and V Haar,
-sigma log-spaced over [1e-10, 1]; G uniform on (-1, 1) (Philox4x32-10), l = 2048;
+sigma log-spaced over [1e-10, 1]; G uniform on (-1, 1) (Philox4x32-10), l = m + 4 = 516;
 k = 64 right-hand sides with N(0,1) entries. A (268 MB) is larger than L2 (129 MB).
+The line also carries the plain float64 form measured on the same workload (the
+comparison the metric names) and the accuracy of both against the exact oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -347,6 +349,8 @@ def run_ours(args, w, world, rank, local):
     line["roofline"] = rl
     line["roofline_phases"] = rl_phases
 
+    if args.mode == "mixed" and not args.no_fp64_form:
+        line["fp64_form"] = fp64_form(torch, rt, A, B, At, Bt, w, args, rank)
     if not args.no_e2e:
         line["e2e"] = e2e(torch, rt, A, B, w, args, dev)
     if rank == 0 and not args.no_cpu_baseline:
@@ -354,6 +358,26 @@ def run_ours(args, w, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def fp64_form(torch, rt, A, B, At, Bt, w, args, rank):
+    """The plain float64 GPU form on the same workload: a few steps, device-timed, and
+    its error on RHS 0 against the exact oracle."""
+    from oracle import exact, metrics
+    steps = 3
+    P = rt.Projector(At, l_max=w.l, k_max=w.k, mode="fp64")
+    P.precondition(w.seed_omega, w.l)
+    P.null_project(Bt, out=Zbuf_of(P, Bt))
+    stream = torch.cuda.current_stream(At.device)
+    ms = time_steps(torch, P, Bt, w.seed_omega + 2000, w.l, steps, stream)
+    out = {"value": w.k * steps / (ms * 1e-3), "unit": "projections/s", "ms_per_step": ms / steps, "steps": steps}
+    if not args.no_accuracy and rank == 0:
+        Z = Zbuf_of(P, Bt).cpu().numpy()
+        Zx, _, _ = exact.exact_project(A, B[:1])
+        out["z_rel_err_vs_exact_oracle"] = metrics.max_rel_err(Z[:1], Zx)
+        out["normalised_residual_max"] = metrics.normalised_residual(A, Z, B, normA=1.0)
+    P.close()
+    return out
 
 
 def e2e(torch, rt, A, B, w, args, dev):
@@ -400,6 +424,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true", help="skip the float64-form comparison")
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
     args = ap.parse_args()
     if args.warmup < 3:
