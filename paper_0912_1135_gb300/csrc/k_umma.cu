@@ -163,15 +163,54 @@ __device__ __forceinline__ void fold_level(int g, const uint32_t (&r)[32], long 
     }
 }
 
-// (hi * 2^40 + lo) * 2^e as a double: one fused multiply-add of the two words (rounded
-// once, or twice when |hi| >= 2^53), then the power of two is added to the exponent
-// field; ldexp only when the result would leave the normal range.
+// (hi * 2^40 + lo) * 2^e rounded to nearest (ties to even), from integer operations: the
+// two words form a 128-bit two's-complement integer, whose magnitude is shifted to 53 bits
+// with a round bit and a sticky bit. Integer instructions keep the conversion off GB300's
+// FP64 pipe (64 cycles per warp instruction). A result outside the normal range is
+// delegated to ldexp.
 __device__ __forceinline__ double words_to_double(long long hi, long long lo, int e) {
-    const double d = fma((double)hi, 1099511627776.0, (double)lo);
-    const long long bits = __double_as_longlong(d);
-    const int ex = (int)((bits >> 52) & 0x7FF);
-    if (d == 0.0 || ex + e <= 0 || ex + e >= 2047) return ldexp(d, e);
-    return __longlong_as_double(bits + ((long long)e << 52));
+    unsigned long long L = ((unsigned long long)hi << 40) + (unsigned long long)lo;
+    const unsigned long long carry = L < ((unsigned long long)hi << 40) ? 1ull : 0ull;
+    unsigned long long H = (unsigned long long)(hi >> 24) + (unsigned long long)(lo >> 63) + carry;
+    const bool neg = (long long)H < 0;
+    if (neg) {
+        L = ~L + 1ull;
+        H = ~H + (L == 0 ? 1ull : 0ull);
+    }
+    if (H == 0 && L == 0) return 0.0;
+    const int p = H != 0 ? 127 - __clzll((long long)H) : 63 - __clzll((long long)L);   // leading bit
+    const int sh = p - 52;
+    unsigned long long m;
+    bool round = false, sticky = false;
+    if (sh <= 0) {
+        m = L << (-sh);
+    } else if (sh < 64) {
+        m = (L >> sh) | (H << (64 - sh));
+        round = (L >> (sh - 1)) & 1ull;
+        sticky = sh > 1 && (L & ((1ull << (sh - 1)) - 1ull)) != 0;
+    } else {
+        const int s2 = sh - 64;                                  // 0 .. 63
+        m = H >> s2;
+        if (s2 == 0) {
+            round = (L >> 63) & 1ull;
+            sticky = (L & 0x7FFFFFFFFFFFFFFFull) != 0;
+        } else {
+            round = (H >> (s2 - 1)) & 1ull;
+            sticky = L != 0 || (s2 > 1 && (H & ((1ull << (s2 - 1)) - 1ull)) != 0);
+        }
+    }
+    int ex = p;
+    if (round && (sticky || (m & 1ull))) {
+        ++m;
+        if (m == (1ull << 53)) { m >>= 1; ++ex; }
+    }
+    const int biased = ex + e + 1023;
+    if (biased <= 0 || biased >= 2047) {
+        const double mag = ldexp((double)m, ex - 52 + e);
+        return neg ? -mag : mag;
+    }
+    const unsigned long long bits = ((unsigned long long)biased << 52) | (m & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
 }
 
 // alpha * v + beta * cin for the common alpha = +-1, beta in {0, 1} without FP64 multiplies.
@@ -539,6 +578,7 @@ struct Sg2Dev {
     uint32_t tmem_cols;
     int acc_bufs, a_stages, b_stages;
     int tn;                       // B rows per tile: 32 or 64
+    int m_fast;                   // tile order: A-row tiles fastest
 };
 
 
@@ -613,17 +653,43 @@ __device__ __forceinline__ bool wait_phase_warp(uint64_t* bar, uint32_t parity, 
     }
 }
 
-// Tile t of the persistent loop -> (x = B-row tile, y = A-row tile, z = K split).
+// Tile order of the persistent loop. Tiles of one K split are enumerated either B-tile
+// fastest or A-tile fastest (m_fast: when there are no more A-row tiles than B-row
+// tiles, so that consecutive CTAs share the larger B tile through L2), and with
+// lower_only only the tiles that touch the lower triangle are enumerated at all.
 struct TileCoord { int i0, j0, z; };
-__device__ __forceinline__ TileCoord tile_of(int t, int tiles_n, int tiles_m, int tn) {
-    TileCoord c;
-    const int per_z = tiles_n * tiles_m;
-    c.z = t / per_z;
-    const int r = t - c.z * per_z;
-    c.i0 = (r / tiles_n) * TM;
-    c.j0 = (r % tiles_n) * tn;
-    return c;
-}
+struct TileSched {
+    int tiles_m, tiles_n, tn, lower, m_fast;
+    __host__ __device__ int row_count(int i) const {           // column tiles of row tile i
+        if (!lower) return tiles_n;
+        const int last = (i * TM + TM - 1) / tn;
+        return last + 1 < tiles_n ? last + 1 : tiles_n;
+    }
+    __host__ __device__ int per_split() const {
+        if (!lower) return tiles_m * tiles_n;
+        int s = 0;
+        for (int i = 0; i < tiles_m; ++i) s += row_count(i);
+        return s;
+    }
+    __device__ TileCoord at(int t, int per_z) const {
+        TileCoord c;
+        c.z = t / per_z;
+        int r = t - c.z * per_z;
+        if (lower) {
+            int i = 0;
+            while (r >= row_count(i)) { r -= row_count(i); ++i; }
+            c.i0 = i * TM;
+            c.j0 = r * tn;
+        } else if (m_fast) {
+            c.i0 = (r % tiles_m) * TM;
+            c.j0 = (r / tiles_m) * tn;
+        } else {
+            c.i0 = (r / tiles_n) * TM;
+            c.j0 = (r % tiles_n) * tn;
+        }
+        return c;
+    }
+};
 
 // Epilogue role of one warp: NCOL = tn / 2 columns of each tile, for TMEM lanes
 // 32 * quarter ... + 31 (tile rows), chunk by chunk, then the tile's partial words or its
@@ -632,15 +698,15 @@ template <int NCOL>
 __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, uint64_t* tfull, uint64_t* tempty,
                                               volatile int* abort_v, int quarter, int half, int lane) {
     const int tn = 2 * NCOL;
-    const int tiles_n = (p.N + tn - 1) / tn, tiles_m = (p.M + TM - 1) / TM;
-    const int ntiles = tiles_n * tiles_m * p.splits;
+    const TileSched ts{(p.M + TM - 1) / TM, (p.N + tn - 1) / tn, tn, p.lower_only, p.m_fast};
+    const int per_z = ts.per_split();
+    const int ntiles = per_z * p.splits;
     const int cb = p.chunk_kb;
     const uint32_t buf_cols = (uint32_t)(p.terms * tn);
     int chunk = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-        const TileCoord c = tile_of(tile, tiles_n, tiles_m, tn);
-        if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+        const TileCoord c = ts.at(tile, per_z);
         const int kbeg = c.z * p.k_per_split;
         const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
         const int nchunks = (nkb + cb - 1) / cb;
@@ -704,8 +770,9 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     __shared__ int abort_s;
 
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int tiles_n = (p.N + tn - 1) / tn, tiles_m = (p.M + TM - 1) / TM;
-    const int ntiles = tiles_n * tiles_m * p.splits;
+    const TileSched ts{(p.M + TM - 1) / TM, (p.N + tn - 1) / tn, tn, p.lower_only, p.m_fast};
+    const int per_z = ts.per_split();
+    const int ntiles = per_z * p.splits;
     const int cb = p.chunk_kb;
     const uint32_t buf_cols = (uint32_t)(p.terms * tn);
 
@@ -733,8 +800,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         uint32_t a_it = 0, b_it = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const TileCoord c = tile_of(tile, tiles_n, tiles_m, tn);
-            if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+            const TileCoord c = ts.at(tile, per_z);
             const int kbeg = c.z * p.k_per_split;
             const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
             for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -772,8 +838,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         int chunk = 0, buf = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-            const TileCoord c = tile_of(tile, tiles_n, tiles_m, tn);
-            if (p.lower_only && c.j0 > c.i0 + TM - 1) continue;
+            const TileCoord c = ts.at(tile, per_z);
             const int kbeg = c.z * p.k_per_split;
             const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
             for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -965,8 +1030,7 @@ static int chunk_for(const SlicedGemm& g) {
     return kc;
 }
 
-static int choose_splits(int M, int N, int tn, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
-    const int tiles = ((M + TM - 1) / TM) * ((N + tn - 1) / tn);
+static int choose_splits(int tiles, int M, int N, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
     int splits = 1;
     const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
     if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
@@ -1002,7 +1066,9 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     const int Kp = (K + KB - 1) / KB * KB;
     const int kchunk = chunk_for(g);
     int kps = 0;
-    const int splits = choose_splits(M, N, tn, Kp, scratch_bytes, kchunk, &kps);
+    const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + tn - 1) / tn;
+    const TileSched ts{tiles_m, tiles_n, tn, g.lower_only ? 1 : 0, tiles_m <= tiles_n ? 1 : 0};
+    const int splits = choose_splits(ts.per_split(), M, N, Kp, scratch_bytes, kchunk, &kps);
     Sg2Dev p;
     p.M = M; p.N = N; p.Kp = Kp; p.sa = g.a.s; p.sb = g.b.s; p.terms = g.terms; p.k_per_split = kps;
     p.chunk_kb = kchunk / KB;
@@ -1014,6 +1080,7 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     p.status = status;
     p.timeout = 4000000000ll;
     p.tn = tn;
+    p.m_fast = ts.m_fast;
     p.acc_bufs = (2 * g.terms * tn <= 512) ? 2 : 1;
     p.tmem_cols = 32;
     while (p.tmem_cols < (uint32_t)(p.acc_bufs * g.terms * tn)) p.tmem_cols <<= 1;
@@ -1038,7 +1105,7 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     cudaError_t e = cudaFuncSetAttribute(sliced_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     p.splits = splits;
-    const int ntiles = ((N + tn - 1) / tn) * ((M + TM - 1) / TM) * splits;
+    const int ntiles = ts.per_split() * splits;
     static int sms = 0;
     if (!sms) {
         int dev = 0;
