@@ -49,6 +49,7 @@ struct SgDev {
     long long* part;    // [split][M][N][2] when gridDim.z > 1
     double* C; int64_t c_rs, c_cs; const int32_t* crow;
     double alpha, beta;
+    int amode, bmode;
     const double* Cin; int64_t cin_rs, cin_cs;
     int lower_only;
     int* status;
@@ -213,13 +214,20 @@ __device__ __forceinline__ double words_to_double(long long hi, long long lo, in
     return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
 }
 
-// alpha * v + beta * cin for the common alpha = +-1, beta in {0, 1} without FP64 multiplies.
-__device__ __forceinline__ double epilogue_value(double v, double alpha, double beta, const double* cin) {
-    double out = alpha == 1.0 ? v : (alpha == -1.0 ? -v : alpha * v);
-    if (beta == 1.0) out += *cin;
-    else if (beta != 0.0) out = fma(beta, *cin, out);
+// alpha * v + beta * cin with the common cases decided on the host: amode 0 (alpha = 1),
+// 1 (alpha = -1: a sign flip), 2 (general); bmode 0 (beta = 0), 1 (beta = 1), 2 (general).
+// The cases cost no float64 comparisons on the device.
+__device__ __forceinline__ double epilogue_value(double v, int amode, double alpha, int bmode, double beta,
+                                                 const double* cin) {
+    double out = amode == 0 ? v
+               : amode == 1 ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull)
+                            : alpha * v;
+    if (bmode == 1) out += *cin;
+    else if (bmode == 2) out = fma(beta, *cin, out);
     return out;
 }
+__host__ inline int alpha_mode(double a) { return a == 1.0 ? 0 : (a == -1.0 ? 1 : 2); }
+__host__ inline int beta_mode(double b) { return b == 0.0 ? 0 : (b == 1.0 ? 1 : 2); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
@@ -505,7 +513,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gemm_kernel(SgDev p) {
                 if (gj >= p.N || (p.lower_only && gj > i)) continue;
                 const double v = words_to_double(hi[j], lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
                 p.C[row * p.c_rs + (int64_t)gj * p.c_cs] =
-                    epilogue_value(v, p.alpha, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
+                    epilogue_value(v, p.amode, p.alpha, p.bmode, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
             }
         }
     }
@@ -519,6 +527,7 @@ struct SgReduceDev {
     const int32_t* ea; const int32_t* eb;
     double* C; int64_t c_rs, c_cs; const int32_t* crow;
     double alpha, beta;
+    int amode, bmode;
     const double* Cin; int64_t cin_rs, cin_cs;
     int lower_only;
 };
@@ -540,7 +549,7 @@ __global__ void sliced_reduce_kernel(SgReduceDev r) {
     const double v = words_to_double(h, l, e);
     const int64_t row = r.crow ? (int64_t)r.crow[i] : (int64_t)i;
     r.C[row * r.c_rs + (int64_t)j * r.c_cs] =
-        epilogue_value(v, r.alpha, r.beta, r.Cin + (int64_t)i * r.cin_rs + (int64_t)j * r.cin_cs);
+        epilogue_value(v, r.amode, r.alpha, r.bmode, r.beta, r.Cin + (int64_t)i * r.cin_rs + (int64_t)j * r.cin_cs);
 }
 
 
@@ -571,6 +580,7 @@ struct Sg2Dev {
     long long* part;
     double* C; int64_t c_rs, c_cs; const int32_t* crow;
     double alpha, beta;
+    int amode, bmode;
     const double* Cin; int64_t cin_rs, cin_cs;
     int lower_only;
     int* status;
@@ -579,6 +589,7 @@ struct Sg2Dev {
     int acc_bufs, a_stages, b_stages;
     int tn;                       // B rows per tile: 32 or 64
     int m_fast;                   // tile order: A-row tiles fastest
+    int vec2;                     // C rows contiguous and 16-byte aligned: paired stores
 };
 
 
@@ -727,22 +738,49 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
         if (!ok) break;
         const int i = c.i0 + quarter * 32 + lane;
         const int jb = c.j0 + half * NCOL;
-        if (*abort_v || i >= p.M) continue;
+        if (*abort_v) continue;
+        const bool valid = i < p.M;                 // rows past M: no output (but join the shuffles)
         if (p.splits > 1) {
+            if (!valid) continue;
             long long* dst = p.part + (((int64_t)c.z * p.M + i) * p.N + jb) * 2;
 #pragma unroll
             for (int j = 0; j < NCOL; ++j)
                 if (jb + j < p.N) { dst[2 * j] = (long long)hi[j]; dst[2 * j + 1] = (long long)lo[j]; }
         } else {
-            const int ea = p.ea ? p.ea[i] : 0;
-            const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
+            // column exponents: one load per lane, shared through the warp
+            const int ebl = (p.eb && lane < NCOL && jb + lane < p.N) ? p.eb[jb + lane] : 0;
+            const int ea = (p.ea && valid ? p.ea[i] : 0) - 86;
+            const int64_t row = p.crow && valid ? (int64_t)p.crow[i] : (int64_t)i;
+            double* crow_p = p.C + row * p.c_rs;
+            const double* cin_p = p.Cin + (int64_t)i * p.cin_rs;
+            if (p.vec2) {
+                // row-contiguous output: pairs of columns as one 16-byte store
 #pragma unroll
-            for (int j = 0; j < NCOL; ++j) {
-                const int gj = jb + j;
-                if (gj >= p.N || (p.lower_only && gj > i)) continue;
-                const double v = words_to_double((long long)hi[j], (long long)lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
-                p.C[row * p.c_rs + (int64_t)gj * p.c_cs] =
-                    epilogue_value(v, p.alpha, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
+                for (int j = 0; j < NCOL; j += 2) {
+                    const int gj = jb + j;
+                    const int e0 = __shfl_sync(0xffffffffu, ebl, j), e1 = __shfl_sync(0xffffffffu, ebl, j + 1);
+                    if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
+                    const double v0 = epilogue_value(words_to_double((long long)hi[j], (long long)lo[j], ea + e0),
+                                                     p.amode, p.alpha, p.bmode, p.beta, cin_p + (int64_t)gj * p.cin_cs);
+                    if (gj + 1 < p.N && !(p.lower_only && gj + 1 > i)) {
+                        const double v1 = epilogue_value(
+                            words_to_double((long long)hi[j + 1], (long long)lo[j + 1], ea + e1), p.amode, p.alpha,
+                            p.bmode, p.beta, cin_p + (int64_t)(gj + 1) * p.cin_cs);
+                        *reinterpret_cast<double2*>(crow_p + gj) = make_double2(v0, v1);
+                    } else {
+                        crow_p[gj] = v0;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < NCOL; ++j) {
+                    const int gj = jb + j;
+                    const int ej = __shfl_sync(0xffffffffu, ebl, j);
+                    if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
+                    crow_p[(int64_t)gj * p.c_cs] =
+                        epilogue_value(words_to_double((long long)hi[j], (long long)lo[j], ea + ej), p.amode, p.alpha,
+                                       p.bmode, p.beta, cin_p + (int64_t)gj * p.cin_cs);
+                }
             }
         }
     }
@@ -943,7 +981,8 @@ void launch_reduce(const SlicedGemm& g, int splits, void* scratch, cudaStream_t 
     r.part = (const long long*)scratch; r.splits = splits; r.M = g.a.rows; r.N = g.b.rows;
     r.ea = g.a.e; r.eb = g.b.e;
     r.C = g.C; r.c_rs = g.c_rs; r.c_cs = g.c_cs; r.crow = g.crow;
-    r.alpha = g.alpha; r.beta = g.beta; r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
+    r.alpha = g.alpha; r.beta = g.beta; r.amode = alpha_mode(g.alpha); r.bmode = beta_mode(g.beta);
+    r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
     r.lower_only = g.lower_only ? 1 : 0;
     const int64_t total = (int64_t)r.M * r.N;
     sliced_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
@@ -992,7 +1031,8 @@ static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t s
     p.Kp = Kp; p.terms = g.terms; p.k_per_split = kps; p.kchunk = kchunk;
     p.part = (long long*)scratch;
     p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
-    p.alpha = g.alpha; p.beta = g.beta; p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
+    p.alpha = g.alpha; p.beta = g.beta; p.amode = alpha_mode(g.alpha); p.bmode = beta_mode(g.beta);
+    p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
     p.lower_only = g.lower_only ? 1 : 0;
     p.status = status;
     p.timeout_cycles = 4000000000ll;   // ~2 s at 2 GHz per K block: a hung MMA reports ETIMEOUT
@@ -1009,7 +1049,8 @@ static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t s
         r.part = (const long long*)scratch; r.splits = splits; r.M = M; r.N = N;
         r.ea = g.a.e; r.eb = g.b.e;
         r.C = g.C; r.c_rs = g.c_rs; r.c_cs = g.c_cs; r.crow = g.crow;
-        r.alpha = g.alpha; r.beta = g.beta; r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
+        r.alpha = g.alpha; r.beta = g.beta; r.amode = alpha_mode(g.alpha); r.bmode = beta_mode(g.beta);
+    r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
         r.lower_only = g.lower_only ? 1 : 0;
         const int64_t total = (int64_t)M * N;
         sliced_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
@@ -1075,12 +1116,14 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     p.ea = g.a.e; p.eb = g.b.e;
     p.part = (long long*)scratch;
     p.C = g.C; p.c_rs = g.c_rs; p.c_cs = g.c_cs; p.crow = g.crow;
-    p.alpha = g.alpha; p.beta = g.beta; p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
+    p.alpha = g.alpha; p.beta = g.beta; p.amode = alpha_mode(g.alpha); p.bmode = beta_mode(g.beta);
+    p.Cin = g.Cin; p.cin_rs = g.cin_rs; p.cin_cs = g.cin_cs;
     p.lower_only = g.lower_only ? 1 : 0;
     p.status = status;
     p.timeout = 4000000000ll;
     p.tn = tn;
     p.m_fast = ts.m_fast;
+    p.vec2 = (g.c_cs == 1 && g.c_rs % 2 == 0 && ((uintptr_t)g.C & 15) == 0) ? 1 : 0;
     p.acc_bufs = (2 * g.terms * tn <= 512) ? 2 : 1;
     p.tmem_cols = 32;
     while (p.tmem_cols < (uint32_t)(p.acc_bufs * g.terms * tn)) p.tmem_cols <<= 1;
