@@ -1100,7 +1100,13 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     // 64 B rows per tile when the levels of one accumulator set fit TMEM at that width
     // (terms * 64 <= 512 columns): half the A-plane reads per flop and twice the MMA work
     // per pipeline stage; 32 otherwise.
-    const int tn = (g.terms * 64 <= 512 && N > 32) ? 64 : 32;
+    // A short contraction into a narrow output (the A^* products: K = m, N = k <= 64) has
+    // few chunks per tile and a per-tile output with Cin: 32 rows then keep two
+    // accumulator sets in TMEM so that readout and output overlap the next tile's MMAs
+    // (measured faster there; slower for the Gram's wide output).
+    const int Kp0 = (K + KB - 1) / KB * KB;
+    const bool short_k = Kp0 <= 1024 && N <= 64 && 2 * g.terms * 32 <= 512 && 2 * g.terms * 64 > 512;
+    const int tn = (g.terms * 64 <= 512 && N > 32 && !short_k) ? 64 : 32;
     CUtensorMap mapA, mapB;
     if (!make_stack_map(&mapA, g.a, TM, 1) || !make_stack_map(&mapB, g.b, tn, g.b.s))
         return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
