@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double* X, int m, int 
 // Per panel p0: (A) CTA 0 factors the diagonal block in shared memory and forms its
 // inverse Z = L_pp^{-1} in the same right-looking sweep (Gauss-Jordan on the identity);
 // (B) every warp of the grid solves panel rows: L[r][p0..] = X[r][p0..] Z^*; (C) all CTAs
-// update the trailing lower triangle on 16 x 16 tiles. A grid-wide counter separates the
+// update the trailing lower triangle on 16 x 16 tiles, CTA 0 taking the tiles of the next
+// diagonal block and factoring it at once (lookahead). A grid-wide counter separates the
 // phases; every wait is bounded (RTPROJ_ETIMEOUT). The reciprocal square root of each
 // pivot starts from the float32 estimate and takes two Newton steps in float64
 // (y <- y (3 - d y^2) / 2), which doubles the correct bits each time.
@@ -302,6 +303,89 @@ __device__ __forceinline__ double rsqrt_newton(double d) {
     return y;
 }
 
+// CTA-wide: factors the nb x nb diagonal block at (p0, p0) of X in shared memory (a) and
+// forms Z = L_pp^{-1} (z) in the same right-looking sweep, then writes L_pp (upper part
+// zero) back to X and Z to zbuf. Per column c: thread 0 takes the pivot (checked through
+// its bit pattern, so no float64 compare), every warp then scales and updates whole rows:
+// lane j of the warp holding row r updates Z[r][j] for j <= c and X[r][j] for c < j <= r,
+// one float64 instruction per row.
+__device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[CHP_NB + 1], double (*z)[CHP_NB + 1],
+                                double* inv_s) {
+    const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
+        const int i = e / CHP_NB, j = e % CHP_NB;
+        a[i][j] = (i < nb && j <= i) ? __ldcg(p.X + (int64_t)(p0 + i) * m + p0 + j) : 0.0;
+        z[i][j] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < nb; ++c) {
+        if (t == 0) {
+            double d = a[c][c];
+            const long long bits = __double_as_longlong(d);
+            // positive, finite, and within the float range of the estimate
+            const bool ok = bits > 0 && bits < 0x7FF0000000000000ll;
+            if (!ok) {
+                set_status(p.status, RTPROJ_ENOTSPD);
+                d = 1.0;
+            }
+            const int ex = (int)((bits >> 52) & 0x7FF);
+            const double y = (ok && ex > 1023 - 100 && ex < 1023 + 100) ? rsqrt_newton(d) : 1.0 / sqrt(d);
+            *inv_s = y;
+            a[c][c] = d * y;                                   // sqrt(d)
+        }
+        __syncthreads();
+        const double y = *inv_s;
+        if (t > c && t < nb) a[t][c] *= y;                      // column c of L
+        else if (t >= CHP_NB && t - CHP_NB <= c) z[c][t - CHP_NB] *= y;   // row c of Z
+        __syncthreads();
+        for (int r = c + 1 + warp; r < nb; r += CHP_THREADS / 32) {
+            const double lrc = a[r][c];
+            const int j = lane;
+            if (j <= r) {
+                double* dst = j <= c ? &z[r][j] : &a[r][j];
+                const double src = j <= c ? z[c][j] : a[j][c];
+                *dst = fma(-lrc, src, *dst);
+            }
+        }
+        __syncthreads();
+    }
+    for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
+        const int i = e / CHP_NB, j = e % CHP_NB;
+        if (i < nb && j < nb) p.X[(int64_t)(p0 + i) * m + p0 + j] = j <= i ? a[i][j] : 0.0;
+        p.zbuf[e] = z[i][j];
+    }
+}
+
+// Trailing update tile `tile` of the panel at p0 (16 x 16, lower triangle of rows/columns
+// [base, m)): X[r][q] -= sum_c L[r][p0+c] L[q][p0+c].
+__device__ void chp_update_tile(const CholPDev& p, int p0, int nb, int base, int tile, double (*pr)[CHP_NB + 1],
+                                double (*pq)[CHP_NB + 1]) {
+    const int m = p.m, t = threadIdx.x;
+    int u = tile, tr = 0;
+    while (u > tr) { u -= tr + 1; ++tr; }
+    const int r0 = base + tr * CHP_TILE, q0 = base + u * CHP_TILE;
+    for (int e = t; e < CHP_TILE * CHP_NB; e += CHP_THREADS) {
+        const int i = e / CHP_NB, c = e % CHP_NB;
+        pr[i][c] = (r0 + i < m && c < nb) ? __ldcg(p.X + (int64_t)(r0 + i) * m + p0 + c) : 0.0;
+        pq[i][c] = (q0 + i < m && c < nb) ? __ldcg(p.X + (int64_t)(q0 + i) * m + p0 + c) : 0.0;
+    }
+    __syncthreads();
+    const int i = t / CHP_TILE, j = t % CHP_TILE;
+    const int r = r0 + i, q = q0 + j;
+    if (r < m && q <= r) {
+        double acc = 0.0;
+#pragma unroll
+        for (int c = 0; c < CHP_NB; ++c) acc = fma(pr[i][c], pq[j][c], acc);
+        double* xp = p.X + (int64_t)r * m + q;
+        *xp = __ldcg(xp) - acc;
+    }
+    __syncthreads();
+}
+
+// Panels with lookahead: CTA 0 updates the three tiles that cover the next diagonal block
+// first and factors that block while the other CTAs finish the trailing update, so that a
+// panel costs two grid exchanges: (L_pp, Z ready) -> panel rows -> (panel rows ready) ->
+// trailing update and the next diagonal block.
 __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDev p) {
     __shared__ double a[CHP_NB][CHP_NB + 1];
     __shared__ double z[CHP_NB][CHP_NB + 1];
@@ -312,57 +396,13 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
     const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int G = gridDim.x;
     unsigned int nsync = 0;
+    if (blockIdx.x == 0) chp_factor_diag(p, 0, min(CHP_NB, m), a, z, &inv_s);
     for (int p0 = 0; p0 < m; p0 += CHP_NB) {
         const int nb = min(CHP_NB, m - p0);
         const int base = p0 + nb, rest = m - base;
-        // (A) diagonal block and its inverse
-        if (blockIdx.x == 0) {
-            for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
-                const int i = e / CHP_NB, j = e % CHP_NB;
-                a[i][j] = (i < nb && j <= i) ? __ldcg(p.X + (int64_t)(p0 + i) * m + p0 + j) : 0.0;
-                z[i][j] = (i == j) ? 1.0 : 0.0;
-            }
-            __syncthreads();
-            for (int c = 0; c < nb; ++c) {
-                if (t == 0) {
-                    double d = a[c][c];
-                    if (!(d > 0.0) || !isfinite(d)) {
-                        set_status(p.status, RTPROJ_ENOTSPD);
-                        d = 1.0;
-                    }
-                    const float df = (float)d;
-                    const double y = (df > 1e-30f && df < 1e30f) ? rsqrt_newton(d) : 1.0 / sqrt(d);
-                    inv_s = y;
-                    a[c][c] = d * y;                       // sqrt(d)
-                }
-                __syncthreads();
-                const double y = inv_s;
-                // column c of L and row c of Z scaled by 1 / L_cc
-                if (t > c && t < nb) a[t][c] *= y;
-                else if (t >= CHP_NB && t - CHP_NB <= c) z[c][t - CHP_NB] *= y;
-                __syncthreads();
-                // trailing update of the block and elimination in Z
-                const int w = nb - c - 1;
-                for (int e = t; e < w * CHP_NB * 2; e += CHP_THREADS) {
-                    const int r = c + 1 + e / (2 * CHP_NB), q = e % (2 * CHP_NB);
-                    if (q < CHP_NB) {
-                        if (q > c && q <= r) a[r][q] = fma(-a[r][c], a[q][c], a[r][q]);
-                    } else {
-                        const int k = q - CHP_NB;
-                        if (k <= c) z[r][k] = fma(-a[r][c], z[c][k], z[r][k]);
-                    }
-                }
-                __syncthreads();
-            }
-            for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
-                const int i = e / CHP_NB, j = e % CHP_NB;
-                if (i < nb && j < nb) p.X[(int64_t)(p0 + i) * m + p0 + j] = j <= i ? a[i][j] : 0.0;
-                p.zbuf[e] = z[i][j];
-            }
-        }
         if (rest <= 0) break;
         if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
-        // (B) panel rows: x_c = sum_{k <= c} b_k Z[c][k], one warp per row
+        // panel rows: x_c = sum_{k <= c} b_k Z[c][k], one warp per row
         for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) z[e / CHP_NB][e % CHP_NB] = __ldcg(p.zbuf + e);
         __syncthreads();
         for (int r = base + blockIdx.x * (CHP_THREADS / 32) + warp; r < m; r += G * (CHP_THREADS / 32)) {
@@ -377,31 +417,19 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
             if (lane < nb) row[lane] = x;
         }
         if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
-        // (C) trailing lower triangle on 16 x 16 tiles: X[r][q] -= sum_c L[r][c] L[q][c]
+        // trailing update; tiles 0-2 (the next diagonal block) on CTA 0, which then factors it
         const int nt = (rest + CHP_TILE - 1) / CHP_TILE;
         const int ntiles = nt * (nt + 1) / 2;
-        for (int tile = blockIdx.x; tile < ntiles; tile += G) {
-            int u = tile, tr = 0;
-            while (u > tr) { u -= tr + 1; ++tr; }
-            const int r0 = base + tr * CHP_TILE, q0 = base + u * CHP_TILE;
-            for (int e = t; e < CHP_TILE * CHP_NB; e += CHP_THREADS) {
-                const int i = e / CHP_NB, c = e % CHP_NB;
-                pr[i][c] = (r0 + i < m && c < nb) ? __ldcg(p.X + (int64_t)(r0 + i) * m + p0 + c) : 0.0;
-                pq[i][c] = (q0 + i < m && c < nb) ? __ldcg(p.X + (int64_t)(q0 + i) * m + p0 + c) : 0.0;
-            }
-            __syncthreads();
-            const int i = t / CHP_TILE, j = t % CHP_TILE;
-            const int r = r0 + i, q = q0 + j;
-            if (r < m && q <= r) {
-                double acc = 0.0;
-#pragma unroll
-                for (int c = 0; c < CHP_NB; ++c) acc = fma(pr[i][c], pq[j][c], acc);
-                double* xp = p.X + (int64_t)r * m + q;
-                *xp = __ldcg(xp) - acc;
-            }
-            __syncthreads();
+        const int lead = ntiles < 3 ? ntiles : 3;
+        if (blockIdx.x == 0) {
+            for (int tile = 0; tile < lead; ++tile) chp_update_tile(p, p0, nb, base, tile, pr, pq);
+            chp_factor_diag(p, base, min(CHP_NB, rest), a, z, &inv_s);
+            if (G == 1)
+                for (int tile = lead; tile < ntiles; ++tile) chp_update_tile(p, p0, nb, base, tile, pr, pq);
+        } else {
+            for (int tile = lead + blockIdx.x - 1; tile < ntiles; tile += G - 1)
+                chp_update_tile(p, p0, nb, base, tile, pr, pq);
         }
-        if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
     }
 }
 
