@@ -245,9 +245,7 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double* X, int m, int 
 // (B) every warp of the grid solves panel rows: L[r][p0..] = X[r][p0..] Z^*; (C) all CTAs
 // update the trailing lower triangle on 16 x 16 tiles, CTA 0 taking the tiles of the next
 // diagonal block and factoring it at once (lookahead). A grid-wide counter separates the
-// phases; every wait is bounded (RTPROJ_ETIMEOUT). The reciprocal square root of each
-// pivot starts from the float32 estimate and takes two Newton steps in float64
-// (y <- y (3 - d y^2) / 2), which doubles the correct bits each time.
+// phases; every wait is bounded (RTPROJ_ETIMEOUT).
 constexpr int CHP_THREADS = 256;
 constexpr int CHP_NB = 32;
 constexpr int CHP_TILE = 16;
@@ -295,22 +293,32 @@ __device__ bool chp_grid_sync(const CholPDev& p, unsigned int k, int* ok_s) {
     return *ok_s != 0;
 }
 
-// 1 / sqrt(d) for d > 0 in the float range: float32 estimate, two Newton steps in float64.
-__device__ __forceinline__ double rsqrt_newton(double d) {
-    double y = (double)rsqrtf((float)d);
-    y = y * fma(-0.5 * d, y * y, 1.5);
-    y = y * fma(-0.5 * d, y * y, 1.5);
-    return y;
+// 1 / sqrt(d) for a pivot d: the float32 estimate and one Newton step in float64,
+// y <- y (3 - d y^2) / 2, which squares the estimate's relative error (about 2^-45 after
+// the step: ample for a preconditioner factor that the refinement corrects). Outside
+// [2^-100, 2^100] the float64 library square root is used. A pivot that is not positive
+// and finite latches RTPROJ_ENOTSPD and is replaced by 1.
+__device__ __forceinline__ double pivot_rsqrt(double d, int* status) {
+    const long long bits = __double_as_longlong(d);
+    if (!(bits > 0 && bits < 0x7FF0000000000000ll)) {
+        set_status(status, RTPROJ_ENOTSPD);
+        return 1.0;
+    }
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex <= 1023 - 100 || ex >= 1023 + 100) return 1.0 / sqrt(d);
+    const double y = (double)rsqrtf((float)d);
+    return y * fma(-0.5 * d, y * y, 1.5);
 }
 
 // CTA-wide: factors the nb x nb diagonal block at (p0, p0) of X in shared memory (a) and
 // forms Z = L_pp^{-1} (z) in the same right-looking sweep, then writes L_pp (upper part
-// zero) back to X and Z to zbuf. Per column c: thread 0 takes the pivot (checked through
-// its bit pattern, so no float64 compare), every warp then scales and updates whole rows:
-// lane j of the warp holding row r updates Z[r][j] for j <= c and X[r][j] for c < j <= r,
-// one float64 instruction per row.
+// zero) back to X and Z to zbuf. Per column c: every warp scales, then updates whole rows
+// (lane j of the warp holding row r updates Z[r][j] for j <= c and X[r][j] for
+// c < j <= r, one float64 instruction per row). Row c+1 is updated first, by warp 0,
+// whose lane c+1 then takes the next pivot's reciprocal square root while the other
+// warps are still updating: the pivot chain overlaps the update.
 __device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[CHP_NB + 1], double (*z)[CHP_NB + 1],
-                                double* inv_s) {
+                                double* ys) {
     const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
         const int i = e / CHP_NB, j = e % CHP_NB;
@@ -318,24 +326,15 @@ __device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[C
         z[i][j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
+    if (t == 0) {
+        const double y = pivot_rsqrt(a[0][0], p.status);
+        ys[0] = y;
+        a[0][0] = a[0][0] * y;
+    }
+    __syncthreads();
     for (int c = 0; c < nb; ++c) {
-        if (t == 0) {
-            double d = a[c][c];
-            const long long bits = __double_as_longlong(d);
-            // positive, finite, and within the float range of the estimate
-            const bool ok = bits > 0 && bits < 0x7FF0000000000000ll;
-            if (!ok) {
-                set_status(p.status, RTPROJ_ENOTSPD);
-                d = 1.0;
-            }
-            const int ex = (int)((bits >> 52) & 0x7FF);
-            const double y = (ok && ex > 1023 - 100 && ex < 1023 + 100) ? rsqrt_newton(d) : 1.0 / sqrt(d);
-            *inv_s = y;
-            a[c][c] = d * y;                                   // sqrt(d)
-        }
-        __syncthreads();
-        const double y = *inv_s;
-        if (t > c && t < nb) a[t][c] *= y;                      // column c of L
+        const double y = ys[c];
+        if (t > c && t < nb) a[t][c] *= y;                                // column c of L
         else if (t >= CHP_NB && t - CHP_NB <= c) z[c][t - CHP_NB] *= y;   // row c of Z
         __syncthreads();
         for (int r = c + 1 + warp; r < nb; r += CHP_THREADS / 32) {
@@ -345,6 +344,13 @@ __device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[C
                 double* dst = j <= c ? &z[r][j] : &a[r][j];
                 const double src = j <= c ? z[c][j] : a[j][c];
                 *dst = fma(-lrc, src, *dst);
+            }
+            if (r == c + 1 && lane == r) {                             // the next pivot, now final
+                __threadfence_block();
+                const double d = a[r][r];
+                const double yn = pivot_rsqrt(d, p.status);
+                ys[r] = yn;
+                a[r][r] = d * yn;                                      // sqrt(d)
             }
         }
         __syncthreads();
@@ -391,12 +397,12 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
     __shared__ double z[CHP_NB][CHP_NB + 1];
     __shared__ double pr[CHP_TILE][CHP_NB + 1];
     __shared__ double pq[CHP_TILE][CHP_NB + 1];
-    __shared__ double inv_s;
+    __shared__ double ys[CHP_NB];
     __shared__ int ok_s;
     const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int G = gridDim.x;
     unsigned int nsync = 0;
-    if (blockIdx.x == 0) chp_factor_diag(p, 0, min(CHP_NB, m), a, z, &inv_s);
+    if (blockIdx.x == 0) chp_factor_diag(p, 0, min(CHP_NB, m), a, z, ys);
     for (int p0 = 0; p0 < m; p0 += CHP_NB) {
         const int nb = min(CHP_NB, m - p0);
         const int base = p0 + nb, rest = m - base;
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
         const int lead = ntiles < 3 ? ntiles : 3;
         if (blockIdx.x == 0) {
             for (int tile = 0; tile < lead; ++tile) chp_update_tile(p, p0, nb, base, tile, pr, pq);
-            chp_factor_diag(p, base, min(CHP_NB, rest), a, z, &inv_s);
+            chp_factor_diag(p, base, min(CHP_NB, rest), a, z, ys);
             if (G == 1)
                 for (int tile = lead; tile < ntiles; ++tile) chp_update_tile(p, p0, nb, base, tile, pr, pq);
         } else {
