@@ -11,7 +11,7 @@
 namespace rtp {
 namespace {
 
-constexpr int TRSM_NB = 4;        // right-hand-side columns per CTA
+constexpr int TRSM_NB = 2;        // right-hand-side columns per column block (two blocks per CTA)
 constexpr int TRSM_THREADS = 256;
 constexpr int TRSM_BS = 32;       // rows per diagonal block
 
@@ -68,70 +68,78 @@ __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int
                                                             double* B, int64_t b_rs, int ncols, const double* Dinv,
                                                             int rhs_lower) {
     extern __shared__ double x[];   // m * TRSM_NB
-    const int j0 = blockIdx.x * TRSM_NB;
-    const int nc = min(TRSM_NB, ncols - j0);
-    const int t = threadIdx.x;
-    for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
-        const int i = e / TRSM_NB, jj = e % TRSM_NB;
-        x[e] = jj < nc ? B[(int64_t)i * b_rs + j0 + jj] : 0.0;
-    }
-    __syncthreads();
-    const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
-    // A lower-triangular right-hand side (zero above its diagonal) gives a lower-triangular
-    // solution of a lower system: rows above this CTA's first column stay zero.
-    const int bi0 = (lower && rhs_lower) ? min(j0, m) / TRSM_BS : 0;
-    for (int bi = bi0; bi < nblk; ++bi) {
-        const int blk = lower ? bi : nblk - 1 - bi;
-        const int r0 = blk * TRSM_BS;
-        const int bs = min(TRSM_BS, m - r0);
-        // x_blk = Dinv_blk x_blk
-        double y = 0.0;
-        const int i = t / TRSM_NB, jj = t % TRSM_NB;
-        const bool act = t < TRSM_BS * TRSM_NB && i < bs;
-        if (act) {
-            const double* drow = Dinv + (size_t)blk * TRSM_BS * TRSM_BS + (size_t)i * TRSM_BS;
-#pragma unroll 8
-            for (int k = 0; k < TRSM_BS; ++k)
-                if (k < bs) y = fma(drow[k], x[(r0 + k) * TRSM_NB + jj], y);
+    // Column blocks in pairs (b, last - b): with a lower right-hand side the first blocks
+    // carry the most rows, so pairing evens out the work per CTA.
+    const int ncb = (ncols + TRSM_NB - 1) / TRSM_NB;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int cbk = pass == 0 ? (int)blockIdx.x : ncb - 1 - (int)blockIdx.x;
+        if (pass == 1 && cbk <= (int)blockIdx.x) break;
+        const int j0 = cbk * TRSM_NB;
+        const int nc = min(TRSM_NB, ncols - j0);
+        const int t = threadIdx.x;
+        for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
+            const int i = e / TRSM_NB, jj = e % TRSM_NB;
+            x[e] = jj < nc ? B[(int64_t)i * b_rs + j0 + jj] : 0.0;
         }
         __syncthreads();
-        if (act) x[(r0 + i) * TRSM_NB + jj] = y;
-        __syncthreads();
-        // rows not yet solved: below the block (lower) or above it (upper)
-        const int rbeg = lower ? r0 + bs : 0;
-        const int rend = lower ? m : r0;
-        for (int r = rbeg + t; r < rend; r += TRSM_THREADS) {
-            double acc[TRSM_NB];
-#pragma unroll
-            for (int q = 0; q < TRSM_NB; ++q) acc[q] = x[r * TRSM_NB + q];
-            const double* trow = T + (int64_t)r * t_rs + (int64_t)r0 * t_cs;
-            if (bs == TRSM_BS) {
-#pragma unroll
-                for (int k0 = 0; k0 < TRSM_BS; k0 += 8) {
-                    double tv[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) tv[q] = trow[(int64_t)(k0 + q) * t_cs];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-#pragma unroll
-                        for (int c = 0; c < TRSM_NB; ++c)
-                            acc[c] = fma(-tv[q], x[(r0 + k0 + q) * TRSM_NB + c], acc[c]);
-                }
-            } else {
-                for (int k = 0; k < bs; ++k) {
-                    const double tv = trow[(int64_t)k * t_cs];
-#pragma unroll
-                    for (int c = 0; c < TRSM_NB; ++c) acc[c] = fma(-tv, x[(r0 + k) * TRSM_NB + c], acc[c]);
-                }
+        const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
+        // A lower-triangular right-hand side (zero above its diagonal) gives a lower-triangular
+        // solution of a lower system: rows above this CTA's first column stay zero.
+        const int bi0 = (lower && rhs_lower) ? min(j0, m) / TRSM_BS : 0;
+        for (int bi = bi0; bi < nblk; ++bi) {
+            const int blk = lower ? bi : nblk - 1 - bi;
+            const int r0 = blk * TRSM_BS;
+            const int bs = min(TRSM_BS, m - r0);
+            // x_blk = Dinv_blk x_blk
+            double y = 0.0;
+            const int i = t / TRSM_NB, jj = t % TRSM_NB;
+            const bool act = t < TRSM_BS * TRSM_NB && i < bs;
+            if (act) {
+                const double* drow = Dinv + (size_t)blk * TRSM_BS * TRSM_BS + (size_t)i * TRSM_BS;
+    #pragma unroll 8
+                for (int k = 0; k < TRSM_BS; ++k)
+                    if (k < bs) y = fma(drow[k], x[(r0 + k) * TRSM_NB + jj], y);
             }
-#pragma unroll
-            for (int c = 0; c < TRSM_NB; ++c) x[r * TRSM_NB + c] = acc[c];
+            __syncthreads();
+            if (act) x[(r0 + i) * TRSM_NB + jj] = y;
+            __syncthreads();
+            // rows not yet solved: below the block (lower) or above it (upper)
+            const int rbeg = lower ? r0 + bs : 0;
+            const int rend = lower ? m : r0;
+            for (int r = rbeg + t; r < rend; r += TRSM_THREADS) {
+                double acc[TRSM_NB];
+    #pragma unroll
+                for (int q = 0; q < TRSM_NB; ++q) acc[q] = x[r * TRSM_NB + q];
+                const double* trow = T + (int64_t)r * t_rs + (int64_t)r0 * t_cs;
+                if (bs == TRSM_BS) {
+    #pragma unroll
+                    for (int k0 = 0; k0 < TRSM_BS; k0 += 8) {
+                        double tv[8];
+    #pragma unroll
+                        for (int q = 0; q < 8; ++q) tv[q] = trow[(int64_t)(k0 + q) * t_cs];
+    #pragma unroll
+                        for (int q = 0; q < 8; ++q)
+    #pragma unroll
+                            for (int c = 0; c < TRSM_NB; ++c)
+                                acc[c] = fma(-tv[q], x[(r0 + k0 + q) * TRSM_NB + c], acc[c]);
+                    }
+                } else {
+                    for (int k = 0; k < bs; ++k) {
+                        const double tv = trow[(int64_t)k * t_cs];
+    #pragma unroll
+                        for (int c = 0; c < TRSM_NB; ++c) acc[c] = fma(-tv, x[(r0 + k) * TRSM_NB + c], acc[c]);
+                    }
+                }
+    #pragma unroll
+                for (int c = 0; c < TRSM_NB; ++c) x[r * TRSM_NB + c] = acc[c];
+            }
+            __syncthreads();
+        }
+        for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
+            const int i = e / TRSM_NB, jj = e % TRSM_NB;
+            if (jj < nc) B[(int64_t)i * b_rs + j0 + jj] = x[e];
         }
         __syncthreads();
-    }
-    for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
-        const int i = e / TRSM_NB, jj = e % TRSM_NB;
-        if (jj < nc) B[(int64_t)i * b_rs + j0 + jj] = x[e];
     }
 }
 
@@ -447,7 +455,7 @@ cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
     const size_t smem = (size_t)m * TRSM_NB * sizeof(double);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
-    const unsigned grid = (unsigned)((ncols + TRSM_NB - 1) / TRSM_NB);
+    const unsigned grid = (unsigned)(((ncols + TRSM_NB - 1) / TRSM_NB + 1) / 2);
     if (lower) {
         tri_diag_inv_kernel<true><<<nblk, TRSM_BS, 0, s>>>(T, t_rs, t_cs, m, dinv_work, status);
         if (smem > 48 * 1024)
