@@ -175,6 +175,7 @@ constexpr int PQ_THREADS = 128;
 constexpr int PQ_WARPS = PQ_THREADS / 32;
 constexpr int PQ_MAXC = 32;
 constexpr int PQ_MAX_G = 256;
+constexpr int PQ_VLOAD = 5;             // slot entries per thread held in registers (l <= 640)
 
 struct PqrDev {
     double* S; int m, l; int64_t lds;
@@ -244,8 +245,9 @@ __device__ __forceinline__ void publish_candidate(const PqrDev& p, int b, int G,
         }
         ssq = warp_sum(ssq);
     }
-    __threadfence();
     if (lane == 0) redv[warp] = ssq;
+    // The CTA barrier orders every thread's slot writes before thread 0's release-add
+    // (release is cumulative), which publishes them at GPU scope.
     __syncthreads();
     if (t == 0) {
         double nsq = 0.0;
@@ -265,11 +267,10 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     __shared__ double s1[PQ_MAXC], s2[PQ_MAXC], wq[PQ_MAXC];   // squared norms: downdated, at last recompute
     __shared__ int posq[PQ_MAXC];
     __shared__ unsigned char doneq[PQ_MAXC];
-    __shared__ unsigned long long redb[PQ_WARPS];
+    __shared__ unsigned long long redb[2 * PQ_WARPS];
     __shared__ double redv[PQ_WARPS];
-    __shared__ int redi[PQ_WARPS];
-    __shared__ int piv_s, owner_s, ok_s, cand_s;
-    __shared__ double nsq_s;
+    __shared__ int redi[2 * PQ_WARPS];
+    __shared__ int ok_s, cand_s;
     const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int c0 = b * cpc;
     const int nc = max(0, min(cpc, m - c0));
@@ -321,35 +322,45 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
         }
-        if (lane == 0) { redb[warp] = best; redi[warp] = bi; }
+        if (lane == 0) { redb[par * PQ_WARPS + warp] = best; redi[par * PQ_WARPS + warp] = bi; }
         __syncthreads();
-        if (t == 0) {
-            unsigned long long bb = redb[0];
-            int ii = redi[0];
-            for (int w = 1; w < PQ_WARPS; ++w)
-                if (redi[w] < m && (ii == m || redb[w] > bb || (redb[w] == bb && redi[w] < ii))) {
-                    bb = redb[w];
-                    ii = redi[w];
-                }
-            piv_s = ii < m ? ii : -1;
-            owner_s = ii < m ? ii / cpc : -1;
-            nsq_s = __longlong_as_double((long long)bb);
+        // every thread combines the warps' results (double-buffered by step parity, so no
+        // second barrier is needed before they are overwritten)
+        unsigned long long bb = redb[par * PQ_WARPS];
+        int ii = redi[par * PQ_WARPS];
+        for (int w = 1; w < PQ_WARPS; ++w) {
+            const unsigned long long xb = redb[par * PQ_WARPS + w];
+            const int xi = redi[par * PQ_WARPS + w];
+            if (xi < m && (ii == m || xb > bb || (xb == bb && xi < ii))) { bb = xb; ii = xi; }
         }
-        __syncthreads();
-        const int piv = piv_s;
-        if (piv < 0) { alive = false; break; }             // cannot happen while columns remain
-        const int owner = owner_s;
+        if (ii >= m) { alive = false; break; }             // cannot happen while columns remain
+        const int piv = ii;
+        const int owner = ii / cpc;
+        const double nsq = __longlong_as_double((long long)bb);
         // 3. the reflector from the owner's slot (rows j .. l-1); every thread derives alpha
         //    and beta from the published squared norm and the slot's first entry
         const double* slot = p.slots + ((int64_t)par * G + owner) * l;
+        // the slot's loads are issued before the scalar chain so that their latency and the
+        // square root and division overlap (PQ_VLOAD entries per thread in registers)
+        double vr[PQ_VLOAD];
+#pragma unroll
+        for (int k = 0; k < PQ_VLOAD; ++k) {
+            const int i = j + t + k * PQ_THREADS;
+            vr[k] = i < l ? __ldcg(slot + i) : 0.0;
+        }
         const double x0 = __ldcg(slot + j);
-        const double nx = sqrt(nsq_s);
+        const double nx = sqrt(nsq);
         double alpha = 0.0, beta = 0.0;
         if (nx > 0.0) {
             alpha = x0 >= 0.0 ? -nx : nx;
             beta = 1.0 / (nx * (nx + fabs(x0)));
         }
-        for (int i = j + t; i < l; i += PQ_THREADS) v[i - j] = i == j ? x0 - alpha : __ldcg(slot + i);
+#pragma unroll
+        for (int k = 0; k < PQ_VLOAD; ++k) {
+            const int i = j + t + k * PQ_THREADS;
+            if (i < l) v[i - j] = i == j ? x0 - alpha : vr[k];
+        }
+        for (int i = j + t + PQ_VLOAD * PQ_THREADS; i < l; i += PQ_THREADS) v[i - j] = __ldcg(slot + i);
         if (t == 0 && owner == b) {
             const int q = piv - c0;
             cols[(size_t)q * l + j] = alpha;
