@@ -400,15 +400,13 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         __syncthreads();
         // 4b. the next candidate (largest downdated squared norm, lowest index on ties): all
         //     warps finish its update, copy it to the slot and the CTA arrives
-        if (t == 0) {
+        // (every thread evaluates the same choice over the nc <= cpc columns: no barrier)
+        int cand = -1;
+        {
             unsigned long long bestn = 0;
-            int bq = -1;
             for (int q = 0; q < nc; ++q)
-                if (posq[q] < 0 && (bq < 0 || sq_bits(s1[q]) > bestn)) { bestn = sq_bits(s1[q]); bq = q; }
-            cand_s = bq;
+                if (posq[q] < 0 && (cand < 0 || sq_bits(s1[q]) > bestn)) { bestn = sq_bits(s1[q]); cand = q; }
         }
-        __syncthreads();
-        const int cand = cand_s;
         publish_candidate(p, b, G, par ^ 1, j, cand, cand >= 0 ? cols + (size_t)cand * l : nullptr, v,
                           cand >= 0 ? wq[cand] : 0.0, cand >= 0 && doneq[cand], s1, s2, redv);
         // 4c. the remaining columns (overlapping the other CTAs' arrivals)
