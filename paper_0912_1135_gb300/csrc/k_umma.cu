@@ -573,6 +573,8 @@ constexpr int W_EPI_WARPS = 8;                  // two per TMEM lane quarter, 16
 constexpr int W_THREADS = 64 + 32 * W_EPI_WARPS;
 constexpr int W_MAX_A_STAGES = 16;
 constexpr int W_MAX_B_STAGES = 8;
+constexpr int A_PPS = 2;                       // A planes per pipeline slot (one TMA box, one barrier)
+constexpr int A_SLOT_BYTES = A_PPS * A_PLANE_BYTES;
 
 struct Sg2Dev {
     int M, N, Kp, sa, sb, terms, k_per_split, chunk_kb, splits;
@@ -796,7 +798,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     const uint32_t b_plane_bytes = (uint32_t)tn * KB * 2;
     const uint32_t b_stage_bytes = (uint32_t)p.sb * b_plane_bytes;
     unsigned char* sA = smem;
-    unsigned char* sB = sA + (size_t)AS * A_PLANE_BYTES;
+    unsigned char* sB = sA + (size_t)AS * A_SLOT_BYTES;
     uint64_t* bars = (uint64_t*)(sB + (size_t)BSN * b_stage_bytes);
     uint64_t* fullA = bars;
     uint64_t* emptyA = fullA + W_MAX_A_STAGES;
@@ -852,15 +854,16 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                 tma_load_3d_lane0(smem_addr(sB + (size_t)bs * b_stage_bytes), &tmB, k0, c.j0, 0, fullB + bs,
                                   b_stage_bytes);
                 ++b_it;
-                for (int pa = 0; pa < p.sa; ++pa) {
+                for (int pa = 0; pa < p.sa; pa += A_PPS) {
+                    // A_PPS planes per slot; a plane past the stack reads as zeros (no MMA uses it)
                     const int as = a_it % AS;
                     if (a_it >= (uint32_t)AS &&
                         !wait_phase_warp(emptyA + as, ((a_it / AS) - 1) & 1, abort_v, p.status, p.timeout)) {
                         ok = false;
                         break;
                     }
-                    tma_load_3d_lane0(smem_addr(sA + (size_t)as * A_PLANE_BYTES), &tmA, k0, c.i0, pa, fullA + as,
-                                      A_PLANE_BYTES);
+                    tma_load_3d_lane0(smem_addr(sA + (size_t)as * A_SLOT_BYTES), &tmA, k0, c.i0, pa, fullA + as,
+                                      A_SLOT_BYTES);
                     ++a_it;
                 }
             }
@@ -896,29 +899,32 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     break;
                 }
                 const uint32_t b_lo = b_lo0 + (uint32_t)bs * (b_stage_bytes >> 4);
-                for (int pa = 0; pa < p.sa; ++pa) {
+                for (int pa0 = 0; pa0 < p.sa; pa0 += A_PPS) {
                     const int as = a_it % AS;
                     if (!wait_phase_warp(fullA + as, (a_it / AS) & 1, abort_v, p.status, p.timeout)) {
                         ok = false;
                         break;
                     }
-                    tc_fence_after();
                     // Plane pa against B levels 0 .. nwin-1: one MMA per window of up to 256 / tn
                     // levels (N = tn per level), at most two windows. Descriptors are built from
                     // precomputed words: the K step adds 32 bytes (2 units) to the start address.
-                    const int nwin = min(p.sb, p.terms - pa);
-                    if (nwin > 0) {
-                        const int n1 = min(wmax, nwin), n2 = nwin - n1;
-                        const uint32_t a_lo = a_lo0 + (uint32_t)as * (A_PLANE_BYTES >> 4);
-                        const uint32_t d = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * tn);
-                        const uint32_t id1 = idesc_bf16(TM, n1 * tn), id2 = idesc_bf16(TM, (n2 > 0 ? n2 : 1) * tn);
 #pragma unroll
-                        for (int kk = 0; kk < KB / 16; ++kk) {
-                            const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
-                            const uint64_t ad = make_desc(a_lo + 2 * kk, desc_hi);
-                            umma_bf16_lane0(d, ad, make_desc(b_lo + 2 * kk, desc_hi), id1, acc);
-                            if (n2 > 0)
-                                umma_bf16_lane0(d + 256, ad, make_desc(b_lo + b_win + 2 * kk, desc_hi), id2, acc);
+                    for (int q = 0; q < A_PPS; ++q) {
+                        const int pa = pa0 + q;
+                        const int nwin = pa < p.sa ? min(p.sb, p.terms - pa) : 0;
+                        if (nwin > 0) {
+                            const int n1 = min(wmax, nwin), n2 = nwin - n1;
+                            const uint32_t a_lo = a_lo0 + (uint32_t)as * (A_SLOT_BYTES >> 4) + (uint32_t)q * (A_PLANE_BYTES >> 4);
+                            const uint32_t d = tmem + (uint32_t)buf * buf_cols + (uint32_t)(pa * tn);
+                            const uint32_t id1 = idesc_bf16(TM, n1 * tn), id2 = idesc_bf16(TM, (n2 > 0 ? n2 : 1) * tn);
+#pragma unroll
+                            for (int kk = 0; kk < KB / 16; ++kk) {
+                                const uint32_t acc = (chunk_start && pa == 0 && kk == 0) ? 0u : 1u;
+                                const uint64_t ad = make_desc(a_lo + 2 * kk, desc_hi);
+                                umma_bf16_lane0(d, ad, make_desc(b_lo + 2 * kk, desc_hi), id1, acc);
+                                if (n2 > 0)
+                                    umma_bf16_lane0(d + 256, ad, make_desc(b_lo + b_win + 2 * kk, desc_hi), id2, acc);
+                            }
                         }
                     }
                     umma_commit_lane0(emptyA + as);
@@ -1108,7 +1114,7 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     const bool short_k = Kp0 <= 1024 && N <= 64 && 2 * g.terms * 32 <= 512 && 2 * g.terms * 64 > 512;
     const int tn = (g.terms * 64 <= 512 && N > 32 && !short_k) ? 64 : 32;
     CUtensorMap mapA, mapB;
-    if (!make_stack_map(&mapA, g.a, TM, 1) || !make_stack_map(&mapB, g.b, tn, g.b.s))
+    if (!make_stack_map(&mapA, g.a, TM, A_PPS) || !make_stack_map(&mapB, g.b, tn, g.b.s))
         return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
     const int Kp = (K + KB - 1) / KB * KB;
     const int kchunk = chunk_for(g);
@@ -1141,16 +1147,17 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     const size_t budget = 220 * 1024 - fixed;
     int best_bs = 0, best_as = 0;
     double best_depth = -1.0;
+    const int a_slots_per_kb = (g.a.s + A_PPS - 1) / A_PPS;
     for (int bsn = 2; bsn <= W_MAX_B_STAGES; ++bsn) {
-        if ((size_t)bsn * b_stage + 2 * A_PLANE_BYTES > budget) break;
-        const int asn = (int)std::min<size_t>(W_MAX_A_STAGES, (budget - (size_t)bsn * b_stage) / A_PLANE_BYTES);
-        const double depth = std::min<double>(bsn, (double)asn / g.a.s);
+        if ((size_t)bsn * b_stage + 2 * A_SLOT_BYTES > budget) break;
+        const int asn = (int)std::min<size_t>(W_MAX_A_STAGES, (budget - (size_t)bsn * b_stage) / A_SLOT_BYTES);
+        const double depth = std::min<double>(bsn, (double)asn / a_slots_per_kb);
         if (depth > best_depth + 1e-9) { best_depth = depth; best_bs = bsn; best_as = asn; }
     }
     if (best_as < 2 || best_bs < 2) return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
     p.a_stages = best_as;
     p.b_stages = best_bs;
-    const size_t smem = fixed + (size_t)best_bs * b_stage + (size_t)best_as * A_PLANE_BYTES;
+    const size_t smem = fixed + (size_t)best_bs * b_stage + (size_t)best_as * A_SLOT_BYTES;
     cudaError_t e = cudaFuncSetAttribute(sliced_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     p.splits = splits;
