@@ -500,10 +500,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gemm_kernel(SgDev p) {
     const int i = i0 + warp * 32 + lane;
     if (i < p.M && !timed_out) {
         if (gridDim.z > 1) {
-            long long* dst = p.part + (((int64_t)z * p.M + i) * p.N + j0) * 2;
+            // split-K partials, column-major per split: entry (i, j) of split z at
+            // ((z N + j) M + i) * 2, so that a warp's 32 rows store contiguously
 #pragma unroll
             for (int j = 0; j < TN; ++j)
-                if (j0 + j < p.N) { dst[2 * j] = hi[j]; dst[2 * j + 1] = lo[j]; }
+                if (j0 + j < p.N)
+                    *reinterpret_cast<longlong2*>(p.part + (((int64_t)z * p.N + j0 + j) * p.M + i) * 2) =
+                        make_longlong2(hi[j], lo[j]);
         } else {
             const int ea = p.ea ? p.ea[i] : 0;
             const int64_t row = p.crow ? (int64_t)p.crow[i] : (int64_t)i;
@@ -536,12 +539,12 @@ __global__ void sliced_reduce_kernel(SgReduceDev r) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t total = (int64_t)r.M * r.N;
     if (idx >= total) return;
-    const int i = (int)(idx / r.N), j = (int)(idx % r.N);
+    const int j = (int)(idx / r.M), i = (int)(idx % r.M);   // consecutive threads: consecutive rows
     if (r.lower_only && j > i) return;
     __int128 acc = 0;
     for (int z = 0; z < r.splits; ++z) {
-        const long long* q = r.part + ((int64_t)z * total + idx) * 2;
-        acc += ((__int128)q[0] << 40) + (__int128)q[1];
+        const longlong2 q = *reinterpret_cast<const longlong2*>(r.part + ((int64_t)z * total + idx) * 2);
+        acc += ((__int128)q.x << 40) + (__int128)q.y;
     }
     const long long h = (long long)(acc >> 40);
     const long long l = (long long)(acc - ((__int128)h << 40));   // in [0, 2^40)
@@ -744,10 +747,11 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
         const bool valid = i < p.M;                 // rows past M: no output (but join the shuffles)
         if (p.splits > 1) {
             if (!valid) continue;
-            long long* dst = p.part + (((int64_t)c.z * p.M + i) * p.N + jb) * 2;
 #pragma unroll
             for (int j = 0; j < NCOL; ++j)
-                if (jb + j < p.N) { dst[2 * j] = (long long)hi[j]; dst[2 * j + 1] = (long long)lo[j]; }
+                if (jb + j < p.N)
+                    *reinterpret_cast<longlong2*>(p.part + (((int64_t)c.z * p.N + jb + j) * p.M + i) * 2) =
+                        make_longlong2((long long)hi[j], (long long)lo[j]);
         } else {
             // column exponents: one load per lane, shared through the warp
             const int ebl = (p.eb && lane < NCOL && jb + lane < p.N) ? p.eb[jb + lane] : 0;
