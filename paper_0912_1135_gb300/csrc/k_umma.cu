@@ -669,6 +669,19 @@ __device__ __forceinline__ bool wait_phase_warp(uint64_t* bar, uint32_t parity, 
     }
 }
 
+// Position in a ring of mbarrier-guarded stages: slot index, phase parity of the current
+// round, and whether a full round has passed (the producer's first round needs no wait).
+// Advanced incrementally: no division by the run-time stage count on the issue path.
+struct Ring {
+    int idx = 0, n = 1;
+    uint32_t phase = 0;
+    bool wrapped = false;
+    __device__ explicit Ring(int stages) : n(stages) {}
+    __device__ __forceinline__ void next() {
+        if (++idx == n) { idx = 0; phase ^= 1u; wrapped = true; }
+    }
+};
+
 // Tile order of the persistent loop. Tiles of one K split are enumerated either B-tile
 // fastest or A-tile fastest (m_fast: when there are no more A-row tiles than B-row
 // tiles, so that consecutive CTAs share the larger B tile through L2), and with
@@ -719,7 +732,7 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
     const int ntiles = per_z * p.splits;
     const int cb = p.chunk_kb;
     const uint32_t buf_cols = (uint32_t)(p.terms * tn);
-    int chunk = 0;
+    Ring tr(p.acc_bufs);
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
         const TileCoord c = ts.at(tile, per_z);
@@ -729,9 +742,9 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
         unsigned long long hi[NCOL], lo[NCOL];
 #pragma unroll
         for (int j = 0; j < NCOL; ++j) { hi[j] = 0; lo[j] = 0; }
-        for (int cc = 0; cc < nchunks; ++cc, ++chunk) {
-            const int buf = chunk % p.acc_bufs;
-            if (!wait_phase(tfull + buf, (chunk / p.acc_bufs) & 1, abort_v, p.status, p.timeout)) {
+        for (int cc = 0; cc < nchunks; ++cc, tr.next()) {
+            const int buf = tr.idx;
+            if (!wait_phase(tfull + buf, tr.phase, abort_v, p.status, p.timeout)) {
                 ok = false;
                 break;
             }
@@ -841,7 +854,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     // tiles strictly above the diagonal when only the lower triangle is wanted.
     if (warp == 0) {
         // ---------------- TMA producer (whole warp, lane 0 issues)
-        uint32_t a_it = 0, b_it = 0;
+        Ring ra(AS), rb(BSN);
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const TileCoord c = ts.at(tile, per_z);
@@ -849,26 +862,24 @@ __global__ void __launch_bounds__(W_THREADS, 1)
             const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 const int k0 = kbeg + kb * KB;
-                const int bs = b_it % BSN;
-                if (b_it >= (uint32_t)BSN &&
-                    !wait_phase_warp(emptyB + bs, ((b_it / BSN) - 1) & 1, abort_v, p.status, p.timeout)) {
+                const int bs = rb.idx;
+                if (rb.wrapped && !wait_phase_warp(emptyB + bs, rb.phase ^ 1u, abort_v, p.status, p.timeout)) {
                     ok = false;
                     break;
                 }
                 tma_load_3d_lane0(smem_addr(sB + (size_t)bs * b_stage_bytes), &tmB, k0, c.j0, 0, fullB + bs,
                                   b_stage_bytes);
-                ++b_it;
+                rb.next();
                 for (int pa = 0; pa < p.sa; pa += A_PPS) {
                     // A_PPS planes per slot; a plane past the stack reads as zeros (no MMA uses it)
-                    const int as = a_it % AS;
-                    if (a_it >= (uint32_t)AS &&
-                        !wait_phase_warp(emptyA + as, ((a_it / AS) - 1) & 1, abort_v, p.status, p.timeout)) {
+                    const int as = ra.idx;
+                    if (ra.wrapped && !wait_phase_warp(emptyA + as, ra.phase ^ 1u, abort_v, p.status, p.timeout)) {
                         ok = false;
                         break;
                     }
                     tma_load_3d_lane0(smem_addr(sA + (size_t)as * A_SLOT_BYTES), &tmA, k0, c.i0, pa, fullA + as,
                                       A_SLOT_BYTES);
-                    ++a_it;
+                    ra.next();
                 }
             }
         }
@@ -879,33 +890,33 @@ __global__ void __launch_bounds__(W_THREADS, 1)
         const uint32_t b_lo0 = (uint32_t)sw128_desc(smem_addr(sB));
         const int wmax = 256 / tn;                                     // levels per MMA window
         const uint32_t b_win = (uint32_t)wmax * (b_plane_bytes >> 4);  // second window's B offset
-        uint32_t a_it = 0, b_it = 0;
-        int chunk = 0, buf = 0;
+        Ring ra(AS), rb(BSN), rt(p.acc_bufs);
+        int buf = 0;
         bool ok = true;
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const TileCoord c = ts.at(tile, per_z);
             const int kbeg = c.z * p.k_per_split;
             const int nkb = (min(p.Kp, kbeg + p.k_per_split) - kbeg) / KB;
+            int kc = 0;                                  // k blocks into the current chunk
             for (int kb = 0; kb < nkb && ok; ++kb) {
-                const bool chunk_start = (kb % cb) == 0;
+                const bool chunk_start = kc == 0;
                 if (chunk_start) {
-                    buf = chunk % p.acc_bufs;
-                    if (chunk >= p.acc_bufs &&
-                        !wait_phase_warp(tempty + buf, ((chunk / p.acc_bufs) - 1) & 1, abort_v, p.status, p.timeout)) {
+                    buf = rt.idx;
+                    if (rt.wrapped && !wait_phase_warp(tempty + buf, rt.phase ^ 1u, abort_v, p.status, p.timeout)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                 }
-                const int bs = b_it % BSN;
-                if (!wait_phase_warp(fullB + bs, (b_it / BSN) & 1, abort_v, p.status, p.timeout)) {
+                const int bs = rb.idx;
+                if (!wait_phase_warp(fullB + bs, rb.phase, abort_v, p.status, p.timeout)) {
                     ok = false;
                     break;
                 }
                 const uint32_t b_lo = b_lo0 + (uint32_t)bs * (b_stage_bytes >> 4);
                 for (int pa0 = 0; pa0 < p.sa; pa0 += A_PPS) {
-                    const int as = a_it % AS;
-                    if (!wait_phase_warp(fullA + as, (a_it / AS) & 1, abort_v, p.status, p.timeout)) {
+                    const int as = ra.idx;
+                    if (!wait_phase_warp(fullA + as, ra.phase, abort_v, p.status, p.timeout)) {
                         ok = false;
                         break;
                     }
@@ -932,14 +943,15 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                         }
                     }
                     umma_commit_lane0(emptyA + as);
-                    ++a_it;
+                    ra.next();
                 }
                 if (!ok) break;
                 umma_commit_lane0(emptyB + bs);
-                ++b_it;
-                if ((kb % cb) == cb - 1 || kb == nkb - 1) {
+                rb.next();
+                if (++kc == cb || kb == nkb - 1) {
                     umma_commit_lane0(tfull + buf);
-                    ++chunk;
+                    rt.next();
+                    kc = 0;
                 }
             }
         }
