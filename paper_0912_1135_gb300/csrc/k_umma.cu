@@ -1120,15 +1120,11 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
                            g.b.ld % 64 == 0 && g.a.ld >= K && g.b.ld >= K;
     if (!shapes_ok || pipelined_disabled()) return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
     // 64 B rows per tile when the levels of one accumulator set fit TMEM at that width
-    // (terms * 64 <= 512 columns): half the A-plane reads per flop and twice the MMA work
-    // per pipeline stage; 32 otherwise.
-    // A short contraction into a narrow output (the A^* products: K = m, N = k <= 64) has
-    // few chunks per tile and a per-tile output with Cin: 32 rows then keep two
-    // accumulator sets in TMEM so that readout and output overlap the next tile's MMAs
-    // (measured faster there; slower for the Gram's wide output).
-    const int Kp0 = (K + KB - 1) / KB * KB;
-    const bool short_k = Kp0 <= 1024 && N <= 64 && 2 * g.terms * 32 <= 512 && 2 * g.terms * 64 > 512;
-    const int tn = (g.terms * 64 <= 512 && N > 32 && !short_k) ? 64 : 32;
+    // (terms * 64 <= 512 columns) and the output is wider than 64: half the A-plane reads
+    // per flop and twice the MMA work per pipeline stage. Narrow outputs (the apply
+    // products, N = k <= 64) take 32: the smaller B stage leaves shared memory for a
+    // deeper A ring and two TMEM accumulator sets (measured faster there).
+    const int tn = (g.terms * 64 <= 512 && N > 64) ? 64 : 32;
     CUtensorMap mapA, mapB;
     if (!make_stack_map(&mapA, g.a, TM, A_PPS) || !make_stack_map(&mapB, g.b, tn, g.b.s))
         return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
