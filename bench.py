@@ -262,6 +262,13 @@ def phase_work(mode, w, o):
     }
 
 
+# DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
+# `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu-baseline --no-accuracy --no-fp64-form`
+# on the 512 x 65536 workload (mixed form); to be replaced by None whenever that kernel
+# changes. Only the float64 QR's figure applies to both forms (the same kernel).
+PROFILED_TRAFFIC = {("dense_512x65536", "qr_persistent_kernel"): 2172160 + 154112}
+
+
 def roofline_entry(mode, phase_ms, phase_cnt, steps, w, pk, opts):
     """Per-phase achieved rate against its peak, and the entry for the dominant phase."""
     work = phase_work(mode, w, opts)
@@ -279,7 +286,8 @@ def roofline_entry(mode, phase_ms, phase_cnt, steps, w, pk, opts):
     e = dict(phases[dom])
     e.pop("ms_per_step")
     e["phase"] = dom
-    e["traffic"] = None
+    key = next((k for k in workloads.WORKLOADS if workloads.WORKLOADS[k].name == w.name), None)
+    e["traffic"] = PROFILED_TRAFFIC.get((key, e["kernel"])) if w.l == workloads.WORKLOADS.get(key, w).l else None
     e["peak_source"] = (f"{pk['_source']} bf16_tflops_sustained" if e["bound"] == "tensor"
                         else "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2070 MHz (FP64 pipe)")
     return e, phases
