@@ -189,7 +189,9 @@ cudaError_t gemm64(const Gemm64& g, double* part, size_t part_elems, cudaStream_
     if (g.K > 0) {
         const int tiles = tiles_m * tiles_n;
         const int want = std::max(1, (4 * 152 + tiles - 1) / tiles);
-        const int maxk = std::max(1, (g.K + 63) / 64);   // at least four 16-k steps per split
+        // Few output tiles (the m x m by m x k products of the apply): splits down to one
+        // 16-k step, so that the small FP64 products use every SM; otherwise at least four.
+        const int maxk = tiles < 32 ? std::max(1, (g.K + BK - 1) / BK) : std::max(1, (g.K + 63) / 64);
         splits = std::min(want, maxk);
         splits = (int)std::min<size_t>((size_t)splits, std::max<size_t>(1, part_elems / slab));
     }
