@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double* X, int m, int 
 }
 
 // ---------------------------------------------------------------------------------
-// Persistent blocked Cholesky: one cooperative launch for all panels of 32 columns.
+// Persistent blocked Cholesky: one cooperative launch for all panels of CHP_NB columns.
 // Per panel p0: (A) CTA 0 factors the diagonal block in shared memory and forms its
 // inverse Z = L_pp^{-1} in the same right-looking sweep (Gauss-Jordan on the identity);
 // (B) every warp of the grid solves panel rows: L[r][p0..] = X[r][p0..] Z^*; (C) all CTAs
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double* X, int m, int 
 // diagonal block and factoring it at once (lookahead). A grid-wide counter separates the
 // phases; every wait is bounded (RTPROJ_ETIMEOUT).
 constexpr int CHP_THREADS = 256;
-constexpr int CHP_NB = 32;
+constexpr int CHP_NB = 16;                 // panel width: the diagonal block's pivots run on one CTA
 constexpr int CHP_TILE = 16;
 
 struct CholPDev {
@@ -426,7 +426,7 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
 #pragma unroll
             for (int k = 0; k < CHP_NB; ++k) {
                 const double bk = __shfl_sync(0xffffffffu, b, k);
-                if (k <= lane) x = fma(bk, z[lane][k], x);
+                if (lane < CHP_NB && k <= lane) x = fma(bk, z[lane][k], x);
             }
             if (lane < nb) row[lane] = x;
         }
@@ -434,7 +434,8 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
         // trailing update; tiles 0-2 (the next diagonal block) on CTA 0, which then factors it
         const int nt = (rest + CHP_TILE - 1) / CHP_TILE;
         const int ntiles = nt * (nt + 1) / 2;
-        const int lead = ntiles < 3 ? ntiles : 3;
+        constexpr int kLead = (CHP_NB / CHP_TILE) * (CHP_NB / CHP_TILE + 1) / 2;   // tiles of the next block
+        const int lead = ntiles < kLead ? ntiles : kLead;
         if (blockIdx.x == 0) {
             for (int tile = 0; tile < lead; ++tile) chp_update_tile(p, p0, nb, base, tile, pr, pq);
             chp_factor_diag(p, base, min(CHP_NB, rest), a, z, ys);
