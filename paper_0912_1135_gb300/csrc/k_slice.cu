@@ -215,16 +215,23 @@ __device__ __forceinline__ void entry_digits(unsigned long long bits, int shift_
     dig[0] = neg ? -b0 : b0;
 }
 
-template <int S>
-__global__ void __launch_bounds__(SLF_THREADS) slice_rows_fast_kernel(SliceDev a) {
-    __shared__ unsigned long long smax[SLF_THREADS / 32];
-    __shared__ int sbad[SLF_THREADS / 32];
-    __shared__ int base_s;
-    const int r = blockIdx.x, t = threadIdx.x;
-    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.X + (int64_t)r * a.x_rs);
+// frexp exponent e of a maximum given as sign-cleared bits (max < 2^e <= 2 max): E - 1022
+// for a normal value, from the leading mantissa bit for a subnormal one; `zero` when 0.
+__device__ __forceinline__ int max_exponent(unsigned long long m2, int zero) {
+    const int E = (int)(m2 >> 52);
+    if (E > 0) return E - 1022;
+    if (m2 != 0) return (64 - __clzll((long long)m2)) - 1074;
+    return zero;
+}
+
+// Largest sign-cleared bit pattern and non-finite flag over columns [c0, c1) of a row,
+// reduced over the CTA; thread 0 receives the result.
+__device__ __forceinline__ void row_span_max(const unsigned long long* row, int c0, int c1, unsigned long long* smax,
+                                             int* sbad, unsigned long long* m_out, int* bad_out) {
+    const int t = threadIdx.x;
     unsigned long long mx = 0;
     int bad = 0;
-    for (int c = t; c < a.cols; c += SLF_THREADS) {
+    for (int c = c0 + t; c < c1; c += SLF_THREADS) {
         const unsigned long long u = __ldg(row + c) & 0x7FFFFFFFFFFFFFFFull;
         if (u >= 0x7FF0000000000000ull) bad = 1;
         else mx = u64_max(mx, u);
@@ -240,20 +247,18 @@ __global__ void __launch_bounds__(SLF_THREADS) slice_rows_fast_kernel(SliceDev a
         unsigned long long m2 = 0;
         int b2 = 0;
         for (int w = 0; w < SLF_THREADS / 32; ++w) { m2 = u64_max(m2, smax[w]); b2 |= sbad[w]; }
-        // e with max < 2^e <= 2 max (the frexp exponent): E - 1022 for a normal maximum,
-        // from the leading bit of the mantissa for a subnormal one, 0 for a zero row
-        int ex = 0;
-        const int E = (int)(m2 >> 52);
-        if (E > 0) ex = E - 1022;
-        else if (m2 != 0) ex = (64 - __clzll((long long)m2)) - 1074;
-        a.e[r] = ex;
-        base_s = 7 + 8 * (S - 1) - ex;
-        if (b2) set_status(a.status, RTPROJ_ENONFINITE);
+        *m_out = m2;
+        *bad_out = b2;
     }
-    __syncthreads();
-    const int base = base_s;
+}
+
+// Digits of columns [c_begin, c_end) of a row (c_begin a multiple of 8), eight per thread,
+// one 16-byte store per plane.
+template <int S>
+__device__ __forceinline__ void row_span_digits(const SliceDev& a, const unsigned long long* row, int r, int base,
+                                                int c_begin, int c_end) {
     __nv_bfloat16* drow = a.d + (int64_t)r * a.ld;
-    for (int c0 = 8 * t; c0 < a.ld; c0 += 8 * SLF_THREADS) {
+    for (int c0 = c_begin + 8 * threadIdx.x; c0 < c_end; c0 += 8 * SLF_THREADS) {
         uint32_t w[S][4];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -270,6 +275,57 @@ __global__ void __launch_bounds__(SLF_THREADS) slice_rows_fast_kernel(SliceDev a
     }
 }
 
+// One CTA per row (many rows).
+template <int S>
+__global__ void __launch_bounds__(SLF_THREADS) slice_rows_fast_kernel(SliceDev a) {
+    __shared__ unsigned long long smax[SLF_THREADS / 32];
+    __shared__ int sbad[SLF_THREADS / 32];
+    __shared__ unsigned long long m_s;
+    __shared__ int bad_s;
+    const int r = blockIdx.x;
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.X + (int64_t)r * a.x_rs);
+    row_span_max(row, 0, a.cols, smax, sbad, &m_s, &bad_s);
+    __syncthreads();
+    const int ex = max_exponent(m_s, 0);
+    if (threadIdx.x == 0) {
+        a.e[r] = ex;
+        if (bad_s) set_status(a.status, RTPROJ_ENONFINITE);
+    }
+    row_span_digits<S>(a, row, r, 7 + 8 * (S - 1) - ex, 0, (int)a.ld);
+}
+
+// Few rows: each row split over SLF_SPAN-column spans, one CTA per (span, row), in two
+// launches. The first takes each span's maximum exponent into e[r] (atomicMax over spans,
+// e pre-filled with SLF_ZERO_ROW), the second writes the digits of its span.
+constexpr int SLF_SPAN = 8 * SLF_THREADS;
+constexpr int SLF_ZERO_ROW = -(1 << 30);
+
+__global__ void __launch_bounds__(SLF_THREADS) slice_rows_exp_kernel(SliceDev a) {
+    __shared__ unsigned long long smax[SLF_THREADS / 32];
+    __shared__ int sbad[SLF_THREADS / 32];
+    __shared__ unsigned long long m_s;
+    __shared__ int bad_s;
+    const int r = blockIdx.y, c0 = blockIdx.x * SLF_SPAN;
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.X + (int64_t)r * a.x_rs);
+    row_span_max(row, c0, min(a.cols, c0 + SLF_SPAN), smax, sbad, &m_s, &bad_s);
+    if (threadIdx.x == 0) {
+        const int ex = max_exponent(m_s, SLF_ZERO_ROW);
+        if (ex != SLF_ZERO_ROW) atomicMax(a.e + r, ex);
+        if (bad_s) set_status(a.status, RTPROJ_ENONFINITE);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(SLF_THREADS) slice_rows_span_kernel(SliceDev a) {
+    const int r = blockIdx.y, c0 = blockIdx.x * SLF_SPAN;
+    const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.X + (int64_t)r * a.x_rs);
+    int ex = a.e[r];
+    if (ex == SLF_ZERO_ROW) ex = 0;                        // an all-zero row: exponent 0
+    __syncthreads();                                       // every thread has read e[r]
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.e[r] = ex;
+    row_span_digits<S>(a, row, r, 7 + 8 * (S - 1) - ex, c0, (int)min(a.ld, (int64_t)(c0 + SLF_SPAN)));
+}
+
 }  // namespace
 
 cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx, const int32_t* cexp,
@@ -283,7 +339,26 @@ cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_
     // 16-byte vector stores need 8-entry aligned planes and rows
     const bool fast = x_cs == 1 && !rowidx && !cexp && st.ld % 8 == 0 && st.plane_stride % 8 == 0 &&
                       ((uintptr_t)st.d & 15) == 0 && ((uintptr_t)X & 7) == 0;
-    if (fast) {
+    if (fast && st.rows < 2 * 152) {
+        // few rows: spread every row over several CTAs
+        const cudaError_t fe = fill_int(st.e, st.rows, SLF_ZERO_ROW, s);
+        if (fe != cudaSuccess) return fe;
+        const dim3 grid((unsigned)((st.ld + SLF_SPAN - 1) / SLF_SPAN), (unsigned)st.rows);
+        slice_rows_exp_kernel<<<grid, SLF_THREADS, 0, s>>>(a);
+        note_launch();
+        switch (st.s) {
+            case 1: slice_rows_span_kernel<1><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 2: slice_rows_span_kernel<2><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 3: slice_rows_span_kernel<3><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 4: slice_rows_span_kernel<4><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 5: slice_rows_span_kernel<5><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 6: slice_rows_span_kernel<6><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 7: slice_rows_span_kernel<7><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 8: slice_rows_span_kernel<8><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            case 9: slice_rows_span_kernel<9><<<grid, SLF_THREADS, 0, s>>>(a); break;
+            default: slice_rows_span_kernel<10><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        }
+    } else if (fast) {
         switch (st.s) {
             case 1: slice_rows_fast_kernel<1><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
             case 2: slice_rows_fast_kernel<2><<<st.rows, SLF_THREADS, 0, s>>>(a); break;
