@@ -1121,10 +1121,13 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     if (!shapes_ok || pipelined_disabled()) return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
     // 64 B rows per tile when the levels of one accumulator set fit TMEM at that width
     // (terms * 64 <= 512 columns) and the output is wider than 64: half the A-plane reads
-    // per flop and twice the MMA work per pipeline stage. Narrow outputs (the apply
-    // products, N = k <= 64) take 32: the smaller B stage leaves shared memory for a
-    // deeper A ring and two TMEM accumulator sets (measured faster there).
-    const int tn = (g.terms * 64 <= 512 && N > 64) ? 64 : 32;
+    // per flop and twice the MMA work per pipeline stage. 32 otherwise, and also when 64
+    // would leave a single TMEM accumulator set on a short contraction (K <= 1024: few
+    // chunks per tile, so the per-tile output must overlap the next tile's MMAs, which
+    // takes two sets). Both choices were measured faster where they apply.
+    const int Kp0 = (K + KB - 1) / KB * KB;
+    const bool wide_ok = g.terms * 64 <= 512 && N > 64 && (2 * g.terms * 64 <= 512 || Kp0 > 1024);
+    const int tn = wide_ok ? 64 : 32;
     CUtensorMap mapA, mapB;
     if (!make_stack_map(&mapA, g.a, TM, A_PPS) || !make_stack_map(&mapB, g.b, tn, g.b.s))
         return sliced_gemm_sync(g, scratch, scratch_bytes, status, s);
