@@ -234,7 +234,8 @@ __device__ __forceinline__ void publish_candidate(const PqrDev& p, int b, int G,
         const int first = j + 1, len1 = p.l - first;
         const int per = (len1 + PQ_WARPS - 1) / PQ_WARPS;
         const int lo = first + warp * per, hi = min(p.l, lo + per);
-        for (int i = lo + lane; i < hi; i += 32) {
+        double ssq1 = 0.0;
+        for (int i = lo + lane; i < hi; i += 64) {
             double x = col[i];
             if (!done) {
                 x = fma(-w, v[i - j], x);
@@ -242,16 +243,26 @@ __device__ __forceinline__ void publish_candidate(const PqrDev& p, int b, int G,
             }
             slot[i] = x;
             ssq = fma(x, x, ssq);
+            const int i2 = i + 32;
+            if (i2 < hi) {
+                double y = col[i2];
+                if (!done) {
+                    y = fma(-w, v[i2 - j], y);
+                    col[i2] = y;
+                }
+                slot[i2] = y;
+                ssq1 = fma(y, y, ssq1);
+            }
         }
-        ssq = warp_sum(ssq);
+        ssq = warp_sum(ssq + ssq1);
     }
     if (lane == 0) redv[warp] = ssq;
     // The CTA barrier orders every thread's slot writes before thread 0's release-add
     // (release is cumulative), which publishes them at GPU scope.
     __syncthreads();
     if (t == 0) {
-        double nsq = 0.0;
-        for (int k = 0; k < PQ_WARPS; ++k) nsq += redv[k];
+        static_assert(PQ_WARPS == 4, "pairwise sum written for four warps");
+        const double nsq = (redv[0] + redv[1]) + (redv[2] + redv[3]);
         if (q >= 0) { s1[q] = nsq; s2[q] = nsq; }
         p.bval[par1 * G + b] = q >= 0 ? nsq : 0.0;
         p.bidx[par1 * G + b] = q >= 0 ? b * p.cpc + q : p.m;
@@ -376,9 +387,16 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             if (posq[q] >= 0) continue;
             double* c = cols + (size_t)q * l + j;
             const double cj = c[0];
-            double w = 0.0;
-            for (int i = lane; i < len; i += 32) w = fma(v[i], c[i], w);
-            w = warp_sum(w) * beta;
+            // two independent partial sums: a dependent float64 chain costs more than the
+            // pipe's issue interval per step
+            double wa = 0.0, wb = 0.0;
+            int i = lane;
+            for (; i + 32 < len; i += 64) {
+                wa = fma(v[i], c[i], wa);
+                wb = fma(v[i + 32], c[i + 32], wb);
+            }
+            if (i < len) wa = fma(v[i], c[i], wa);
+            const double w = warp_sum(wa + wb) * beta;
             const double r = fma(-w, v[0], cj);
             const double sq = s1[q];
             const double sq_new = fma(-r, r, sq);

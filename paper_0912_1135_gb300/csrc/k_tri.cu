@@ -16,44 +16,50 @@ constexpr int TRSM_THREADS = 256;
 constexpr int TRSM_BS = 32;       // rows per diagonal block
 
 // Inverse of each 32 x 32 diagonal block of T (lower or upper), one warp per block:
-// lane j forms column j by substitution. Dinv[b] is row-major 32 x 32.
+// lane j forms column j by substitution, right-looking: once entry i of the column is
+// known, it is removed from the partial sums of the rows still to come, so every float64
+// instruction is an independent update (the pipe takes 64 cycles per warp instruction;
+// a predicated 32 x 32 loop or a dependent chain would cost more). The reciprocals of
+// the diagonal entries are formed once, independently of each other. Dinv[b] is
+// row-major 32 x 32.
 template <bool lower>
 __global__ void tri_diag_inv_kernel(const double* T, int64_t t_rs, int64_t t_cs, int m, double* Dinv, int* status) {
     const int b = blockIdx.x, j = threadIdx.x;
     const int r0 = b * TRSM_BS;
     const int bs = min(TRSM_BS, m - r0);
     double* out = Dinv + (size_t)b * TRSM_BS * TRSM_BS;
-    double col[TRSM_BS];
-#pragma unroll
-    for (int i = 0; i < TRSM_BS; ++i) col[i] = 0.0;
     auto D = [&](int i, int k) { return T[(int64_t)(r0 + i) * t_rs + (int64_t)(r0 + k) * t_cs]; };
+    // lane i holds 1 / D(i, i) (1 for rows past the block, which stay zero)
+    double rd = 1.0;
     if (j < bs) {
-        if (lower) {
+        double d = D(j, j);
+        if (!(d != 0.0) || !isfinite(d)) { set_status(status, RTPROJ_ENONFINITE); d = 1.0; }
+        rd = 1.0 / d;
+    }
+    double col[TRSM_BS];                   // partial sums, then the column
 #pragma unroll
-            for (int i = 0; i < TRSM_BS; ++i) {
-                if (i < j || i >= bs) continue;
-                double s = (i == j) ? 1.0 : 0.0;
+    for (int i = 0; i < TRSM_BS; ++i) col[i] = (i == j) ? 1.0 : 0.0;
+    if (lower) {
 #pragma unroll
-                for (int k = 0; k < TRSM_BS; ++k)
-                    if (k >= j && k < i) s = fma(-D(i, k), col[k], s);
-                double d = D(i, i);
-                if (!(d != 0.0) || !isfinite(d)) { set_status(status, RTPROJ_ENONFINITE); d = 1.0; }
-                col[i] = s / d;
-            }
-        } else {
+        for (int i = 0; i < TRSM_BS; ++i) {
+            const double ri = __shfl_sync(0xffffffffu, rd, i);
+            col[i] = (i < bs && i >= j) ? col[i] * ri : 0.0;
 #pragma unroll
-            for (int ii = TRSM_BS - 1; ii >= 0; --ii) {
-                const int i = ii;
-                if (i > j) continue;
-                double s = (i == j) ? 1.0 : 0.0;
-#pragma unroll
-                for (int k = 0; k < TRSM_BS; ++k)
-                    if (k > i && k <= j) s = fma(-D(i, k), col[k], s);
-                double d = D(i, i);
-                if (!(d != 0.0) || !isfinite(d)) { set_status(status, RTPROJ_ENONFINITE); d = 1.0; }
-                col[i] = s / d;
-            }
+            for (int r = i + 1; r < TRSM_BS; ++r)
+                if (r < bs) col[r] = fma(-D(r, i), col[i], col[r]);
         }
+    } else {
+#pragma unroll
+        for (int i = TRSM_BS - 1; i >= 0; --i) {
+            const double ri = __shfl_sync(0xffffffffu, rd, i);
+            col[i] = (i < bs && i <= j) ? col[i] * ri : 0.0;
+#pragma unroll
+            for (int r = 0; r < i; ++r) col[r] = fma(-D(r, i), col[i], col[r]);
+        }
+    }
+    if (j >= bs) {
+#pragma unroll
+        for (int i = 0; i < TRSM_BS; ++i) col[i] = 0.0;
     }
 #pragma unroll
     for (int i = 0; i < TRSM_BS; ++i) out[i * TRSM_BS + j] = col[i];
@@ -95,10 +101,17 @@ __global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int
             const int i = t / TRSM_NB, jj = t % TRSM_NB;
             const bool act = t < TRSM_BS * TRSM_NB && i < bs;
             if (act) {
+                // four independent partial sums (Dinv is zero outside the block)
                 const double* drow = Dinv + (size_t)blk * TRSM_BS * TRSM_BS + (size_t)i * TRSM_BS;
-    #pragma unroll 8
-                for (int k = 0; k < TRSM_BS; ++k)
+                double y1 = 0.0, y2 = 0.0, y3 = 0.0;
+    #pragma unroll
+                for (int k = 0; k < TRSM_BS; k += 4) {
                     if (k < bs) y = fma(drow[k], x[(r0 + k) * TRSM_NB + jj], y);
+                    if (k + 1 < bs) y1 = fma(drow[k + 1], x[(r0 + k + 1) * TRSM_NB + jj], y1);
+                    if (k + 2 < bs) y2 = fma(drow[k + 2], x[(r0 + k + 2) * TRSM_NB + jj], y2);
+                    if (k + 3 < bs) y3 = fma(drow[k + 3], x[(r0 + k + 3) * TRSM_NB + jj], y3);
+                }
+                y = (y + y1) + (y2 + y3);
             }
             __syncthreads();
             if (act) x[(r0 + i) * TRSM_NB + jj] = y;
