@@ -331,13 +331,33 @@ __device__ __forceinline__ double pivot_rsqrt(double d, int* status) {
     return y * fma(-0.5 * d, y * y, 1.5);
 }
 
+// Reciprocal 1/d of a pivot d: the float32 estimate and one Newton step in float64,
+// r <- r + r (1 - d r), which squares the estimate's relative error (about 2^-46 after the
+// step). Outside [2^-100, 2^100] the float64 division is used. A pivot that is not
+// positive and finite latches RTPROJ_ENOTSPD and is replaced by 1.
+__device__ __forceinline__ double pivot_rcp(double d, int* status) {
+    const long long bits = __double_as_longlong(d);
+    if (!(bits > 0 && bits < 0x7FF0000000000000ll)) {
+        set_status(status, RTPROJ_ENOTSPD);
+        return 1.0;
+    }
+    const int ex = (int)((bits >> 52) & 0x7FF);
+    if (ex <= 1023 - 100 || ex >= 1023 + 100) return 1.0 / d;
+    float rf;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"((float)d));
+    const double r = (double)rf;
+    return fma(r, fma(-d, r, 1.0), r);
+}
+
 // CTA-wide: factors the nb x nb diagonal block at (p0, p0) of X in shared memory (a) and
 // forms Z = L_pp^{-1} (z) in the same right-looking sweep, then writes L_pp (upper part
-// zero) back to X and Z to zbuf. Per column c: every warp scales, then updates whole rows
-// (lane j of the warp holding row r updates Z[r][j] for j <= c and X[r][j] for
-// c < j <= r, one float64 instruction per row). Row c+1 is updated first, by warp 0,
-// whose lane c+1 then takes the next pivot's reciprocal square root while the other
-// warps are still updating: the pivot chain overlaps the update.
+// zero) back to X and Z to zbuf. The sweep is the unscaled elimination X = L' D L'^*
+// (L' unit lower, D the pivots): per column c, with the multiplier L'[r][c] = a[r][c] / d_c,
+// row r of the trailing block loses L'[r][c] times column c (a) and row r of Z' = L'^{-1}
+// loses L'[r][c] times row c of Z' (z). Only 1/d_c is on the pivot chain: the lane that
+// updates the next pivot takes its reciprocal at once, and one barrier separates columns.
+// At the end L = L' D^{1/2} and Z = D^{-1/2} Z', with the reciprocal square roots of all
+// pivots formed in parallel.
 __device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[CHP_NB + 1], double (*z)[CHP_NB + 1],
                                 double* ys) {
     const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -347,39 +367,32 @@ __device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[C
         z[i][j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
-    if (t == 0) {
-        const double y = pivot_rsqrt(a[0][0], p.status);
-        ys[0] = y;
-        a[0][0] = a[0][0] * y;
-    }
+    if (t == 0) ys[0] = pivot_rcp(a[0][0], p.status);      // 1 / d_0
     __syncthreads();
-    for (int c = 0; c < nb; ++c) {
-        const double y = ys[c];
-        if (t > c && t < nb) a[t][c] *= y;                                // column c of L
-        else if (t >= CHP_NB && t - CHP_NB <= c) z[c][t - CHP_NB] *= y;   // row c of Z
-        __syncthreads();
+    for (int c = 0; c + 1 < nb; ++c) {
+        const double rc = ys[c];
         for (int r = c + 1 + warp; r < nb; r += CHP_THREADS / 32) {
-            const double lrc = a[r][c];
+            const double mrc = a[r][c] * rc;                 // L'[r][c]
             const int j = lane;
             if (j <= r) {
                 double* dst = j <= c ? &z[r][j] : &a[r][j];
                 const double src = j <= c ? z[c][j] : a[j][c];
-                *dst = fma(-lrc, src, *dst);
-            }
-            if (r == c + 1 && lane == r) {                             // the next pivot, now final
-                __threadfence_block();
-                const double d = a[r][r];
-                const double yn = pivot_rsqrt(d, p.status);
-                ys[r] = yn;
-                a[r][r] = d * yn;                                      // sqrt(d)
+                const double upd = fma(-mrc, src, *dst);
+                *dst = upd;
+                if (r == c + 1 && j == r) ys[r] = pivot_rcp(upd, p.status);   // the next pivot, now final
             }
         }
         __syncthreads();
     }
+    // 1 / sqrt(d_c) for every pivot, then L and Z scaled by them
+    const double yc = t < nb ? pivot_rsqrt(a[t][t], p.status) : 0.0;
+    __syncthreads();
+    if (t < nb) ys[t] = yc;
+    __syncthreads();
     for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
         const int i = e / CHP_NB, j = e % CHP_NB;
-        if (i < nb && j < nb) p.X[(int64_t)(p0 + i) * m + p0 + j] = j <= i ? a[i][j] : 0.0;
-        p.zbuf[e] = z[i][j];
+        if (i < nb && j < nb) p.X[(int64_t)(p0 + i) * m + p0 + j] = j <= i ? a[i][j] * ys[j] : 0.0;
+        p.zbuf[e] = (i < nb) ? z[i][j] * ys[i] : z[i][j];
     }
 }
 
@@ -400,11 +413,17 @@ __device__ void chp_update_tile(const CholPDev& p, int p0, int nb, int base, int
     const int i = t / CHP_TILE, j = t % CHP_TILE;
     const int r = r0 + i, q = q0 + j;
     if (r < m && q <= r) {
-        double acc = 0.0;
-#pragma unroll
-        for (int c = 0; c < CHP_NB; ++c) acc = fma(pr[i][c], pq[j][c], acc);
         double* xp = p.X + (int64_t)r * m + q;
-        *xp = __ldcg(xp) - acc;
+        const double x0 = __ldcg(xp);
+        double acc0 = 0.0, acc1 = 0.0, acc2 = 0.0, acc3 = 0.0;   // independent partial sums
+#pragma unroll
+        for (int c = 0; c < CHP_NB; c += 4) {
+            acc0 = fma(pr[i][c], pq[j][c], acc0);
+            acc1 = fma(pr[i][c + 1], pq[j][c + 1], acc1);
+            acc2 = fma(pr[i][c + 2], pq[j][c + 2], acc2);
+            acc3 = fma(pr[i][c + 3], pq[j][c + 3], acc3);
+        }
+        *xp = x0 - ((acc0 + acc1) + (acc2 + acc3));
     }
     __syncthreads();
 }
@@ -435,13 +454,15 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
         for (int r = base + blockIdx.x * (CHP_THREADS / 32) + warp; r < m; r += G * (CHP_THREADS / 32)) {
             double* row = p.X + (int64_t)r * m + p0;
             const double b = lane < nb ? __ldcg(row + lane) : 0.0;
-            double x = 0.0;
+            double x0 = 0.0, x1 = 0.0;                          // independent partial sums
 #pragma unroll
-            for (int k = 0; k < CHP_NB; ++k) {
-                const double bk = __shfl_sync(0xffffffffu, b, k);
-                if (lane < CHP_NB && k <= lane) x = fma(bk, z[lane][k], x);
+            for (int k = 0; k < CHP_NB; k += 2) {
+                const double bk0 = __shfl_sync(0xffffffffu, b, k);
+                const double bk1 = __shfl_sync(0xffffffffu, b, k + 1);
+                if (lane < CHP_NB && k <= lane) x0 = fma(bk0, z[lane][k], x0);
+                if (lane < CHP_NB && k + 1 <= lane) x1 = fma(bk1, z[lane][k + 1], x1);
             }
-            if (lane < nb) row[lane] = x;
+            if (lane < nb) row[lane] = x0 + x1;
         }
         if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
         // trailing update; tiles 0-2 (the next diagonal block) on CTA 0, which then factors it
