@@ -155,22 +155,28 @@ __global__ void qr_extract_r_kernel(const double* S, int m, int64_t lds, double*
 // ---------------------------------------------------------------------------------
 // Persistent form: one cooperative launch for all m steps. CTA b keeps columns
 // [b*cpc, b*cpc + cpc) of S^* (rows of S) in shared memory for the whole factorization,
-// one warp per column. A step costs one grid-wide exchange. Before arriving for step j,
-// each CTA publishes its candidate: its remaining column with the largest downdated
-// squared norm (lowest index on ties), fully updated through step j-1 by all its warps,
-// copied to the CTA's slot in global memory together with its exactly recomputed squared
-// tail norm. After everyone has arrived, each CTA picks the global pivot among the
-// candidates (largest squared norm, lowest column index on ties), reads that column from
-// its owner's slot, forms the reflector itself (all CTAs compute bitwise the same alpha,
-// beta and v) and applies it: first the row-j entry of each active column, so that the
-// squared norms are downdated (LAPACK's rule, in squares: no division, no square root)
-// and the next candidate is known early; the candidate's full update, slot copy and
-// arrival follow, and the other columns' updates overlap the wait. Columns never move:
-// the pivot column is retired and R[:, j] is the retired column's first j+1 entries.
-// Slots and candidates alternate between two buffers by step parity. Every wait has a
-// clock deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all CTAs leave their
-// loops. (GB300's FP64 pipe takes 64 cycles per warp instruction, active lanes or not,
-// so the step is arranged to keep float64 instructions off its critical path.)
+// one warp per column, and consecutive steps are separated by one grid-wide exchange.
+// The pivot rule is the textbook one (Businger-Golub with the norms recomputed every
+// step): the pivot of step j is the remaining column whose trailing rows j .. l-1 have
+// the largest squared norm, lowest index on ties. Step j in CTA b:
+//  1. wait until every CTA has arrived for step j, read the G candidates (one per CTA:
+//     its best remaining column's index and exact squared norm) and pick the pivot;
+//  2. read the pivot column (rows j .. l-1) from its staging slot; every CTA derives the
+//     same alpha = -sign(x_j) ||x|| and beta = 1 / (||x|| (||x|| + |x_j|)) from the
+//     published squared norm and forms v = x - alpha e_j;
+//  3. every warp applies I - beta v v^* to its column (row j becomes the R entry), and
+//     in the same pass recomputes the column's squared norm over rows j+1 .. l-1 and
+//     copies those rows to the column's staging slot for step j+1;
+//  4. thread 0 publishes the CTA's best remaining column (index and squared norm) and
+//     arrives.
+// So the candidate's update, norm and copy run in parallel with the other columns' (one
+// warp each) instead of after them. Columns never move: the pivot column is retired and
+// R[:, j] is the retired column's first j+1 entries. Staging slots and candidates
+// alternate between two buffers by step parity (a retired column's slot is never
+// rewritten, so late readers of a pivot column are safe). Every wait has a clock
+// deadline; on expiry the kernel raises RTPROJ_ETIMEOUT and all CTAs leave their loops.
+// (GB300's FP64 pipe takes 64 cycles per warp instruction, active lanes or not, so long
+// float64 chains are split into independent partial sums.)
 constexpr int PQ_THREADS = 128;
 constexpr int PQ_WARPS = PQ_THREADS / 32;
 constexpr int PQ_MAXC = 32;
@@ -181,7 +187,7 @@ struct PqrDev {
     double* S; int m, l; int64_t lds;
     double* R; int32_t* perm;
     int cpc;
-    double* slots;           // 2 x G x l: candidate columns by step parity
+    double* slots;           // 2 x G x cpc x l: staging copies of the columns by step parity
     double* bval;            // 2 x G: candidate squared tail norms
     int* bidx;               // 2 x G: candidate column indices (m = none)
     unsigned int* counter;   // arrivals (monotonic)
@@ -220,54 +226,20 @@ __device__ bool wait_geq(const unsigned int* p, unsigned int target, int* abort_
 // integer order is the numeric order, and integer compares stay off the FP64 pipe.
 __device__ __forceinline__ unsigned long long sq_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-// Candidate of this CTA for step j + 1 (parity par1): local column q (or none when q < 0),
-// finishing its update with w (unless `done`) and copying rows j+1 .. l-1 to the slot;
-// all warps share the rows. Its squared tail norm is recomputed exactly and published.
-// Called by every thread of the CTA.
-__device__ __forceinline__ void publish_candidate(const PqrDev& p, int b, int G, int par1, int j, int q, double* col,
-                                                  const double* v, double w, bool done, double* s1, double* s2,
-                                                  double* redv) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    double ssq = 0.0;
-    if (q >= 0) {
-        double* slot = p.slots + ((int64_t)par1 * G + b) * p.l;
-        const int first = j + 1, len1 = p.l - first;
-        const int per = (len1 + PQ_WARPS - 1) / PQ_WARPS;
-        const int lo = first + warp * per, hi = min(p.l, lo + per);
-        double ssq1 = 0.0;
-        for (int i = lo + lane; i < hi; i += 64) {
-            double x = col[i];
-            if (!done) {
-                x = fma(-w, v[i - j], x);
-                col[i] = x;
-            }
-            slot[i] = x;
-            ssq = fma(x, x, ssq);
-            const int i2 = i + 32;
-            if (i2 < hi) {
-                double y = col[i2];
-                if (!done) {
-                    y = fma(-w, v[i2 - j], y);
-                    col[i2] = y;
-                }
-                slot[i2] = y;
-                ssq1 = fma(y, y, ssq1);
-            }
-        }
-        ssq = warp_sum(ssq + ssq1);
-    }
-    if (lane == 0) redv[warp] = ssq;
-    // The CTA barrier orders every thread's slot writes before thread 0's release-add
-    // (release is cumulative), which publishes them at GPU scope.
-    __syncthreads();
-    if (t == 0) {
-        static_assert(PQ_WARPS == 4, "pairwise sum written for four warps");
-        const double nsq = (redv[0] + redv[1]) + (redv[2] + redv[3]);
-        if (q >= 0) { s1[q] = nsq; s2[q] = nsq; }
-        p.bval[par1 * G + b] = q >= 0 ? nsq : 0.0;
-        p.bidx[par1 * G + b] = q >= 0 ? b * p.cpc + q : p.m;
-        red_release_add(p.counter, 1u);
-    }
+// Thread 0, after the CTA barrier that follows the columns' updates: publishes the best
+// remaining local column for step s (largest squared norm, lowest index on ties) and
+// arrives. The barrier orders every thread's staging-slot writes before the release-add
+// (release is cumulative), which publishes them at GPU scope.
+__device__ __forceinline__ void publish_best(const PqrDev& p, int b, int G, int s, int nc, const int* posq,
+                                             const double* nsq) {
+    unsigned long long best = 0;
+    int bq = -1;
+    for (int q = 0; q < nc; ++q)
+        if (posq[q] < 0 && (bq < 0 || sq_bits(nsq[q]) > best)) { best = sq_bits(nsq[q]); bq = q; }
+    const int par = s & 1;
+    p.bval[par * G + b] = bq >= 0 ? nsq[bq] : 0.0;
+    p.bidx[par * G + b] = bq >= 0 ? b * p.cpc + bq : p.m;
+    red_release_add(p.counter, 1u);
 }
 
 __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) {
@@ -275,41 +247,37 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     const int l = p.l, m = p.m, cpc = p.cpc;
     double* cols = smem_d;                 // cpc x l
     double* v = cols + (size_t)cpc * l;    // l
-    __shared__ double s1[PQ_MAXC], s2[PQ_MAXC], wq[PQ_MAXC];   // squared norms: downdated, at last recompute
-    __shared__ int posq[PQ_MAXC];
-    __shared__ unsigned char doneq[PQ_MAXC];
+    __shared__ double nsq[PQ_MAXC];        // squared norm of rows j+1 .. l-1 (exact, this step)
+    __shared__ int posq[PQ_MAXC];          // step at which the column was retired, -1 while active
     __shared__ unsigned long long redb[2 * PQ_WARPS];
-    __shared__ double redv[PQ_WARPS];
     __shared__ int redi[2 * PQ_WARPS];
-    __shared__ int ok_s, cand_s;
+    __shared__ int ok_s;
     const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int c0 = b * cpc;
     const int nc = max(0, min(cpc, m - c0));
-    const double tol3z = 1.4901161193847656e-08;   // sqrt(eps): LAPACK's recompute threshold
+    const size_t slot_par = (size_t)G * cpc * l;   // doubles per parity buffer
 
     for (int q = 0; q < nc; ++q)
-        for (int i = t; i < l; i += PQ_THREADS) cols[(size_t)q * l + i] = p.S[(int64_t)(c0 + q) * p.lds + i];
+        for (int i = t; i < l; i += PQ_THREADS) {
+            const double x = p.S[(int64_t)(c0 + q) * p.lds + i];
+            cols[(size_t)q * l + i] = x;
+            p.slots[((size_t)b * cpc + q) * l + i] = x;           // step 0's staging copy
+        }
     __syncthreads();
     for (int q = warp; q < nc; q += PQ_WARPS) {
         const double* c = cols + (size_t)q * l;
-        double s = 0.0;
-        for (int i = lane; i < l; i += 32) s = fma(c[i], c[i], s);
-        s = warp_sum(s);
-        if (lane == 0) { s1[q] = s; s2[q] = s; posq[q] = -1; }
+        double s0 = 0.0, s1 = 0.0;
+        int i = lane;
+        for (; i + 32 < l; i += 64) {
+            s0 = fma(c[i], c[i], s0);
+            s1 = fma(c[i + 32], c[i + 32], s1);
+        }
+        if (i < l) s0 = fma(c[i], c[i], s0);
+        const double s = warp_sum(s0 + s1);
+        if (lane == 0) { nsq[q] = s; posq[q] = -1; }
     }
     __syncthreads();
-    if (t == 0) {
-        unsigned long long best = 0;
-        int bq = -1;
-        for (int q = 0; q < nc; ++q)
-            if (bq < 0 || sq_bits(s1[q]) > best) { best = sq_bits(s1[q]); bq = q; }
-        cand_s = bq;
-    }
-    __syncthreads();
-    {
-        const int q = cand_s;
-        publish_candidate(p, b, G, 0, -1, q, q >= 0 ? cols + (size_t)q * l : nullptr, v, 0.0, true, s1, s2, redv);
-    }
+    if (t == 0) publish_best(p, b, G, 0, nc, posq, nsq);
 
     bool alive = true;
     for (int j = 0; j < m && alive; ++j) {
@@ -319,7 +287,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
                                      p.timeout);
         __syncthreads();
         if (!ok_s) { alive = false; break; }
-        // 2. global pivot: largest squared norm, lowest column index on ties
+        // global pivot: largest squared norm, lowest column index on ties
         unsigned long long best = 0;
         int bi = m;
         for (int g = t; g < G; g += PQ_THREADS) {
@@ -346,11 +314,9 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         }
         if (ii >= m) { alive = false; break; }             // cannot happen while columns remain
         const int piv = ii;
-        const int owner = ii / cpc;
-        const double nsq = __longlong_as_double((long long)bb);
-        // 3. the reflector from the owner's slot (rows j .. l-1); every thread derives alpha
-        //    and beta from the published squared norm and the slot's first entry
-        const double* slot = p.slots + ((int64_t)par * G + owner) * l;
+        const double nsq_piv = __longlong_as_double((long long)bb);
+        // 2. the reflector from the pivot column's staging slot (rows j .. l-1)
+        const double* slot = p.slots + (size_t)par * slot_par + (size_t)piv * l;
         // the slot's loads are issued before the scalar chain so that their latency and the
         // square root and division overlap (PQ_VLOAD entries per thread in registers)
         double vr[PQ_VLOAD];
@@ -360,7 +326,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             vr[k] = i < l ? __ldcg(slot + i) : 0.0;
         }
         const double x0 = __ldcg(slot + j);
-        const double nx = sqrt(nsq);
+        const double nx = sqrt(nsq_piv);
         double alpha = 0.0, beta = 0.0;
         if (nx > 0.0) {
             alpha = x0 >= 0.0 ? -nx : nx;
@@ -372,7 +338,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             if (i < l) v[i - j] = i == j ? x0 - alpha : vr[k];
         }
         for (int i = j + t + PQ_VLOAD * PQ_THREADS; i < l; i += PQ_THREADS) v[i - j] = __ldcg(slot + i);
-        if (t == 0 && owner == b) {
+        if (t == 0 && piv >= c0 && piv < c0 + nc) {
             const int q = piv - c0;
             cols[(size_t)q * l + j] = alpha;
             posq[q] = j;
@@ -380,15 +346,12 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         }
         __syncthreads();
         const int len = l - j;
-        // 4a. row j of each active column and its downdated squared norm s1 - r^2; when the
-        //     downdate falls to tol3z times the norm at the last recompute (LAPACK's test on
-        //     the ratio), the column is updated in full here and its norm recomputed
+        // 3. each active column: w = beta v^* c, c <- c - w v (row j is the R entry), the
+        //    squared norm of rows j+1 .. l-1 and their copy to the staging slot of step j+1
+        double* next = p.slots + (size_t)(par ^ 1) * slot_par;
         for (int q = warp; q < nc; q += PQ_WARPS) {
             if (posq[q] >= 0) continue;
             double* c = cols + (size_t)q * l + j;
-            const double cj = c[0];
-            // two independent partial sums: a dependent float64 chain costs more than the
-            // pipe's issue interval per step
             double wa = 0.0, wb = 0.0;
             int i = lane;
             for (; i + 32 < len; i += 64) {
@@ -397,44 +360,30 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             }
             if (i < len) wa = fma(v[i], c[i], wa);
             const double w = warp_sum(wa + wb) * beta;
-            const double r = fma(-w, v[0], cj);
-            const double sq = s1[q];
-            const double sq_new = fma(-r, r, sq);
-            const bool recompute = sq != 0.0 && sq_new <= tol3z * s2[q];
-            if (recompute) {
-                double ss = 0.0;
-                for (int i = 1 + lane; i < len; i += 32) {
-                    const double x = fma(-w, v[i], c[i]);
-                    c[i] = x;
-                    ss = fma(x, x, ss);
+            double* dst = next + ((size_t)b * cpc + q) * l + j;
+            double s0 = 0.0, s1 = 0.0;
+            for (i = 1 + lane; i < len; i += 64) {
+                const double x = fma(-w, v[i], c[i]);
+                c[i] = x;
+                dst[i] = x;
+                s0 = fma(x, x, s0);
+                const int i2 = i + 32;
+                if (i2 < len) {
+                    const double y = fma(-w, v[i2], c[i2]);
+                    c[i2] = y;
+                    dst[i2] = y;
+                    s1 = fma(y, y, s1);
                 }
-                ss = warp_sum(ss);
-                if (lane == 0) { s1[q] = ss; s2[q] = ss; }
-            } else if (lane == 0 && sq != 0.0) {
-                s1[q] = sq_new;
             }
-            if (lane == 0) { c[0] = r; wq[q] = w; doneq[q] = recompute ? 1 : 0; }
+            const double ssq = warp_sum(s0 + s1);
+            if (lane == 0) {
+                c[0] = fma(-w, v[0], c[0]);
+                nsq[q] = ssq;
+            }
         }
         __syncthreads();
-        // 4b. the next candidate (largest downdated squared norm, lowest index on ties): all
-        //     warps finish its update, copy it to the slot and the CTA arrives
-        // (every thread evaluates the same choice over the nc <= cpc columns: no barrier)
-        int cand = -1;
-        {
-            unsigned long long bestn = 0;
-            for (int q = 0; q < nc; ++q)
-                if (posq[q] < 0 && (cand < 0 || sq_bits(s1[q]) > bestn)) { bestn = sq_bits(s1[q]); cand = q; }
-        }
-        publish_candidate(p, b, G, par ^ 1, j, cand, cand >= 0 ? cols + (size_t)cand * l : nullptr, v,
-                          cand >= 0 ? wq[cand] : 0.0, cand >= 0 && doneq[cand], s1, s2, redv);
-        // 4c. the remaining columns (overlapping the other CTAs' arrivals)
-        for (int q = warp; q < nc; q += PQ_WARPS) {
-            if (posq[q] >= 0 || q == cand || doneq[q]) continue;
-            double* c = cols + (size_t)q * l + j;
-            const double w = wq[q];
-            for (int i = 1 + lane; i < len; i += 32) c[i] = fma(-w, v[i], c[i]);
-        }
-        __syncthreads();
+        // 4. the CTA's candidate for step j+1
+        if (t == 0) publish_best(p, b, G, j + 1, nc, posq, nsq);
     }
     if (!alive) return;
     // R[:, pos] = first pos+1 entries of the retired column
@@ -475,7 +424,8 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
 
 size_t pivoted_qr_work_doubles(int m, int l) {
     const size_t steps = (size_t)3 * m + 3 * (size_t)l + 2048;                       // per-step form
-    const size_t persistent = (size_t)2 * PQ_MAX_G * l + 4 * (size_t)PQ_MAX_G + 64;   // slots, candidates
+    // staging slots (G * cpc < m + cpc columns per parity), candidates, counter and flag
+    const size_t persistent = (size_t)2 * ((size_t)m + PQ_MAXC) * l + 4 * (size_t)PQ_MAX_G + 64;
     return steps > persistent ? steps : persistent;
 }
 
@@ -499,7 +449,7 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 PqrDev p;
                 p.S = S; p.m = m; p.l = l; p.lds = lds; p.R = R; p.perm = perm; p.cpc = cpc;
                 double* w = work;
-                p.slots = w;                    w += (size_t)2 * G * l;
+                p.slots = w;                    w += (size_t)2 * G * cpc * l;
                 p.bval = w;                     w += 2 * (size_t)G;
                 p.bidx = (int*)w;               w += G;          // 2G ints
                 unsigned int* ctr = (unsigned int*)w;            // counter, abort
