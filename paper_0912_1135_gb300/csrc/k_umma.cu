@@ -595,6 +595,7 @@ struct Sg2Dev {
     int tn;                       // B rows per tile: 32 or 64
     int m_fast;                   // tile order: A-row tiles fastest
     int vec2;                     // C rows contiguous and 16-byte aligned: paired stores
+    int issue_cfg;                // compile-time MMA issue path (0: the general loop)
 };
 
 
@@ -621,6 +622,15 @@ __device__ __forceinline__ void umma_bf16_lane0(uint32_t d_tmem, uint64_t a_desc
         "setp.ne.b32 p, %4, 0;\n\t"
         "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void umma_bf16_lane0_acc(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc) {
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t.reg .u32 l;\n\t"
+        "mov.u32 l, %%laneid;\n\t"
+        "setp.eq.u32 e, l, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, 1;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit_lane0(uint64_t* bar) {
@@ -723,6 +733,56 @@ struct TileSched {
 // Epilogue role of one warp: NCOL = tn / 2 columns of each tile, for TMEM lanes
 // 32 * quarter ... + 31 (tile rows), chunk by chunk, then the tile's partial words or its
 // final values.
+// The MMA issuer's work on one k block for a fixed digit configuration (SA A planes,
+// TERMS levels, TN B rows per level): A slots SLOT, SLOT+1, ... are awaited in turn and
+// each of their planes pa meets B levels 0 .. TERMS-pa-1 in windows of 256/TN levels, four
+// K steps of 16. Plane, window and K offsets, instruction descriptors and the accumulate
+// flag are compile-time constants, so between two MMAs the issuing warp only adds a
+// constant to a base: with the general loop's run-time bounds the issue path, not the
+// tensor pipe, set the pace for windows narrower than 256 columns. Returns false on abort.
+template <int SA, int TERMS, int TN, int SLOT = 0>
+__device__ __forceinline__ bool issue_kblock(Ring& ra, uint32_t a_lo0, uint32_t b_lo, uint32_t desc_hi, uint32_t dbase,
+                                             uint32_t acc0, uint64_t* fullA, uint64_t* emptyA, volatile int* abort_v,
+                                             const Sg2Dev& p) {
+    constexpr int WMAX = 256 / TN;
+    constexpr uint32_t B_WIN = (uint32_t)WMAX * (uint32_t)((TN * KB * 2) >> 4);
+    const int as = ra.idx;
+    if (!wait_phase_warp(fullA + as, ra.phase, abort_v, p.status, p.timeout)) return false;
+    const uint32_t a_slot = a_lo0 + (uint32_t)as * (A_SLOT_BYTES >> 4);
+#pragma unroll
+    for (int q = 0; q < A_PPS; ++q) {
+        const int pa = SLOT * A_PPS + q;
+        if (pa < SA) {
+            const int nwin = TERMS - pa;
+#pragma unroll
+            for (int w0 = 0; w0 < nwin; w0 += WMAX) {
+                const int nw = (nwin - w0) < WMAX ? (nwin - w0) : WMAX;
+                const uint32_t id = idesc_bf16(TM, nw * TN);
+                const uint32_t d = dbase + (uint32_t)((pa + w0) * TN);
+#pragma unroll
+                for (int kk = 0; kk < KB / 16; ++kk) {
+                    const uint64_t ad = make_desc(a_slot + (uint32_t)(q * (A_PLANE_BYTES >> 4) + 2 * kk), desc_hi);
+                    const uint64_t bd = make_desc(b_lo + (uint32_t)w0 / WMAX * B_WIN + (uint32_t)(2 * kk), desc_hi);
+                    if (pa == 0 && kk == 0) umma_bf16_lane0(d, ad, bd, id, acc0);
+                    else umma_bf16_lane0_acc(d, ad, bd, id);
+                }
+            }
+        }
+    }
+    umma_commit_lane0(emptyA + as);
+    ra.next();
+    constexpr int NSLOTS = (SA + A_PPS - 1) / A_PPS;
+    if constexpr (SLOT + 1 < NSLOTS)
+        return issue_kblock<SA, TERMS, TN, SLOT + 1>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p);
+    else
+        return true;
+}
+
+// Configurations with a compile-time issue path (digit planes of A, levels, B rows per
+// level); issue_cfg is the position in this list plus one.
+struct IssueCfg { int sa, terms, tn; };
+constexpr IssueCfg kIssueCfgs[] = {{7, 7, 32}, {9, 9, 32}, {3, 3, 64}, {1, 5, 64}, {5, 5, 64}, {7, 7, 64}};
+
 template <int NCOL>
 __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, uint64_t* tfull, uint64_t* tempty,
                                               volatile int* abort_v, int quarter, int half, int lane) {
@@ -914,6 +974,18 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     break;
                 }
                 const uint32_t b_lo = b_lo0 + (uint32_t)bs * (b_stage_bytes >> 4);
+                if (p.issue_cfg > 0) {
+                    const uint32_t dbase = tmem + (uint32_t)buf * buf_cols;
+                    const uint32_t acc0 = chunk_start ? 0u : 1u;
+                    switch (p.issue_cfg) {
+                    case 1: ok = issue_kblock<7, 7, 32>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    case 2: ok = issue_kblock<9, 9, 32>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    case 3: ok = issue_kblock<3, 3, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    case 4: ok = issue_kblock<1, 5, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    case 5: ok = issue_kblock<5, 5, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    default: ok = issue_kblock<7, 7, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    }
+                } else
                 for (int pa0 = 0; pa0 < p.sa; pa0 += A_PPS) {
                     const int as = ra.idx;
                     if (!wait_phase_warp(fullA + as, ra.phase, abort_v, p.status, p.timeout)) {
@@ -1151,6 +1223,9 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     p.tn = tn;
     p.m_fast = ts.m_fast;
     p.vec2 = (g.c_cs == 1 && g.c_rs % 2 == 0 && ((uintptr_t)g.C & 15) == 0) ? 1 : 0;
+    p.issue_cfg = 0;
+    for (int i = 0; i < (int)(sizeof(kIssueCfgs) / sizeof(kIssueCfgs[0])); ++i)
+        if (kIssueCfgs[i].sa == g.a.s && kIssueCfgs[i].terms == g.terms && kIssueCfgs[i].tn == tn) p.issue_cfg = i + 1;
     p.acc_bufs = (2 * g.terms * tn <= 512) ? 2 : 1;
     p.tmem_cols = 32;
     while (p.tmem_cols < (uint32_t)(p.acc_bufs * g.terms * tn)) p.tmem_cols <<= 1;
