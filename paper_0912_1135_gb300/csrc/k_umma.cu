@@ -1165,15 +1165,31 @@ static int chunk_for(const SlicedGemm& g) {
     return kc;
 }
 
+// Split-K factor for a persistent grid of 152 CTAs: the number of rounds of work units
+// (tiles x splits) times the K blocks of one unit, plus a fixed cost per round (pipeline
+// fill and output) and per split (the partial sums written and reduced), both counted in
+// K blocks of 64; the lowest cost wins, fewer splits on ties. A split count just past a
+// multiple of 152 units would add a nearly empty round.
 static int choose_splits(int tiles, int M, int N, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
-    int splits = 1;
+    constexpr int kSMs = 152;
     const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
-    if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
-    while (splits > 1 && (size_t)splits * M * N * 16 > scratch_bytes) --splits;
-    int kps = (Kp + splits - 1) / splits;
-    kps = (kps + kchunk - 1) / kchunk * kchunk;
-    *kps_out = kps;
-    return (Kp + kps - 1) / kps;
+    const double per_split = (double)M * N * 32.0 / (7.0e12 / 1.0e6);   // partials: microseconds
+    int best = 1, best_kps = (Kp + kchunk - 1) / kchunk * kchunk;
+    double best_cost = 1e300;
+    for (int sp = 1; sp <= std::min(max_splits, 64); ++sp) {
+        if (sp > 1 && (size_t)sp * M * N * 16 > scratch_bytes) break;
+        int kps = (Kp + sp - 1) / sp;
+        kps = (kps + kchunk - 1) / kchunk * kchunk;
+        const int eff = (Kp + kps - 1) / kps;
+        if (eff != sp) continue;
+        const long long units = (long long)tiles * eff;
+        const long long rounds = (units + kSMs - 1) / kSMs;
+        // one K block of 64 is about one microsecond on one SM for these products
+        const double cost = (double)rounds * ((double)kps / KB + 3.0) + (sp > 1 ? per_split * sp : 0.0);
+        if (cost < best_cost - 1e-9) { best_cost = cost; best = eff; best_kps = kps; }
+    }
+    *kps_out = best_kps;
+    return best;
 }
 
 cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
