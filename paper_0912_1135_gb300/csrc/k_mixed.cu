@@ -39,7 +39,7 @@ int s_all(const rtproj_opts& o) {
 }
 
 struct MixedLayout {
-    size_t A, eA, AT, eAT, G, eG, Mp, Ms, eM, W, eW, B, eB, H, eH, S, eS, scratch, total;
+    size_t A, eA, AT, eAT, G, eG, Mp, Ms, eM, W, eW, B, eB, H, eH, S, eS, T, eT, Tt, eTt, scratch, total;
 };
 
 MixedLayout mixed_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts& o) {
@@ -66,6 +66,10 @@ MixedLayout mixed_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, con
     L.eH = take((size_t)k_max * 4);
     L.S = take((size_t)o.resid_slices * k_max * ldn * 2);
     L.eS = take((size_t)k_max * 4);
+    L.T = take((size_t)o.apply_slices * m * ldm * 2);
+    L.eT = take((size_t)m * 4);
+    L.Tt = take((size_t)o.apply_slices * m * ldm * 2);
+    L.eTt = take((size_t)m * 4);
     L.scratch = take(kScratch);
     L.total = off;
     return L;
@@ -104,6 +108,15 @@ __global__ void mprime_kernel(const double* RinvT, const int32_t* perm, const in
     const int i = (int)(idx / m), t = (int)(idx % m);
     const int k = perm[t];
     Mp[(int64_t)i * m + k] = ldexp(RinvT[idx], eA[k]);
+}
+
+// D[i][perm[t]] = T[i][t] (m x m): T Pi^* with Pi the pivot permutation, so that
+// (T Pi x) = D x for x in the original order.
+__global__ void permute_columns_kernel(const double* T, const int32_t* perm, int m, double* D) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    const int i = (int)(idx / m), t = (int)(idx % m);
+    D[(int64_t)i * m + perm[t]] = T[idx];
 }
 
 __global__ void axpy_kernel(double* y, const double* x, int64_t n) {
@@ -163,6 +176,8 @@ rtproj_status mixed_bind(rtproj_ctx* h, char* base, size_t bytes) {
     h->Bs = stack(base, L.B, L.eB, (int)h->k_max, n, o.apply_slices, ldn);
     h->Hs = stack(base, L.H, L.eH, (int)h->k_max, m, std::max(o.apply_slices, o.resid_slices), ldm);
     h->Ss = stack(base, L.S, L.eS, (int)h->k_max, n, o.resid_slices, ldn);
+    h->Ts = stack(base, L.T, L.eT, m, m, o.apply_slices, ldm);
+    h->Tts = stack(base, L.Tt, L.eTt, m, m, o.apply_slices, ldm);
     h->sg_scratch = base + L.scratch;
     h->sg_scratch_bytes = kScratch;
     return RTPROJ_OK;
@@ -201,6 +216,40 @@ rtproj_status mixed_gram(rtproj_ctx* h) {
     return gemm(h, h->Ws, h->Ws, h->opts.gram2_slices, h->Lc, m, 1, 1.0, 0.0, nullptr, 0, 0, true);
 }
 
+// Steps 2-6 of the apply (Section 4) fold into h = Pi^* T1^* T1 Pi c with T1 = L^{-1} R^{-*}
+// (L L^* = X). With D = T1 Pi (columns permuted to the original order) this is D^* (D c):
+// two products of m x m digit stacks, sliced here once per preconditioner, against the
+// k right-hand sides. Every digit product is exact, so each product is accurate to
+// 2^{-8 apply_slices} relative to |D||c| -- tighter than float64 rounding of the same
+// products, and the refinement pass corrects what remains.
+rtproj_status mixed_prepare_middle(rtproj_ctx* h) {
+    const int m = (int)h->m;
+    const int64_t total = (int64_t)m * m;
+    phase_begin(h, RTPROJ_PHASE_SLICE);
+    permute_columns_kernel<<<(unsigned)((total + 255) / 256), 256, 0, h->stream>>>(h->T1, h->perm, m, h->Mprime);
+    note_launch();
+    MX_CHECK(cudaGetLastError());
+    MX_CHECK(slice_rows(h->Mprime, m, 1, nullptr, nullptr, h->Ts, h->status, h->stream));
+    MX_CHECK(slice_rows(h->Mprime, 1, m, nullptr, nullptr, h->Tts, h->status, h->stream));
+    phase_end(h, RTPROJ_PHASE_SLICE);
+    return RTPROJ_OK;
+}
+
+namespace {
+
+// out = D^* (D c) for the m x k block c (row-major, leading dimension k).
+rtproj_status middle_mixed(rtproj_ctx* h, const double* c, double* out, int k) {
+    const int ap = h->opts.apply_slices;
+    const SliceStack Hk = rows_of(h->Hs, k, ap);
+    MX_CHECK(slice_rows(c, 1, k, nullptr, nullptr, Hk, h->status, h->stream));             // c^*: k x m
+    rtproj_status st = gemm(h, h->Ts, Hk, ap, h->ebuf, k, 1);                              // u = D c
+    if (st != RTPROJ_OK) return st;
+    MX_CHECK(slice_rows(h->ebuf, 1, k, nullptr, nullptr, Hk, h->status, h->stream));        // u^*: k x m
+    return gemm(h, h->Tts, Hk, ap, out, k, 1);                                             // D^* u
+}
+
+}  // namespace
+
 rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, double* Z, int64_t ldz, double* ROW,
                             int64_t ldr, double* X, int64_t ldx) {
     const rtproj_opts& o = h->opts;
@@ -218,7 +267,7 @@ rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, 
     phase_end(h, RTPROJ_PHASE_APPLY_A);
     // h0 = Pi^* T1^* T1 Pi c
     phase_begin(h, RTPROJ_PHASE_APPLY_M);
-    st = middle_fp64(h, h->cbuf, h->hbuf, k);
+    st = middle_mixed(h, h->cbuf, h->hbuf, k);
     if (st != RTPROJ_OK) return st;
     phase_end(h, RTPROJ_PHASE_APPLY_M);
     // s = b - A^* h0
@@ -244,7 +293,7 @@ rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, 
         phase_end(h, RTPROJ_PHASE_APPLY_A);
         // dh, h += dh
         phase_begin(h, RTPROJ_PHASE_APPLY_M);
-        st = middle_fp64(h, h->cbuf, h->dhbuf, k);
+        st = middle_mixed(h, h->cbuf, h->dhbuf, k);
         if (st != RTPROJ_OK) return st;
         const int64_t mk = (int64_t)m * k;
         axpy_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(h->hbuf, h->dhbuf, mk);

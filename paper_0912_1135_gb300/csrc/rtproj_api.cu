@@ -222,6 +222,7 @@ rtproj_status mixed_bind(rtproj_ctx* h, char* base, size_t bytes);
 rtproj_status mixed_prepare_a(rtproj_ctx* h);
 rtproj_status mixed_sketch(rtproj_ctx* h, uint64_t seed, int64_t l, double* S, int64_t lds);
 rtproj_status mixed_gram(rtproj_ctx* h);
+rtproj_status mixed_prepare_middle(rtproj_ctx* h);
 rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, double* Z, int64_t ldz,
                             double* ROW, int64_t ldr, double* X, int64_t ldx);
 }  // namespace rtp
@@ -374,6 +375,10 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     RT_CHECK(cudaMemcpyAsync(h->T1, h->RinvT, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
     RT_CHECK(trsm(h->Lc, m, 1, true, m, h->T1, m, m, h->dinv, h->status, s, true));     // R^{-*} is lower
     phase_end(h, RTPROJ_PHASE_FACTOR);
+    if (h->opts.mode == RTPROJ_MIXED_REFINED) {
+        st = mixed_prepare_middle(h);
+        if (st != RTPROJ_OK) return st;
+    }
     RT_CHECK(cudaEventRecord(h->ev1, s));
     RT_CHECK(cudaStreamSynchronize(s));
     int dev_status = 0;

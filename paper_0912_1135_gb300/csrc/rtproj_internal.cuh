@@ -202,6 +202,8 @@ struct rtproj_ctx {
     rtp::SliceStack Bs;          // right-hand sides: k x n
     rtp::SliceStack Hs;          // h or dh with rows scaled by 2^{e_A}, transposed: k x m
     rtp::SliceStack Ss;          // refinement residual s: k x n
+    rtp::SliceStack Ts;          // T1 Pi (columns permuted): m x m, reduction over m
+    rtp::SliceStack Tts;         // (T1 Pi)^*: m x m, reduction over m
     double* Mprime = nullptr;    // m x m
     void* sg_scratch = nullptr;  // int64 split-K partials
     size_t sg_scratch_bytes = 0;
