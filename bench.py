@@ -416,36 +416,55 @@ def fp64_form(torch, rt, A, B, At, Bt, w, args, rank):
 
 
 def e2e(torch, rt, A, B, w, args, dev):
-    """Same metric through the public API from pinned host buffers: per step the H2D copy of
-    A and B, create + precondition + null_project, and the D2H copy of Z."""
+    """Same metric through the public API from pinned host buffers. Every step copies its A
+    and B host-to-device, creates a Projector (A is sliced at create), preconditions,
+    projects and copies Z device-to-host, all inside the timed region. As a serving loop
+    would, the next step's host-to-device copies run on a second stream while the current
+    step computes (two device buffers for A and B)."""
     Ah = torch.from_numpy(A).pin_memory()
     Bh = torch.from_numpy(B).pin_memory()
-    Zh = torch.empty(B.shape, dtype=torch.float64).pin_memory()
+    Zh = [torch.empty(B.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
     steps = max(1, min(args.steps, 5))
-    stream = torch.cuda.current_stream(dev)
+    comp = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(dev)
+    Ad = [torch.empty(A.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    Bd = [torch.empty(B.shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+    for ev in freed:
+        ev.record(comp)
 
-    def one(i):
-        Ad = Ah.to(dev, non_blocking=True)
-        Bd = Bh.to(dev, non_blocking=True)
-        with rt.Projector(Ad, l_max=w.l, k_max=w.k, mode=args.mode) as P:
+    def issue_copy(i):
+        s = i % 2
+        with torch.cuda.stream(copy):
+            copy.wait_event(freed[s])          # the buffers' previous step is done with them
+            Ad[s].copy_(Ah, non_blocking=True)
+            Bd[s].copy_(Bh, non_blocking=True)
+            copied[s].record(copy)
+
+    def run(i):
+        s = i % 2
+        comp.wait_event(copied[s])
+        with rt.Projector(Ad[s], l_max=w.l, k_max=w.k, mode=args.mode, stream=comp) as P:
             P.precondition(w.seed_omega + i, w.l)
-            Z = P.null_project(Bd)
-            Zh.copy_(Z, non_blocking=True)
-            stream.synchronize()
+            Z = P.null_project(Bd[s])
+            Zh[s].copy_(Z, non_blocking=True)
+        freed[s].record(comp)
 
-    one(0)
+    issue_copy(0)
+    run(0)
     torch.cuda.synchronize()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
     t0 = time.perf_counter()
-    for i in range(steps):
-        one(i + 1)
-    ev1.record(stream)
+    issue_copy(1)
+    for i in range(1, steps + 1):
+        if i + 1 <= steps:
+            issue_copy(i + 1)
+        run(i)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     return {"value": w.k * steps / wall, "unit": "projections/s", "h2d_bytes_per_step": int(A.nbytes + B.nbytes),
-            "d2h_bytes_per_step": int(B.nbytes), "steps": steps}
+            "d2h_bytes_per_step": int(B.nbytes), "steps": steps,
+            "pipelining": "the next step's H2D copies overlap the current step's compute (second stream)"}
 
 
 def main():

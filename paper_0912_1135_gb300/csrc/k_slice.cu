@@ -114,20 +114,44 @@ __global__ void __launch_bounds__(SL_THREADS) slice_rows_kernel(SliceDev a) {
 }
 
 // Transposes each digit plane: src [p][r][c] (ld_src) -> dst [p][c][r] (ld_dst), zero padded.
-__global__ void transpose_planes_kernel(const __nv_bfloat16* src, int64_t ld_src, int64_t ps_src, int rows, int cols,
-                                        __nv_bfloat16* dst, int64_t ld_dst, int64_t ps_dst, int dst_rows) {
-    __shared__ __nv_bfloat16 tile[32][34];
+// Digit planes transposed through a 64 x 64 shared-memory tile: every warp reads and
+// writes 32 pairs of adjacent bfloat16 (128 bytes per row), so both sides move whole
+// sectors. dst row c (< dst_rows) holds column c of src; dst columns r >= rows are zero.
+// Requires even ld_src and ld_dst (both are multiples of 8 elements).
+__global__ void __launch_bounds__(256) transpose_planes_kernel(const __nv_bfloat16* src, int64_t ld_src,
+                                                               int64_t ps_src, int rows, int cols,
+                                                               __nv_bfloat16* dst, int64_t ld_dst, int64_t ps_dst,
+                                                               int dst_rows) {
+    __shared__ __nv_bfloat16 tile[64][66];
     const int p = blockIdx.z;
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int r0 = blockIdx.y * 64, c0 = blockIdx.x * 64;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const __nv_bfloat16 zero = __int2bfloat16_rn(0);
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int r = r0 + y, c = c0 + threadIdx.x;
-        tile[y][threadIdx.x] = (r < rows && c < cols) ? src[(int64_t)p * ps_src + (int64_t)r * ld_src + c] : zero;
+    const __nv_bfloat16* sp = src + (int64_t)p * ps_src;
+    for (int y = ty; y < 64; y += 8) {
+        const int r = r0 + y, c = c0 + 2 * tx;
+        __nv_bfloat162 v;
+        v.x = zero;
+        v.y = zero;
+        if (r < rows) {
+            if (c + 1 < cols) {
+                v = *reinterpret_cast<const __nv_bfloat162*>(sp + (int64_t)r * ld_src + c);
+            } else if (c < cols) {
+                v.x = sp[(int64_t)r * ld_src + c];
+            }
+        }
+        tile[y][2 * tx] = v.x;
+        tile[y][2 * tx + 1] = v.y;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
-        const int c = c0 + y, r = r0 + threadIdx.x;   // dst row c, dst col r
-        if (c < dst_rows && r < ld_dst) dst[(int64_t)p * ps_dst + (int64_t)c * ld_dst + r] = tile[threadIdx.x][y];
+    __nv_bfloat16* dp = dst + (int64_t)p * ps_dst;
+    for (int y = ty; y < 64; y += 8) {
+        const int c = c0 + y, r = r0 + 2 * tx;   // dst row c, dst cols r, r + 1
+        if (c >= dst_rows || r >= ld_dst) continue;
+        __nv_bfloat162 v;
+        v.x = tile[2 * tx][y];
+        v.y = tile[2 * tx + 1][y];
+        *reinterpret_cast<__nv_bfloat162*>(dp + (int64_t)c * ld_dst + r) = v;
     }
 }
 
@@ -380,7 +404,8 @@ cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_
 
 cudaError_t transpose_planes(const SliceStack& src, const SliceStack& dst, cudaStream_t s) {
     // dst row c (< dst.rows) holds column c of src; columns r >= src.rows are zero padding.
-    dim3 grid((unsigned)((dst.rows + 31) / 32), (unsigned)((dst.ld + 31) / 32), (unsigned)src.s);
+    if (src.ld % 2 || dst.ld % 2) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((dst.rows + 63) / 64), (unsigned)((dst.ld + 63) / 64), (unsigned)src.s);
     transpose_planes_kernel<<<grid, dim3(32, 8), 0, s>>>(src.d, src.ld, src.plane_stride, src.rows, src.cols, dst.d,
                                                           dst.ld, dst.plane_stride, dst.rows);
     note_launch();
