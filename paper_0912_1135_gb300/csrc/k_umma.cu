@@ -226,6 +226,16 @@ __device__ __forceinline__ double epilogue_value(double v, int amode, double alp
     else if (bmode == 2) out = fma(beta, *cin, out);
     return out;
 }
+// The same with the Cin entry already loaded.
+__device__ __forceinline__ double epilogue_value_v(double v, int amode, double alpha, int bmode, double beta,
+                                                   double cin) {
+    double out = amode == 0 ? v
+               : amode == 1 ? __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull)
+                            : alpha * v;
+    if (bmode == 1) out += cin;
+    else if (bmode == 2) out = fma(beta, cin, out);
+    return out;
+}
 __host__ inline int alpha_mode(double a) { return a == 1.0 ? 0 : (a == -1.0 ? 1 : 2); }
 __host__ inline int beta_mode(double b) { return b == 0.0 ? 0 : (b == 1.0 ? 1 : 2); }
 
@@ -832,33 +842,79 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
             const int64_t row = p.crow && valid ? (int64_t)p.crow[i] : (int64_t)i;
             double* crow_p = p.C + row * p.c_rs;
             const double* cin_p = p.Cin + (int64_t)i * p.cin_rs;
-            if (p.vec2) {
-                // row-contiguous output: pairs of columns as one 16-byte store
+            if (p.bmode == 0) {
+                // no Cin: the stores follow the conversions directly
+                if (p.vec2) {
+                    // row-contiguous output: pairs of columns as one 16-byte store
 #pragma unroll
-                for (int j = 0; j < NCOL; j += 2) {
-                    const int gj = jb + j;
-                    const int e0 = __shfl_sync(0xffffffffu, ebl, j), e1 = __shfl_sync(0xffffffffu, ebl, j + 1);
-                    if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
-                    const double v0 = epilogue_value(words_to_double((long long)hi[j], (long long)lo[j], ea + e0),
-                                                     p.amode, p.alpha, p.bmode, p.beta, cin_p + (int64_t)gj * p.cin_cs);
-                    if (gj + 1 < p.N && !(p.lower_only && gj + 1 > i)) {
-                        const double v1 = epilogue_value(
-                            words_to_double((long long)hi[j + 1], (long long)lo[j + 1], ea + e1), p.amode, p.alpha,
-                            p.bmode, p.beta, cin_p + (int64_t)(gj + 1) * p.cin_cs);
-                        *reinterpret_cast<double2*>(crow_p + gj) = make_double2(v0, v1);
-                    } else {
-                        crow_p[gj] = v0;
+                    for (int j = 0; j < NCOL; j += 2) {
+                        const int gj = jb + j;
+                        const int e0 = __shfl_sync(0xffffffffu, ebl, j), e1 = __shfl_sync(0xffffffffu, ebl, j + 1);
+                        if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
+                        const double v0 = epilogue_value_v(words_to_double((long long)hi[j], (long long)lo[j], ea + e0),
+                                                           p.amode, p.alpha, 0, 0.0, 0.0);
+                        if (gj + 1 < p.N && !(p.lower_only && gj + 1 > i)) {
+                            const double v1 = epilogue_value_v(
+                                words_to_double((long long)hi[j + 1], (long long)lo[j + 1], ea + e1), p.amode,
+                                p.alpha, 0, 0.0, 0.0);
+                            *reinterpret_cast<double2*>(crow_p + gj) = make_double2(v0, v1);
+                        } else {
+                            crow_p[gj] = v0;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < NCOL; ++j) {
+                        const int gj = jb + j;
+                        const int ej = __shfl_sync(0xffffffffu, ebl, j);
+                        if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
+                        crow_p[(int64_t)gj * p.c_cs] = epilogue_value_v(
+                            words_to_double((long long)hi[j], (long long)lo[j], ea + ej), p.amode, p.alpha, 0, 0.0, 0.0);
                     }
                 }
             } else {
+                // Cin is read eight entries ahead of the stores, in groups: C may alias Cin (an
+                // update in place), so a load placed after a store would wait for the previous
+                // element's whole round trip
+                constexpr int CG = 8;
 #pragma unroll
-                for (int j = 0; j < NCOL; ++j) {
-                    const int gj = jb + j;
-                    const int ej = __shfl_sync(0xffffffffu, ebl, j);
-                    if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
-                    crow_p[(int64_t)gj * p.c_cs] =
-                        epilogue_value(words_to_double((long long)hi[j], (long long)lo[j], ea + ej), p.amode, p.alpha,
-                                       p.bmode, p.beta, cin_p + (int64_t)gj * p.cin_cs);
+                for (int g0 = 0; g0 < NCOL; g0 += CG) {
+                    double cv[CG];
+#pragma unroll
+                    for (int q = 0; q < CG; ++q) {
+                        const int gj = jb + g0 + q;
+                        cv[q] = (p.bmode != 0 && valid && gj < p.N && !(p.lower_only && gj > i))
+                                    ? __ldcg(cin_p + (int64_t)gj * p.cin_cs) : 0.0;
+                    }
+                    if (p.vec2) {
+                        // row-contiguous output: pairs of columns as one 16-byte store
+#pragma unroll
+                        for (int q = 0; q < CG; q += 2) {
+                            const int j = g0 + q, gj = jb + j;
+                            const int e0 = __shfl_sync(0xffffffffu, ebl, j), e1 = __shfl_sync(0xffffffffu, ebl, j + 1);
+                            if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
+                            const double v0 = epilogue_value_v(words_to_double((long long)hi[j], (long long)lo[j], ea + e0),
+                                                               p.amode, p.alpha, p.bmode, p.beta, cv[q]);
+                            if (gj + 1 < p.N && !(p.lower_only && gj + 1 > i)) {
+                                const double v1 = epilogue_value_v(
+                                    words_to_double((long long)hi[j + 1], (long long)lo[j + 1], ea + e1), p.amode,
+                                    p.alpha, p.bmode, p.beta, cv[q + 1]);
+                                *reinterpret_cast<double2*>(crow_p + gj) = make_double2(v0, v1);
+                            } else {
+                                crow_p[gj] = v0;
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < CG; ++q) {
+                            const int j = g0 + q, gj = jb + j;
+                            const int ej = __shfl_sync(0xffffffffu, ebl, j);
+                            if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
+                            crow_p[(int64_t)gj * p.c_cs] =
+                                epilogue_value_v(words_to_double((long long)hi[j], (long long)lo[j], ea + ej), p.amode,
+                                                 p.alpha, p.bmode, p.beta, cv[q]);
+                        }
+                    }
                 }
             }
         }
