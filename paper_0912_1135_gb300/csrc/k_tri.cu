@@ -3,7 +3,8 @@
 // Section 4 forms Y = X^{-1} explicitly (Eq. 16). This library factors X = L L^*
 // instead (X is symmetric positive definite with kappa(X) = kappa(P^{-1}A)^2, small)
 // and folds R and L into T1 = L^{-1} R^{-*}, so that steps 3-5 of the apply become
-// two dense triangular products: P^{-*} Y P^{-1} c = Pi^* T1^* T1 Pi c.
+// two dense products with T1: P^{-*} Y P^{-1} c = Pi^* T1^* T1 Pi c (triangular float64
+// products in the float64 form, digit-sliced tensor-core products in the mixed form).
 #include "rtproj_internal.cuh"
 
 #include <algorithm>
