@@ -12,148 +12,172 @@
 namespace rtp {
 namespace {
 
-constexpr int TRSM_NB = 2;        // right-hand-side columns per column block (two blocks per CTA)
-constexpr int TRSM_THREADS = 256;
+constexpr int TRSM_THREADS = 512;
 constexpr int TRSM_BS = 32;       // rows per diagonal block
+constexpr int TRSM_DPARTS = 4;    // partial sums per entry of the diagonal-block product (4 warps)
 
-// Inverse of each 32 x 32 diagonal block of T (lower or upper), one warp per block:
-// lane j forms column j by substitution, right-looking: once entry i of the column is
-// known, it is removed from the partial sums of the rows still to come, so every float64
-// instruction is an independent update (the pipe takes 64 cycles per warp instruction;
-// a predicated 32 x 32 loop or a dependent chain would cost more). The reciprocals of
-// the diagonal entries are formed once, independently of each other. Dinv[b] is
-// row-major 32 x 32.
+// Inverse of each 32 x 32 diagonal block of T (lower or upper), one CTA of four warps per
+// block, in two levels: with the block written lower triangular as D = [A 0; B C] (the
+// transpose of an upper block), D^{-1} = [A^{-1} 0; -C^{-1} B A^{-1}  C^{-1}]. One warp
+// inverts A (lanes 0-15) and C (lanes 16-31) at once, lane j forming column j of its
+// 16 x 16 block by right-looking substitution (once entry i is known it is removed from
+// the rows below, so each float64 instruction is an independent update); then all four
+// warps form F = B A^{-1} and -C^{-1} F as small products. The GB300 float64 pipe takes
+// 64 cycles per warp instruction, so the 16-step chains and the products spread over four
+// sub-partitions cost far less than one warp's 32 x 32 substitution. A block past the
+// end of T (bs < 32) is padded with the identity. Dinv[b] is row-major 32 x 32, zero
+// outside the block's triangle and outside bs x bs.
+constexpr int TDI_THREADS = 128;
 template <bool lower>
-__global__ void tri_diag_inv_kernel(const double* T, int64_t t_rs, int64_t t_cs, int m, double* Dinv, int* status) {
-    const int b = blockIdx.x, j = threadIdx.x;
+__global__ void __launch_bounds__(TDI_THREADS) tri_diag_inv_kernel(const double* T, int64_t t_rs, int64_t t_cs,
+                                                                   int m, double* Dinv, int* status) {
+    constexpr int H = TRSM_BS / 2;
+    __shared__ double a[TRSM_BS][TRSM_BS + 1];     // the block, lower triangular
+    __shared__ double inv[TRSM_BS][TRSM_BS + 1];   // its inverse (lower triangle)
+    __shared__ double f[H][H + 1];
+    __shared__ double rd[TRSM_BS];
+    const int b = blockIdx.x, t = threadIdx.x;
     const int r0 = b * TRSM_BS;
     const int bs = min(TRSM_BS, m - r0);
+    for (int e = t; e < TRSM_BS * TRSM_BS; e += TDI_THREADS) {
+        const int i = e / TRSM_BS, k = e % TRSM_BS;
+        double v = i == k ? 1.0 : 0.0;
+        if (i < bs && k <= i) {
+            const int64_t ti = r0 + (lower ? i : k), tk = r0 + (lower ? k : i);
+            v = T[ti * t_rs + tk * t_cs];
+        }
+        a[i][k] = v;
+    }
+    __syncthreads();
+    if (t < TRSM_BS) {
+        double d = a[t][t];
+        if (!(d != 0.0) || !isfinite(d)) {
+            set_status(status, RTPROJ_ENONFINITE);
+            d = 1.0;
+        }
+        rd[t] = 1.0 / d;
+    }
+    __syncthreads();
+    if (t < TRSM_BS) {   // A^{-1} on lanes 0-15, C^{-1} on lanes 16-31
+        const int off = (t / H) * H, jj = t % H;
+        double col[H];   // partial sums, then column jj
+#pragma unroll
+        for (int i = 0; i < H; ++i) col[i] = i == jj ? 1.0 : 0.0;
+#pragma unroll
+        for (int i = 0; i < H; ++i) {
+            col[i] = i >= jj ? col[i] * rd[off + i] : 0.0;
+#pragma unroll
+            for (int r = i + 1; r < H; ++r) col[r] = fma(-a[off + r][off + i], col[i], col[r]);
+        }
+#pragma unroll
+        for (int i = 0; i < H; ++i) inv[off + i][off + jj] = col[i];
+    }
+    __syncthreads();
+    for (int e = t; e < H * H; e += TDI_THREADS) {   // F = B A^{-1} (A^{-1} is zero above its diagonal)
+        const int i = e / H, j = e % H;
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < H; k += 2) {
+            s0 = fma(a[H + i][k], inv[k][j], s0);
+            s1 = fma(a[H + i][k + 1], inv[k + 1][j], s1);
+        }
+        f[i][j] = s0 + s1;
+    }
+    __syncthreads();
+    for (int e = t; e < H * H; e += TDI_THREADS) {   // lower-left block -C^{-1} F
+        const int i = e / H, j = e % H;
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < H; k += 2) {
+            s0 = fma(inv[H + i][H + k], f[k][j], s0);
+            s1 = fma(inv[H + i][H + k + 1], f[k + 1][j], s1);
+        }
+        inv[H + i][j] = -(s0 + s1);
+    }
+    __syncthreads();
     double* out = Dinv + (size_t)b * TRSM_BS * TRSM_BS;
-    auto D = [&](int i, int k) { return T[(int64_t)(r0 + i) * t_rs + (int64_t)(r0 + k) * t_cs]; };
-    // lane i holds 1 / D(i, i) (1 for rows past the block, which stay zero)
-    double rd = 1.0;
-    if (j < bs) {
-        double d = D(j, j);
-        if (!(d != 0.0) || !isfinite(d)) { set_status(status, RTPROJ_ENONFINITE); d = 1.0; }
-        rd = 1.0 / d;
+    for (int e = t; e < TRSM_BS * TRSM_BS; e += TDI_THREADS) {
+        const int i = e / TRSM_BS, j = e % TRSM_BS;
+        const int li = lower ? i : j, lj = lower ? j : i;
+        out[e] = (i < bs && j < bs && lj <= li) ? inv[li][lj] : 0.0;
     }
-    double col[TRSM_BS];                   // partial sums, then the column
-#pragma unroll
-    for (int i = 0; i < TRSM_BS; ++i) col[i] = (i == j) ? 1.0 : 0.0;
-    if (lower) {
-#pragma unroll
-        for (int i = 0; i < TRSM_BS; ++i) {
-            const double ri = __shfl_sync(0xffffffffu, rd, i);
-            col[i] = (i < bs && i >= j) ? col[i] * ri : 0.0;
-#pragma unroll
-            for (int r = i + 1; r < TRSM_BS; ++r)
-                if (r < bs) col[r] = fma(-D(r, i), col[i], col[r]);
-        }
-    } else {
-#pragma unroll
-        for (int i = TRSM_BS - 1; i >= 0; --i) {
-            const double ri = __shfl_sync(0xffffffffu, rd, i);
-            col[i] = (i < bs && i <= j) ? col[i] * ri : 0.0;
-#pragma unroll
-            for (int r = 0; r < i; ++r) col[r] = fma(-D(r, i), col[i], col[r]);
-        }
-    }
-    if (j >= bs) {
-#pragma unroll
-        for (int i = 0; i < TRSM_BS; ++i) col[i] = 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < TRSM_BS; ++i) out[i * TRSM_BS + j] = col[i];
 }
 
-// Solves op(T) X = B for TRSM_NB columns of B per CTA, block by block: the 32 rows of a
-// diagonal block are obtained at once from the precomputed block inverse (a small
-// matrix product, no sequential chain), then all threads subtract that block's
-// contribution from the rows still to be solved. Three barriers per block.
+// Solves op(T) x = b for one column of B at a time. The CTAs (one per SM) take columns
+// from a shared counter in increasing order: with a lower-triangular right-hand side the
+// first columns carry the most rows, so the longest solves start first and the short ones
+// fill in behind them. Per diagonal block: the block's rows are obtained at once from the
+// precomputed block inverse (four partial sums per entry on four warps, so the float64
+// pipes of all four sub-partitions share the product), then every thread subtracts that
+// block's contribution from one row still to be solved, with the 32 entries of its row of
+// T loaded before the products. Two barriers per block.
 template <bool lower>
-__global__ void __launch_bounds__(TRSM_THREADS) trsm_kernel(const double* T, int64_t t_rs, int64_t t_cs, int m,
-                                                            double* B, int64_t b_rs, int ncols, const double* Dinv,
-                                                            int rhs_lower) {
-    extern __shared__ double x[];   // m * TRSM_NB
-    // Column blocks in pairs (b, last - b): with a lower right-hand side the first blocks
-    // carry the most rows, so pairing evens out the work per CTA.
-    const int ncb = (ncols + TRSM_NB - 1) / TRSM_NB;
-    for (int pass = 0; pass < 2; ++pass) {
-        const int cbk = pass == 0 ? (int)blockIdx.x : ncb - 1 - (int)blockIdx.x;
-        if (pass == 1 && cbk <= (int)blockIdx.x) break;
-        const int j0 = cbk * TRSM_NB;
-        const int nc = min(TRSM_NB, ncols - j0);
-        const int t = threadIdx.x;
-        for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
-            const int i = e / TRSM_NB, jj = e % TRSM_NB;
-            x[e] = jj < nc ? B[(int64_t)i * b_rs + j0 + jj] : 0.0;
-        }
+__global__ void __launch_bounds__(TRSM_THREADS, 1) trsm_kernel(const double* __restrict__ T, int64_t t_rs, int64_t t_cs,
+                                                            int m, double* B, int64_t b_rs, int ncols,
+                                                            const double* __restrict__ Dinv, int rhs_lower,
+                                                            unsigned int* next_col) {
+    extern __shared__ double x[];   // m: the column being solved
+    __shared__ int col_s;
+    const int t = threadIdx.x;
+    const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
+    for (;;) {
+        if (t == 0) col_s = (int)atomicAdd(next_col, 1u);
         __syncthreads();
-        const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
+        const int j = col_s;
+        if (j >= ncols) break;
         // A lower-triangular right-hand side (zero above its diagonal) gives a lower-triangular
-        // solution of a lower system: rows above this CTA's first column stay zero.
-        const int bi0 = (lower && rhs_lower) ? min(j0, m) / TRSM_BS : 0;
+        // solution of a lower system: the rows above column j's diagonal block stay zero.
+        const int bi0 = (lower && rhs_lower) ? min(j, m) / TRSM_BS : 0;
+        const int row0 = bi0 * TRSM_BS;
+        for (int i = row0 + t; i < m; i += TRSM_THREADS) x[i] = B[(int64_t)i * b_rs + j];
+        __syncthreads();
         for (int bi = bi0; bi < nblk; ++bi) {
             const int blk = lower ? bi : nblk - 1 - bi;
             const int r0 = blk * TRSM_BS;
             const int bs = min(TRSM_BS, m - r0);
-            // x_blk = Dinv_blk x_blk
+            // x_blk = Dinv_blk x_blk: entry i on lanes 4i .. 4i+3 (k = part, part + 4, ...)
+            const int di = t / TRSM_DPARTS, part = t % TRSM_DPARTS;
             double y = 0.0;
-            const int i = t / TRSM_NB, jj = t % TRSM_NB;
-            const bool act = t < TRSM_BS * TRSM_NB && i < bs;
-            if (act) {
-                // four independent partial sums (Dinv is zero outside the block)
-                const double* drow = Dinv + (size_t)blk * TRSM_BS * TRSM_BS + (size_t)i * TRSM_BS;
-                double y1 = 0.0, y2 = 0.0, y3 = 0.0;
-    #pragma unroll
-                for (int k = 0; k < TRSM_BS; k += 4) {
-                    if (k < bs) y = fma(drow[k], x[(r0 + k) * TRSM_NB + jj], y);
-                    if (k + 1 < bs) y1 = fma(drow[k + 1], x[(r0 + k + 1) * TRSM_NB + jj], y1);
-                    if (k + 2 < bs) y2 = fma(drow[k + 2], x[(r0 + k + 2) * TRSM_NB + jj], y2);
-                    if (k + 3 < bs) y3 = fma(drow[k + 3], x[(r0 + k + 3) * TRSM_NB + jj], y3);
+            if (t < TRSM_BS * TRSM_DPARTS) {
+                const double* drow = Dinv + ((size_t)blk * TRSM_BS + di) * TRSM_BS;
+                double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+                for (int k0 = 0; k0 < TRSM_BS; k0 += 2 * TRSM_DPARTS) {
+                    const int k = k0 + part;
+                    if (k < bs) y0 = fma(drow[k], x[r0 + k], y0);
+                    if (k + TRSM_DPARTS < bs) y1 = fma(drow[k + TRSM_DPARTS], x[r0 + k + TRSM_DPARTS], y1);
                 }
-                y = (y + y1) + (y2 + y3);
+                y = y0 + y1;
+                y += __shfl_xor_sync(0xffffffffu, y, 1);
+                y += __shfl_xor_sync(0xffffffffu, y, 2);
             }
             __syncthreads();
-            if (act) x[(r0 + i) * TRSM_NB + jj] = y;
+            if (t < TRSM_BS * TRSM_DPARTS && part == 0 && di < bs) x[r0 + di] = y;
             __syncthreads();
             // rows not yet solved: below the block (lower) or above it (upper)
             const int rbeg = lower ? r0 + bs : 0;
             const int rend = lower ? m : r0;
             for (int r = rbeg + t; r < rend; r += TRSM_THREADS) {
-                double acc[TRSM_NB];
-    #pragma unroll
-                for (int q = 0; q < TRSM_NB; ++q) acc[q] = x[r * TRSM_NB + q];
                 const double* trow = T + (int64_t)r * t_rs + (int64_t)r0 * t_cs;
+                double a0 = x[r], a1 = 0.0;
                 if (bs == TRSM_BS) {
-    #pragma unroll
-                    for (int k0 = 0; k0 < TRSM_BS; k0 += 8) {
-                        double tv[8];
-    #pragma unroll
-                        for (int q = 0; q < 8; ++q) tv[q] = trow[(int64_t)(k0 + q) * t_cs];
-    #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-    #pragma unroll
-                            for (int c = 0; c < TRSM_NB; ++c)
-                                acc[c] = fma(-tv[q], x[(r0 + k0 + q) * TRSM_NB + c], acc[c]);
+                    double tv[TRSM_BS];
+#pragma unroll
+                    for (int k = 0; k < TRSM_BS; ++k) tv[k] = trow[(int64_t)k * t_cs];
+#pragma unroll
+                    for (int k = 0; k < TRSM_BS; k += 2) {
+                        a0 = fma(-tv[k], x[r0 + k], a0);
+                        a1 = fma(-tv[k + 1], x[r0 + k + 1], a1);
                     }
                 } else {
-                    for (int k = 0; k < bs; ++k) {
-                        const double tv = trow[(int64_t)k * t_cs];
-    #pragma unroll
-                        for (int c = 0; c < TRSM_NB; ++c) acc[c] = fma(-tv, x[(r0 + k) * TRSM_NB + c], acc[c]);
-                    }
+                    for (int k = 0; k < bs; ++k) a0 = fma(-trow[(int64_t)k * t_cs], x[r0 + k], a0);
                 }
-    #pragma unroll
-                for (int c = 0; c < TRSM_NB; ++c) x[r * TRSM_NB + c] = acc[c];
+                x[r] = a0 + a1;
             }
             __syncthreads();
         }
-        for (int e = t; e < m * TRSM_NB; e += TRSM_THREADS) {
-            const int i = e / TRSM_NB, jj = e % TRSM_NB;
-            if (jj < nc) B[(int64_t)i * b_rs + j0 + jj] = x[e];
-        }
-        __syncthreads();
+        for (int i = row0 + t; i < m; i += TRSM_THREADS) B[(int64_t)i * b_rs + j] = x[i];
+        __syncthreads();   // x and col_s are reused by the next column
     }
 }
 
@@ -351,7 +375,8 @@ __device__ __forceinline__ double pivot_rcp(double d, int* status) {
 }
 
 // CTA-wide: factors the nb x nb diagonal block at (p0, p0) of X in shared memory (a) and
-// forms Z = L_pp^{-1} (z) in the same right-looking sweep, then writes L_pp (upper part
+// forms Z = L_pp^{-1} (z) in the same right-looking sweep (a_loaded: the block's lower
+// triangle is already in a, left there by the lookahead tile), then writes L_pp (upper part
 // zero) back to X and Z to zbuf. The sweep is the unscaled elimination X = L' D L'^*
 // (L' unit lower, D the pivots): per column c, with the multiplier L'[r][c] = a[r][c] / d_c,
 // row r of the trailing block loses L'[r][c] times column c (a) and row r of Z' = L'^{-1}
@@ -360,11 +385,11 @@ __device__ __forceinline__ double pivot_rcp(double d, int* status) {
 // At the end L = L' D^{1/2} and Z = D^{-1/2} Z', with the reciprocal square roots of all
 // pivots formed in parallel.
 __device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[CHP_NB + 1], double (*z)[CHP_NB + 1],
-                                double* ys) {
+                                double* ys, bool a_loaded) {
     const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     for (int e = t; e < CHP_NB * CHP_NB; e += CHP_THREADS) {
         const int i = e / CHP_NB, j = e % CHP_NB;
-        a[i][j] = (i < nb && j <= i) ? __ldcg(p.X + (int64_t)(p0 + i) * m + p0 + j) : 0.0;
+        if (!a_loaded) a[i][j] = (i < nb && j <= i) ? __ldcg(p.X + (int64_t)(p0 + i) * m + p0 + j) : 0.0;
         z[i][j] = (i == j) ? 1.0 : 0.0;
     }
     __syncthreads();
@@ -398,9 +423,10 @@ __device__ void chp_factor_diag(const CholPDev& p, int p0, int nb, double (*a)[C
 }
 
 // Trailing update tile `tile` of the panel at p0 (16 x 16, lower triangle of rows/columns
-// [base, m)): X[r][q] -= sum_c L[r][p0+c] L[q][p0+c].
+// [base, m)): X[r][q] -= sum_c L[r][p0+c] L[q][p0+c]. With `out` the updated entries go to
+// out[i][j] (tile-local indices) instead of X.
 __device__ void chp_update_tile(const CholPDev& p, int p0, int nb, int base, int tile, double (*pr)[CHP_NB + 1],
-                                double (*pq)[CHP_NB + 1]) {
+                                double (*pq)[CHP_NB + 1], double (*out)[CHP_NB + 1] = nullptr) {
     const int m = p.m, t = threadIdx.x;
     int u = tile, tr = 0;
     while (u > tr) { u -= tr + 1; ++tr; }
@@ -424,13 +450,16 @@ __device__ void chp_update_tile(const CholPDev& p, int p0, int nb, int base, int
             acc2 = fma(pr[i][c + 2], pq[j][c + 2], acc2);
             acc3 = fma(pr[i][c + 3], pq[j][c + 3], acc3);
         }
-        *xp = x0 - ((acc0 + acc1) + (acc2 + acc3));
+        const double xn = x0 - ((acc0 + acc1) + (acc2 + acc3));
+        if (out) out[i][j] = xn;
+        else *xp = xn;
     }
     __syncthreads();
 }
 
-// Panels with lookahead: CTA 0 updates the three tiles that cover the next diagonal block
-// first and factors that block while the other CTAs finish the trailing update, so that a
+// Panels with lookahead: CTA 0 updates the tile that covers the next diagonal block first
+// (into shared memory) and factors that block while the other CTAs finish the trailing
+// update, so that a
 // panel costs two grid exchanges: (L_pp, Z ready) -> panel rows -> (panel rows ready) ->
 // trailing update and the next diagonal block.
 __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDev p) {
@@ -443,7 +472,7 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
     const int m = p.m, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int G = gridDim.x;
     unsigned int nsync = 0;
-    if (blockIdx.x == 0) chp_factor_diag(p, 0, min(CHP_NB, m), a, z, ys);
+    if (blockIdx.x == 0) chp_factor_diag(p, 0, min(CHP_NB, m), a, z, ys, false);
     for (int p0 = 0; p0 < m; p0 += CHP_NB) {
         const int nb = min(CHP_NB, m - p0);
         const int base = p0 + nb, rest = m - base;
@@ -466,14 +495,15 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
             if (lane < nb) row[lane] = x0 + x1;
         }
         if (!chp_grid_sync(p, ++nsync, &ok_s)) return;
-        // trailing update; tiles 0-2 (the next diagonal block) on CTA 0, which then factors it
+        // trailing update; tile 0 (the next diagonal block) on CTA 0, which updates it into
+        // shared memory and factors it from there
         const int nt = (rest + CHP_TILE - 1) / CHP_TILE;
         const int ntiles = nt * (nt + 1) / 2;
-        constexpr int kLead = (CHP_NB / CHP_TILE) * (CHP_NB / CHP_TILE + 1) / 2;   // tiles of the next block
-        const int lead = ntiles < kLead ? ntiles : kLead;
+        static_assert(CHP_NB == CHP_TILE, "the next diagonal block is one tile");
+        const int lead = 1;
         if (blockIdx.x == 0) {
-            for (int tile = 0; tile < lead; ++tile) chp_update_tile(p, p0, nb, base, tile, pr, pq);
-            chp_factor_diag(p, base, min(CHP_NB, rest), a, z, ys);
+            chp_update_tile(p, p0, nb, base, 0, pr, pq, a);
+            chp_factor_diag(p, base, min(CHP_NB, rest), a, z, ys, true);
             if (G == 1)
                 for (int tile = lead; tile < ntiles; ++tile) chp_update_tile(p, p0, nb, base, tile, pr, pq);
         } else {
@@ -488,27 +518,35 @@ __global__ void __launch_bounds__(CHP_THREADS, 1) chol_persistent_kernel(CholPDe
 cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
                  double* Bm, int64_t b_rs, int ncols, double* dinv_work, int* status, cudaStream_t s, bool rhs_lower) {
     if (m <= 0 || ncols <= 0) return cudaSuccess;
-    const size_t smem = (size_t)m * TRSM_NB * sizeof(double);
+    const size_t smem = (size_t)m * sizeof(double);
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     const int nblk = (m + TRSM_BS - 1) / TRSM_BS;
-    const unsigned grid = (unsigned)(((ncols + TRSM_NB - 1) / TRSM_NB + 1) / 2);
+    unsigned int* next_col = (unsigned int*)(dinv_work + (size_t)nblk * TRSM_BS * TRSM_BS);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min(ncols, std::max(sms, 1));
+    cudaError_t e = cudaMemsetAsync(next_col, 0, sizeof(unsigned int), s);
+    if (e != cudaSuccess) return e;
     if (lower) {
-        tri_diag_inv_kernel<true><<<nblk, TRSM_BS, 0, s>>>(T, t_rs, t_cs, m, dinv_work, status);
+        tri_diag_inv_kernel<true><<<nblk, TDI_THREADS, 0, s>>>(T, t_rs, t_cs, m, dinv_work, status);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(trsm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         trsm_kernel<true><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, dinv_work,
-                                                             rhs_lower ? 1 : 0);
+                                                             rhs_lower ? 1 : 0, next_col);
     } else {
-        tri_diag_inv_kernel<false><<<nblk, TRSM_BS, 0, s>>>(T, t_rs, t_cs, m, dinv_work, status);
+        tri_diag_inv_kernel<false><<<nblk, TDI_THREADS, 0, s>>>(T, t_rs, t_cs, m, dinv_work, status);
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(trsm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        trsm_kernel<false><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, dinv_work, 0);
+        trsm_kernel<false><<<grid, TRSM_THREADS, smem, s>>>(T, t_rs, t_cs, m, Bm, b_rs, ncols, dinv_work, 0,
+                                                              next_col);
     }
     note_launch(2);
     return cudaGetLastError();
 }
 
-size_t trsm_work_doubles(int m) { return (size_t)((m + TRSM_BS - 1) / TRSM_BS) * TRSM_BS * TRSM_BS; }
+// the diagonal-block inverses, then one word for the column counter
+size_t trsm_work_doubles(int m) { return (size_t)((m + TRSM_BS - 1) / TRSM_BS) * TRSM_BS * TRSM_BS + 2; }
 
 cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s) {
     // Persistent cooperative form; the per-panel launches below when it cannot run.

@@ -60,7 +60,7 @@ constexpr size_t kPartElems = 1216ull * 4096ull;   // bounds every split-K slab 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t status, S, qr_work, perm, R, RinvT, Lc, T1, dinv, W, part, cbuf, ebuf, hbuf, dhbuf, sbuf;
+    size_t status, S, qr_work, perm, R, RinvT, Lc, Lt, T1, dinv, W, part, cbuf, ebuf, hbuf, dhbuf, sbuf;
     size_t mixed_base, mixed_bytes;
     size_t total;
 };
@@ -89,6 +89,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtp
     L.R = take((size_t)m * m * 8);
     L.RinvT = take((size_t)m * m * 8);
     L.Lc = take((size_t)m * m * 8);
+    L.Lt = take((size_t)m * m * 8);
     L.T1 = take((size_t)m * m * 8);
     L.dinv = take(trsm_work_doubles((int)m) * 8);
     L.W = take((size_t)m * n * 8);
@@ -285,6 +286,7 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A
     h->R = (double*)(b + L.R);
     h->RinvT = (double*)(b + L.RinvT);
     h->Lc = (double*)(b + L.Lc);
+    h->Lt = (double*)(b + L.Lt);
     h->T1 = (double*)(b + L.T1);
     h->dinv = (double*)(b + L.dinv);
     h->W = (double*)(b + L.W);
@@ -372,8 +374,10 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     // 4. X = L L^* (in place of Y = X^{-1}, Eq. 16), T1 = L^{-1} R^{-*}
     phase_begin(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(cholesky(h->Lc, m, h->part, h->part_elems, h->status, s));
+    // the solve reads L through its transpose, so that a warp's loads of T are coalesced
+    RT_CHECK(transpose_copy(h->Lc, m, h->Lt, m, m, m, s));
     RT_CHECK(cudaMemcpyAsync(h->T1, h->RinvT, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
-    RT_CHECK(trsm(h->Lc, m, 1, true, m, h->T1, m, m, h->dinv, h->status, s, true));     // R^{-*} is lower
+    RT_CHECK(trsm(h->Lt, 1, m, true, m, h->T1, m, m, h->dinv, h->status, s, true));     // R^{-*} is lower
     phase_end(h, RTPROJ_PHASE_FACTOR);
     if (h->opts.mode == RTPROJ_MIXED_REFINED) {
         st = mixed_prepare_middle(h);

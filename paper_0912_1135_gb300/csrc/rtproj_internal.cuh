@@ -103,7 +103,8 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
 // Triangular solves and Cholesky (k_tri.cu).
 // Solves op(T) X = Bm in place; T (m x m) element (i,j) at T[i*t_rs + j*t_cs];
 // lower selects forward substitution. Bm element (i, j) at Bm[i*b_rs + j], j < ncols.
-// dinv_work: trsm_work_doubles(m) doubles (inverses of the 32 x 32 diagonal blocks).
+// dinv_work: trsm_work_doubles(m) doubles (inverses of the 32 x 32 diagonal blocks and a
+// column counter). T is read row by row across a warp's threads: t_rs = 1 coalesces.
 // rhs_lower (lower solves only): Bm is zero above its diagonal, so the solution is too and
 // the rows above each column are skipped.
 cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
@@ -183,6 +184,7 @@ struct rtproj_ctx {
     double* R = nullptr;         // m x m
     double* RinvT = nullptr;     // m x m, R^{-*}
     double* Lc = nullptr;        // m x m, chol(X)
+    double* Lt = nullptr;        // m x m, chol(X)^* (read by the second triangular solve)
     double* T1 = nullptr;        // m x m, Lc^{-1} R^{-*}
     double* dinv = nullptr;      // inverses of the 32 x 32 diagonal blocks (trsm)
     double* W = nullptr;         // m x n, P^{-1} A (float64 mode)
