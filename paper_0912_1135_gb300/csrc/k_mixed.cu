@@ -185,8 +185,7 @@ rtproj_status mixed_bind(rtproj_ctx* h, char* base, size_t bytes) {
 
 rtproj_status mixed_prepare_a(rtproj_ctx* h) {
     phase_begin(h, RTPROJ_PHASE_SLICE);
-    MX_CHECK(slice_rows(h->A, h->lda, 1, nullptr, nullptr, h->As, h->status, h->stream));
-    MX_CHECK(transpose_planes(h->As, h->Ats, h->stream));
+    MX_CHECK(slice_rows_dual(h->A, h->lda, h->As, h->Ats, h->status, h->stream));
     MX_CHECK(fill_int(h->Ats.e, (int)h->n, 0, h->stream));
     phase_end(h, RTPROJ_PHASE_SLICE);
     // A is read only here in this form: remember whether it held non-finite entries, so

@@ -350,6 +350,73 @@ __global__ void __launch_bounds__(SLF_THREADS) slice_rows_span_kernel(SliceDev a
     row_span_digits<S>(a, row, r, 7 + 8 * (S - 1) - ex, c0, (int)min(a.ld, (int64_t)(c0 + SLF_SPAN)));
 }
 
+// Both digit layouts of a long-row operand in one pass over it: with the row exponents
+// already in e (slice_rows_exp_kernel), CTA (bx, by) takes rows [64 by, 64 by + 64) and
+// columns [64 bx, 64 bx + 64) of X, writes their digits to the row-major planes (a.d,
+// rows < a.rows) and, through a shared-memory tile per plane, to the transposed planes
+// t_d (row c holds column c of X, leading dimension t_ld, rows < t_rows). Tile rows at or
+// past a.rows and columns at or past a.cols give zero digits (the padding of both
+// layouts). Each thread turns two groups of eight consecutive entries of one row into
+// digits: one 16-byte store per plane to the row-major planes; the transposed planes are
+// written from shared memory as 16-byte stores of eight consecutive rows of X.
+constexpr int SLD_TILE = 64;
+constexpr int SLD_THREADS = 256;
+constexpr int SLD_PAD = SLD_TILE + 2;   // bfloat16 per shared row: odd word stride, no bank conflicts on reads
+
+template <int S>
+__global__ void __launch_bounds__(SLD_THREADS) slice_dual_kernel(SliceDev a, __nv_bfloat16* t_d, int64_t t_ld,
+                                                                 int64_t t_ps, int t_rows) {
+    extern __shared__ __align__(16) unsigned char sld_raw[];
+    auto tile = reinterpret_cast<__nv_bfloat16(*)[SLD_TILE][SLD_PAD]>(sld_raw);   // [S][column][row]
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int r0 = blockIdx.y * SLD_TILE, c0 = blockIdx.x * SLD_TILE;
+    const int g = lane & 7;                                  // group of eight columns
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+        const int rr = (warp * 2 + it) * 4 + (lane >> 3);    // tile row, 0 .. 63
+        const int r = r0 + rr, cb = c0 + 8 * g;
+        const bool live = r < a.rows;
+        int ex = live ? a.e[r] : 0;
+        if (ex == SLF_ZERO_ROW) ex = 0;                      // an all-zero row: exponent 0
+        const int base = 7 + 8 * (S - 1) - ex;
+        const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.X + (int64_t)r * a.x_rs);
+        unsigned long long bits[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) bits[k] = (live && cb + k < a.cols) ? __ldg(row + cb + k) : 0ull;
+        uint32_t w[S][4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            int d0[S], d1[S];
+            entry_digits<S>(bits[2 * h], base, d0);
+            entry_digits<S>(bits[2 * h + 1], base, d1);
+#pragma unroll
+            for (int p = 0; p < S; ++p) {
+                const uint32_t b0 = bf16_bits_of_int(d0[p]), b1 = bf16_bits_of_int(d1[p]);
+                w[p][h] = b0 | (b1 << 16);
+                tile[p][8 * g + 2 * h][rr] = __ushort_as_bfloat16((unsigned short)b0);
+                tile[p][8 * g + 2 * h + 1][rr] = __ushort_as_bfloat16((unsigned short)b1);
+            }
+        }
+        if (live) {
+            __nv_bfloat16* drow = a.d + (int64_t)r * a.ld + cb;
+#pragma unroll
+            for (int p = 0; p < S; ++p)
+                *reinterpret_cast<uint4*>(drow + (int64_t)p * a.ps) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+        }
+    }
+    __syncthreads();   // the tile is complete, and every thread has read its rows' exponents
+    if (blockIdx.x == 0 && t < SLD_TILE && r0 + t < a.rows && a.e[r0 + t] == SLF_ZERO_ROW) a.e[r0 + t] = 0;
+    // transposed planes: row c0 + cc, columns r0 + 8 q .. r0 + 8 q + 7 (eight lanes per row)
+    for (int v = t; v < S * SLD_TILE * (SLD_TILE / 8); v += SLD_THREADS) {
+        const int q = v & 7, cc = (v >> 3) & (SLD_TILE - 1), p = v / (SLD_TILE * (SLD_TILE / 8));
+        const int c = c0 + cc;
+        if (c >= t_rows) continue;
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&tile[p][cc][8 * q]);
+        *reinterpret_cast<uint4*>(t_d + (int64_t)p * t_ps + (int64_t)c * t_ld + r0 + 8 * q) =
+            make_uint4(src[0], src[1], src[2], src[3]);
+    }
+}
+
 }  // namespace
 
 cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx, const int32_t* cexp,
@@ -397,6 +464,48 @@ cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_
         }
     } else {
         slice_rows_kernel<<<st.rows, SL_THREADS, 0, s>>>(a);
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t slice_rows_dual(const double* X, int64_t x_rs, const SliceStack& st, const SliceStack& tst, int* status,
+                            cudaStream_t s) {
+    if (st.rows <= 0) return cudaSuccess;
+    const bool ok = st.s >= 1 && st.s <= 10 && tst.s == st.s && st.ld % SLD_TILE == 0 && tst.ld % SLD_TILE == 0 &&
+                    st.ld >= st.cols && tst.ld >= st.rows && tst.rows == st.cols && tst.cols == st.rows &&
+                    st.plane_stride % 8 == 0 && tst.plane_stride % 8 == 0 && ((uintptr_t)st.d & 15) == 0 &&
+                    ((uintptr_t)tst.d & 15) == 0 && ((uintptr_t)X & 7) == 0;
+    if (!ok) {
+        const cudaError_t e = slice_rows(X, x_rs, 1, nullptr, nullptr, st, status, s);
+        return e != cudaSuccess ? e : transpose_planes(st, tst, s);
+    }
+    SliceDev a;
+    a.X = X; a.x_rs = x_rs; a.x_cs = 1; a.rowidx = nullptr; a.cexp = nullptr;
+    a.rows = st.rows; a.cols = st.cols; a.s = st.s;
+    a.d = st.d; a.ld = st.ld; a.ps = st.plane_stride; a.e = st.e; a.status = status;
+    cudaError_t e = fill_int(st.e, st.rows, SLF_ZERO_ROW, s);
+    if (e != cudaSuccess) return e;
+    const dim3 egrid((unsigned)((st.cols + SLF_SPAN - 1) / SLF_SPAN), (unsigned)st.rows);
+    slice_rows_exp_kernel<<<egrid, SLF_THREADS, 0, s>>>(a);
+    note_launch();
+    const dim3 grid((unsigned)(st.ld / SLD_TILE), (unsigned)(tst.ld / SLD_TILE));
+    const size_t smem = (size_t)st.s * SLD_TILE * SLD_PAD * sizeof(__nv_bfloat16);
+    auto launch = [&](auto kern) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        kern<<<grid, SLD_THREADS, smem, s>>>(a, tst.d, tst.ld, tst.plane_stride, tst.rows);
+    };
+    switch (st.s) {
+        case 1: launch(slice_dual_kernel<1>); break;
+        case 2: launch(slice_dual_kernel<2>); break;
+        case 3: launch(slice_dual_kernel<3>); break;
+        case 4: launch(slice_dual_kernel<4>); break;
+        case 5: launch(slice_dual_kernel<5>); break;
+        case 6: launch(slice_dual_kernel<6>); break;
+        case 7: launch(slice_dual_kernel<7>); break;
+        case 8: launch(slice_dual_kernel<8>); break;
+        case 9: launch(slice_dual_kernel<9>); break;
+        default: launch(slice_dual_kernel<10>); break;
     }
     note_launch();
     return cudaGetLastError();

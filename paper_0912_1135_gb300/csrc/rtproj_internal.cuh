@@ -137,6 +137,11 @@ struct SliceStack {
 cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx, const int32_t* cexp,
                        const SliceStack& st, int* status, cudaStream_t s);
 // Digit planes of src transposed into dst (dst.rows = src.cols, dst.ld >= src.rows).
+// Row-major digits of X (rows x cols, contiguous rows) into st and the same digits
+// transposed into tst (tst.rows = st.cols, tst.cols = st.rows, same s), in one pass over
+// the digits: the row exponents first, then 64 x 64 tiles that write both layouts.
+cudaError_t slice_rows_dual(const double* X, int64_t x_rs, const SliceStack& st, const SliceStack& tst, int* status,
+                            cudaStream_t s);
 cudaError_t transpose_planes(const SliceStack& src, const SliceStack& dst, cudaStream_t s);
 // Writes G^* (l x n, reduction over n) as one digit plane plus its row exponents (exact).
 cudaError_t omega_plane(uint64_t seed, int dist, int n, int l, const SliceStack& st, cudaStream_t s);
