@@ -425,7 +425,7 @@ def e2e(torch, rt, A, B, w, args, dev):
     Ah = torch.from_numpy(A).pin_memory()
     Bh = torch.from_numpy(B).pin_memory()
     Zh = [torch.empty(B.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
-    steps = max(1, min(args.steps, 5))
+    steps = max(1, min(args.steps, 15))
     comp = torch.cuda.current_stream(dev)
     copy = torch.cuda.Stream(dev)
     d2h = torch.cuda.Stream(dev)

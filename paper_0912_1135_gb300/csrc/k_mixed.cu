@@ -142,7 +142,7 @@ __global__ void rows_op_kernel(const double* X, int64_t ldx, const double* B, in
 
 rtproj_status gemm(rtproj_ctx* h, const SliceStack& a, const SliceStack& b, int terms, double* C, int64_t c_rs,
                    int64_t c_cs, double alpha = 1.0, double beta = 0.0, const double* Cin = nullptr,
-                   int64_t cin_rs = 0, int64_t cin_cs = 0, bool lower = false) {
+                   int64_t cin_rs = 0, int64_t cin_cs = 0, bool lower = false, int32_t* row_exp = nullptr) {
     SlicedGemm g;
     g.a = a;
     g.b = b;
@@ -150,6 +150,7 @@ rtproj_status gemm(rtproj_ctx* h, const SliceStack& a, const SliceStack& b, int 
     g.C = C; g.c_rs = c_rs; g.c_cs = c_cs;
     g.alpha = alpha; g.beta = beta; g.Cin = Cin; g.cin_rs = cin_rs; g.cin_cs = cin_cs;
     g.lower_only = lower;
+    g.row_exp = row_exp;
     MX_CHECK(sliced_gemm(g, h->sg_scratch, h->sg_scratch_bytes, h->status, h->stream));
     return RTPROJ_OK;
 }
@@ -209,9 +210,12 @@ rtproj_status mixed_gram(rtproj_ctx* h) {
     note_launch();
     MX_CHECK(cudaGetLastError());
     MX_CHECK(slice_rows(h->Mprime, m, 1, nullptr, nullptr, h->Ms, h->status, h->stream));
-    rtproj_status st = gemm(h, h->Ms, first(h->Ats, h->opts.gram_slices), h->opts.gram_slices, h->W, n, 1);
+    // W's row exponents are gathered by the product's output stage, so slicing W reads it once
+    MX_CHECK(fill_int(h->Ws.e, m, kZeroRowExp, h->stream));
+    rtproj_status st = gemm(h, h->Ms, first(h->Ats, h->opts.gram_slices), h->opts.gram_slices, h->W, n, 1, 1.0, 0.0,
+                            nullptr, 0, 0, false, h->Ws.e);
     if (st != RTPROJ_OK) return st;
-    MX_CHECK(slice_rows(h->W, n, 1, nullptr, nullptr, h->Ws, h->status, h->stream));
+    MX_CHECK(slice_rows_given_exp(h->W, n, h->Ws, h->status, h->stream));
     return gemm(h, h->Ws, h->Ws, h->opts.gram2_slices, h->Lc, m, 1, 1.0, 0.0, nullptr, 0, 0, true);
 }
 

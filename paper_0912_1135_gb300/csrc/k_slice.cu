@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(SLF_THREADS) slice_rows_fast_kernel(SliceDev a
 // launches. The first takes each span's maximum exponent into e[r] (atomicMax over spans,
 // e pre-filled with SLF_ZERO_ROW), the second writes the digits of its span.
 constexpr int SLF_SPAN = 8 * SLF_THREADS;
-constexpr int SLF_ZERO_ROW = -(1 << 30);
+constexpr int SLF_ZERO_ROW = kZeroRowExp;
 
 __global__ void __launch_bounds__(SLF_THREADS) slice_rows_exp_kernel(SliceDev a) {
     __shared__ unsigned long long smax[SLF_THREADS / 32];
@@ -464,6 +464,52 @@ cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_
         }
     } else {
         slice_rows_kernel<<<st.rows, SL_THREADS, 0, s>>>(a);
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+namespace {
+bool fast_rows_ok(const double* X, const SliceStack& st) {
+    return st.s >= 1 && st.s <= 10 && st.ld >= st.cols && st.ld % 64 == 0 && st.plane_stride % 8 == 0 &&
+           ((uintptr_t)st.d & 15) == 0 && ((uintptr_t)X & 7) == 0;
+}
+SliceDev rows_dev(const double* X, int64_t x_rs, const SliceStack& st, int* status) {
+    SliceDev a;
+    a.X = X; a.x_rs = x_rs; a.x_cs = 1; a.rowidx = nullptr; a.cexp = nullptr;
+    a.rows = st.rows; a.cols = st.cols; a.s = st.s;
+    a.d = st.d; a.ld = st.ld; a.ps = st.plane_stride; a.e = st.e; a.status = status;
+    return a;
+}
+}  // namespace
+
+cudaError_t row_exponents(const double* X, int64_t x_rs, int rows, int cols, int32_t* e, int* status, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    if (((uintptr_t)X & 7) != 0) return cudaErrorInvalidValue;
+    SliceDev a{};
+    a.X = X; a.x_rs = x_rs; a.x_cs = 1; a.rows = rows; a.cols = cols; a.e = e; a.status = status;
+    const dim3 grid((unsigned)((cols + SLF_SPAN - 1) / SLF_SPAN), (unsigned)rows);
+    slice_rows_exp_kernel<<<grid, SLF_THREADS, 0, s>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t slice_rows_given_exp(const double* X, int64_t x_rs, const SliceStack& st, int* status, cudaStream_t s) {
+    if (st.rows <= 0) return cudaSuccess;
+    if (!fast_rows_ok(X, st)) return slice_rows(X, x_rs, 1, nullptr, nullptr, st, status, s);
+    const SliceDev a = rows_dev(X, x_rs, st, status);
+    const dim3 grid((unsigned)((st.ld + SLF_SPAN - 1) / SLF_SPAN), (unsigned)st.rows);
+    switch (st.s) {
+        case 1: slice_rows_span_kernel<1><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 2: slice_rows_span_kernel<2><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 3: slice_rows_span_kernel<3><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 4: slice_rows_span_kernel<4><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 5: slice_rows_span_kernel<5><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 6: slice_rows_span_kernel<6><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 7: slice_rows_span_kernel<7><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 8: slice_rows_span_kernel<8><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        case 9: slice_rows_span_kernel<9><<<grid, SLF_THREADS, 0, s>>>(a); break;
+        default: slice_rows_span_kernel<10><<<grid, SLF_THREADS, 0, s>>>(a); break;
     }
     note_launch();
     return cudaGetLastError();

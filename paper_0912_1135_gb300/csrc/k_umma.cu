@@ -602,6 +602,7 @@ struct Sg2Dev {
     int m_fast;                   // tile order: A-row tiles fastest
     int vec2;                     // C rows contiguous and 16-byte aligned: paired stores
     int issue_cfg;                // compile-time MMA issue path (0: the general loop)
+    int32_t* row_exp;             // optional: row exponents of C gathered by atomic maxima
 };
 
 
@@ -789,6 +790,25 @@ __device__ __forceinline__ bool issue_kblock(Ring& ra, uint32_t a_lo0, uint32_t 
 struct IssueCfg { int sa, terms, tn; };
 constexpr IssueCfg kIssueCfgs[] = {{7, 7, 32}, {9, 9, 32}, {3, 3, 64}, {1, 5, 64}, {5, 5, 64}, {7, 7, 64}};
 
+// Running record of max |v| for the row exponent, in two integer operations per value:
+// the largest sign-cleared upper word (sign, exponent field, top 20 mantissa bits) and the
+// OR of the lower words. The frexp exponent of the maximum follows from the upper word's
+// maximum alone unless every upper word is zero; then the leading bit of the OR is that
+// of the largest lower word. A non-finite value shows as an all-ones exponent field.
+__device__ __forceinline__ void track_abs_max(double v, uint32_t& mxh, uint32_t& orl) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const uint32_t h = (uint32_t)(u >> 32) & 0x7FFFFFFFu;
+    mxh = h > mxh ? h : mxh;
+    orl |= (uint32_t)u;
+}
+// frexp exponent e (m < 2^e <= 2m) of the maximum recorded by track_abs_max (not all zero).
+__device__ __forceinline__ int frexp_exponent_of_words(uint32_t mxh, uint32_t orl) {
+    const int E = (int)(mxh >> 20);
+    if (E > 0) return E - 1022;
+    if (mxh != 0) return (32 - __clz((int)mxh)) + 32 - 1074;
+    return (32 - __clz((int)orl)) - 1074;
+}
+
 template <int NCOL>
 __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, uint64_t* tfull, uint64_t* tempty,
                                               volatile int* abort_v, int quarter, int half, int lane) {
@@ -841,7 +861,9 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
             if (p.bmode == 0) {
                 // no Cin: the stores follow the conversions directly
                 if (p.vec2) {
-                    // row-contiguous output: pairs of columns as one 16-byte store
+                    // row-contiguous output: pairs of columns as one 16-byte store; with row_exp
+                    // the largest sign-cleared bit pattern of the stored values is kept
+                    uint32_t mxh = 0, orl = 0;
 #pragma unroll
                     for (int j = 0; j < NCOL; j += 2) {
                         const int gj = jb + j;
@@ -849,14 +871,20 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
                         if (!valid || gj >= p.N || (p.lower_only && gj > i)) continue;
                         const double v0 = epilogue_value_v(words_to_double((long long)hi[j], (long long)lo[j], ea + e0),
                                                            p.amode, p.alpha, 0, 0.0, 0.0);
+                        track_abs_max(v0, mxh, orl);
                         if (gj + 1 < p.N && !(p.lower_only && gj + 1 > i)) {
                             const double v1 = epilogue_value_v(
                                 words_to_double((long long)hi[j + 1], (long long)lo[j + 1], ea + e1), p.amode,
                                 p.alpha, 0, 0.0, 0.0);
+                            track_abs_max(v1, mxh, orl);
                             *reinterpret_cast<double2*>(crow_p + gj) = make_double2(v0, v1);
                         } else {
                             crow_p[gj] = v0;
                         }
+                    }
+                    if (p.row_exp && valid) {
+                        if (mxh >= 0x7FF00000u) set_status(p.status, RTPROJ_ENONFINITE);
+                        else if ((mxh | orl) != 0) atomicMax(p.row_exp + row, frexp_exponent_of_words(mxh, orl));
                     }
                 } else {
 #pragma unroll
@@ -1244,14 +1272,18 @@ static int choose_splits(int tiles, int M, int N, int Kp, size_t scratch_bytes, 
     return best;
 }
 
-cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
+namespace {
+cudaError_t sliced_gemm_impl(const SlicedGemm& g0, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s,
+                             bool* exp_done) {
     SlicedGemm g = g0;
+    bool swapped = false;
     // The pipelined kernel needs terms <= sb (the first MMA of a chunk covers every level).
     // Put the operand with more digits on the B side: swap and write C transposed.
     if (g.b.s < g.terms && g.a.s >= g.terms && !g.crow && !g.lower_only) {
         std::swap(g.a, g.b);
         std::swap(g.c_rs, g.c_cs);
         std::swap(g.cin_rs, g.cin_cs);
+        swapped = true;
     }
     const int M = g.a.rows, N = g.b.rows, K = g.a.cols;
     if (M <= 0 || N <= 0) return cudaSuccess;
@@ -1319,6 +1351,8 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     cudaError_t e = cudaFuncSetAttribute(sliced_gemm2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     p.splits = splits;
+    p.row_exp = (g.row_exp && !swapped && splits == 1 && p.bmode == 0 && p.vec2 && !g.crow) ? g.row_exp : nullptr;
+    *exp_done = p.row_exp != nullptr;
     const int ntiles = ts.per_split() * splits;
     static int sms = 0;
     if (!sms) {
@@ -1332,6 +1366,16 @@ cudaError_t sliced_gemm(const SlicedGemm& g0, void* scratch, size_t scratch_byte
     note_launch();
     if (splits > 1) launch_reduce(g, splits, scratch, s);
     return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
+    if (g.row_exp && g.c_cs != 1) return cudaErrorInvalidValue;
+    bool exp_done = false;
+    const cudaError_t e = sliced_gemm_impl(g, scratch, scratch_bytes, status, s, &exp_done);
+    if (e != cudaSuccess || !g.row_exp || exp_done) return e;
+    // the output path that gathers them was not taken: one pass over C
+    return row_exponents(g.C, g.c_rs, g.a.rows, g.b.rows, g.row_exp, status, s);
 }
 
 }  // namespace rtp

@@ -132,11 +132,23 @@ struct SliceStack {
     int max_digit = 128;     // bound on |digit| (255 for the G plane)
 };
 
+// Row exponent of an all-zero row while row maxima are being gathered (atomic maxima over
+// parts of a row start from it); slicing reads it as exponent 0.
+constexpr int kZeroRowExp = -(1 << 30);
+
 // Slices X (element (r, c) at X[r*x_rs + c*x_cs], multiplied by 2^cexp[c] when cexp is
 // given) into the stack; optional row gather. Columns cols..ld-1 are written as zeros.
 cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_t* rowidx, const int32_t* cexp,
                        const SliceStack& st, int* status, cudaStream_t s);
 // Digit planes of src transposed into dst (dst.rows = src.cols, dst.ld >= src.rows).
+// Row exponents of X (rows x cols, contiguous rows): e[r] <- max(e[r], the frexp exponent
+// of max_c |X[r][c]|), e pre-filled with kZeroRowExp; non-finite entries raise
+// RTPROJ_ENONFINITE in status.
+cudaError_t row_exponents(const double* X, int64_t x_rs, int rows, int cols, int32_t* e, int* status, cudaStream_t s);
+// Slices X (contiguous rows) into st with the row exponents already in st.e (gathered as
+// by row_exponents, kZeroRowExp for an all-zero row): one read of X, spread over spans of
+// every row. Falls back to slice_rows when the fast layout conditions do not hold.
+cudaError_t slice_rows_given_exp(const double* X, int64_t x_rs, const SliceStack& st, int* status, cudaStream_t s);
 // Row-major digits of X (rows x cols, contiguous rows) into st and the same digits
 // transposed into tst (tst.rows = st.cols, tst.cols = st.rows, same s), in one pass over
 // the digits: the row exponents first, then 64 x 64 tiles that write both layouts.
@@ -157,6 +169,10 @@ struct SlicedGemm {
     double alpha = 1.0, beta = 0.0;
     const double* Cin = nullptr; int64_t cin_rs = 0, cin_cs = 0;
     bool lower_only = false;
+    // Optional: row exponents of the output gathered as by row_exponents (e pre-filled with
+    // kZeroRowExp), from the values as they are stored, so that slicing C needs no pass of
+    // its own over C for them.
+    int32_t* row_exp = nullptr;
 };
 size_t sliced_gemm_scratch_bytes(int M, int N, int K);
 cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s);
