@@ -145,7 +145,10 @@ class Projector:
         nbytes = lib.rtproj_workspace_bytes(self.m, self.n, self.l_max, self.k_max, ctypes.byref(self.opts))
         if nbytes == 0:
             raise RtprojError(1, "rtproj_workspace_bytes")
-        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        # allocated on the handle's stream, so that the caching allocator reuses the memory
+        # only after the work queued on that stream
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             code = lib.rtproj_create(ctypes.byref(h), self.m, self.n, _dev_ptr(A), self.lda, self.l_max, self.k_max,
@@ -181,7 +184,8 @@ class Projector:
         return self
 
     def sketch(self, seed: int, l: int) -> torch.Tensor:
-        S = torch.empty((self.m, l), dtype=torch.float64, device=self.device)
+        with torch.cuda.stream(self.stream):
+            S = torch.empty((self.m, l), dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
             _check(load_library().rtproj_sketch(self._h, ctypes.c_uint64(seed), l, _dev_ptr(S), l), "rtproj_sketch")
         return S
@@ -222,9 +226,11 @@ class Projector:
                 out_null: torch.Tensor | None = None):
         B = self._rhs(B)
         k = B.shape[0]
-        Z = (out_null if out_null is not None else torch.empty((k, self.n), dtype=torch.float64, device=self.device)) if null else None
-        ROW = torch.empty((k, self.n), dtype=torch.float64, device=self.device) if row else None
-        X = torch.empty((k, self.m), dtype=torch.float64, device=self.device) if lstsq else None
+        with torch.cuda.stream(self.stream):   # outputs belong to the handle's stream
+            Z = (out_null if out_null is not None else torch.empty((k, self.n), dtype=torch.float64,
+                                                                   device=self.device)) if null else None
+            ROW = torch.empty((k, self.n), dtype=torch.float64, device=self.device) if row else None
+            X = torch.empty((k, self.m), dtype=torch.float64, device=self.device) if lstsq else None
         ptr = lambda t: _dev_ptr(t) if t is not None else None
         ld = lambda t: t.stride(0) if t is not None else 0
         with torch.cuda.device(self.device):
