@@ -356,9 +356,10 @@ __global__ void __launch_bounds__(SLF_THREADS) slice_rows_span_kernel(SliceDev a
 // rows < a.rows) and, through a shared-memory tile per plane, to the transposed planes
 // t_d (row c holds column c of X, leading dimension t_ld, rows < t_rows). Tile rows at or
 // past a.rows and columns at or past a.cols give zero digits (the padding of both
-// layouts). Each thread turns two groups of eight consecutive entries of one row into
-// digits: one 16-byte store per plane to the row-major planes; the transposed planes are
-// written from shared memory as 16-byte stores of eight consecutive rows of X.
+// layouts). Each thread turns two groups of eight consecutive entries of a row (one group
+// per pass, the two in different rows) into digits: one 16-byte store per plane to the
+// row-major planes; the transposed planes are written from shared memory as 16-byte
+// stores of eight consecutive rows of X.
 constexpr int SLD_TILE = 64;
 constexpr int SLD_THREADS = 256;
 constexpr int SLD_PAD = SLD_TILE + 2;   // bfloat16 per shared row: odd word stride, no bank conflicts on reads

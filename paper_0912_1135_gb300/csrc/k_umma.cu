@@ -862,7 +862,7 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
                 // no Cin: the stores follow the conversions directly
                 if (p.vec2) {
                     // row-contiguous output: pairs of columns as one 16-byte store; with row_exp
-                    // the largest sign-cleared bit pattern of the stored values is kept
+                    // the stored values' maximum magnitude is recorded (track_abs_max)
                     uint32_t mxh = 0, orl = 0;
 #pragma unroll
                     for (int j = 0; j < NCOL; j += 2) {
@@ -1370,7 +1370,7 @@ cudaError_t sliced_gemm_impl(const SlicedGemm& g0, void* scratch, size_t scratch
 }  // namespace
 
 cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes, int* status, cudaStream_t s) {
-    if (g.row_exp && g.c_cs != 1) return cudaErrorInvalidValue;
+    if (g.row_exp && (g.c_cs != 1 || g.lower_only)) return cudaErrorInvalidValue;   // whole contiguous rows only
     bool exp_done = false;
     const cudaError_t e = sliced_gemm_impl(g, scratch, scratch_bytes, status, s, &exp_done);
     if (e != cudaSuccess || !g.row_exp || exp_done) return e;

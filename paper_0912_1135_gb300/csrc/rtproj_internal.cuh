@@ -171,7 +171,7 @@ struct SlicedGemm {
     bool lower_only = false;
     // Optional: row exponents of the output gathered as by row_exponents (e pre-filled with
     // kZeroRowExp), from the values as they are stored, so that slicing C needs no pass of
-    // its own over C for them.
+    // its own over C for them. Needs contiguous output rows (c_cs = 1) and !lower_only.
     int32_t* row_exp = nullptr;
 };
 size_t sliced_gemm_scratch_bytes(int M, int N, int K);
