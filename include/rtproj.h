@@ -23,7 +23,9 @@
  *   - All work is enqueued on the stream given to rtproj_create (a cudaStream_t
  *     passed as void*; NULL means the legacy default stream). Calls are
  *     asynchronous except rtproj_precondition, rtproj_get_info, rtproj_export_state
- *     and rtproj_sketch, which synchronize that stream once.
+ *     and rtproj_sketch, which synchronize that stream once, and rtproj_create in the
+ *     mixed mode, which waits for the slicing of A to learn whether A held non-finite
+ *     entries.
  *   - Errors: invalid arguments return immediately with a status and enqueue
  *     nothing. Conditions found on the device (rank deficiency, Cholesky breakdown,
  *     non-finite values, an expired bounded wait) are latched in a device status
@@ -122,9 +124,10 @@ size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max
                               const rtproj_opts* opts);
 
 /* Creates a handle bound to the device matrix A (m x n, row-major, lda >= n, 1 <= m <= n),
-   the caller's device workspace and stream. In the mixed mode it also enqueues the
-   slicing of A into bfloat16 slice planes (kept in the workspace). The current CUDA
-   device must be the one that holds A and the workspace. */
+   the caller's device workspace and stream. In the mixed mode it also slices A into
+   bfloat16 slice planes, in both the row-major and the transposed layout (kept in the
+   workspace), and synchronizes the stream once; the later calls of that mode read only
+   the planes. The current CUDA device must be the one that holds A and the workspace. */
 rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A, int64_t lda,
                             int64_t l_max, int64_t k_max, void* workspace, size_t ws_bytes,
                             void* stream, const rtproj_opts* opts);
