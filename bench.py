@@ -7,7 +7,7 @@ refinement pass in the mixed form). value = k * steps / (device time of the time
 steps), all ranks together; each rank runs an independent replica (one GPU each).
 
 Workload (synthetic, seeded): A = U diag(sigma) V^T, 512 x 65536 float64, U and V Haar,
-sigma log-spaced over [1e-10, 1]; G uniform on (-1, 1) (Philox4x32-10), l = m + 4 = 516;
+sigma log-spaced over [1e-10, 1]; G standard normal (Box-Muller on Philox4x32-10), l = m + 4 = 516;
 k = 64 right-hand sides with N(0,1) entries. A (268 MB) is larger than L2 (129 MB).
 The line also carries the plain float64 form measured on the same workload (the
 comparison the metric names) and the accuracy of both against the exact oracle.
@@ -345,7 +345,7 @@ def run_ours(args, w, world, rank, local):
         "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "bf16-slices/f64",
         "data": "synthetic",
         "config": {"workload": w.name, "mode": args.mode, "m": w.m, "n": w.n, "k": w.k, "l": w.l,
-                   "kappa": 1.0 / w.sigma_min, "omega": "uniform(-1,1), Philox4x32-10",
+                   "kappa": 1.0 / w.sigma_min, "omega": "gaussian (Box-Muller on Philox4x32-10, 2^-12 grid)",
                    "step": "precondition(seed, l) + null_project(k RHS)",
                    "l2": "inputs larger than L2 (A is 268 MB float64)", "parallelism": f"replicas x{world}"},
         "phase_ms_per_step": {p: phase_ms[p] / args.steps for p in phase_ms if phase_cnt[p]},

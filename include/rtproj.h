@@ -12,7 +12,10 @@
  * (Eqs. 12-13), G an n x l random matrix generated on the device and never stored.
  *
  * Conventions (all functions):
- *   - Matrices are row-major float64. A is m x n with leading dimension lda >= n.
+ *   - Matrices are row-major. A, the right-hand sides and the outputs of the apply are
+ *     float64, or float32 when the handle was created with opts.dtype = RTPROJ_F32 (they
+ *     are then passed as void*; every internal quantity stays float64 and float32 input is
+ *     widened exactly). A is m x n with leading dimension lda >= n (in elements).
  *     Right-hand sides are stored as ROWS: B is k x n (row j is the j-th vector b),
  *     ldb >= n; null/row-space outputs are k x n; least-squares outputs are k x m.
  *   - Pointers named A, B, Z, ROW, H, S, workspace are DEVICE pointers unless the
@@ -23,9 +26,10 @@
  *   - All work is enqueued on the stream given to rtproj_create (a cudaStream_t
  *     passed as void*; NULL means the legacy default stream). Calls are
  *     asynchronous except rtproj_precondition, rtproj_get_info, rtproj_export_state
- *     and rtproj_sketch, which synchronize that stream once, and rtproj_create in the
+ *     and rtproj_sketch, which synchronize that stream once, rtproj_create in the
  *     mixed mode, which waits for the slicing of A to learn whether A held non-finite
- *     entries.
+ *     entries, and the apply calls when opts.refine_tol > 0, which read the size of
+ *     each refinement correction back to decide whether to stop.
  *   - Errors: invalid arguments return immediately with a status and enqueue
  *     nothing. Conditions found on the device (rank deficiency, Cholesky breakdown,
  *     non-finite values, an expired bounded wait) are latched in a device status
@@ -54,7 +58,8 @@ typedef enum {
     RTPROJ_ENOTSPD = 4,      /* Cholesky of X = P^{-1} A A^* P^{-*} broke down            */
     RTPROJ_ENONFINITE = 5,   /* a NaN or infinity reached the factorizations             */
     RTPROJ_ETIMEOUT = 6,     /* a bounded device-side wait gave up                        */
-    RTPROJ_ENOMEM = 7,       /* workspace smaller than rtproj_workspace_bytes()           */
+    RTPROJ_ENOMEM = 7,       /* workspace smaller than rtproj_workspace_bytes(), or (for
+                                rtproj_sketch_noalloc) m * l above its fixed scratch array */
     RTPROJ_ECUDA = 8,        /* a CUDA runtime call failed                                */
     RTPROJ_EUNSUPPORTED = 9  /* option combination not supported                          */
 } rtproj_status;
@@ -71,25 +76,48 @@ typedef enum {
     RTPROJ_MIXED_REFINED = 1
 } rtproj_mode;
 
-/* Distribution of the entries of G (Eq. 12). Entry (i, j) of G takes byte
-   u = byte (i & 3) of word ((i & 15) >> 2) of Philox4x32-10 (Salmon et al., SC'11)
-   at counter (i >> 4, j, 0, 0) with key (seed mod 2^32, seed >> 32). */
+/* Element type of A, the right-hand sides and the apply's outputs. */
+typedef enum {
+    RTPROJ_F64 = 0,
+    RTPROJ_F32 = 1
+} rtproj_dtype;
+
+/* Distribution of the entries of G (Eq. 12), from Philox4x32-10 (Salmon, Moraes, Dror &
+   Shaw, SC'11) with key (seed mod 2^32, seed >> 32).
+   UNIFORM and RADEMACHER: entry (i, j) takes byte u = byte (i & 3) of word
+   ((i & 15) >> 2) of the block at counter (i >> 4, j, 0, 0).
+   GAUSSIAN: entries 4q .. 4q+3 of column j come from the block (x, y, z, w) at counter
+   (q, j, 1, 0) by the Box-Muller transform (Box & Muller, Ann. Math. Stat. 1958) in
+   float32: u1 = ((x >> 9) + 1/2) 2^-23, u2 = (y >> 9) 2^-23, r = sqrt(-2 ln u1),
+   entries 4q and 4q+1 are r cos(2 pi u2) and r sin(2 pi u2), and (z, w) give 4q+2 and
+   4q+3 the same way; each variate is then rounded to the nearest multiple of 2^-12
+   (ties to even), so |G_ij| < 5.78 and every entry is exact in two bfloat16 digits. */
 typedef enum {
     RTPROJ_OMEGA_UNIFORM = 0,     /* (2u - 255)/256: uniform on (-1,1), as in Tables 1, 2, 5, 6 */
-    RTPROJ_OMEGA_RADEMACHER = 1   /* +1 if u >= 128 else -1                                    */
+    RTPROJ_OMEGA_RADEMACHER = 1,  /* +1 if u >= 128 else -1                                    */
+    RTPROJ_OMEGA_GAUSSIAN = 2     /* standard normal (Section 3, Theorem 3.1; Tables 3, 4)     */
 } rtproj_omega;
 
 typedef struct {
     int mode;            /* rtproj_mode (default RTPROJ_MIXED_REFINED)                    */
-    int omega;           /* rtproj_omega (default RTPROJ_OMEGA_UNIFORM)                   */
+    int omega;           /* rtproj_omega (default RTPROJ_OMEGA_GAUSSIAN)                  */
     int sketch_slices;   /* mixed: slices of A in S = A G            (default 5, 1..10)  */
     int gram_slices;     /* mixed: slices in W = P^{-1} A            (default 7, 1..10)  */
     int gram2_slices;    /* mixed: slices in X = W W^*               (default 3, 1..10)  */
     int apply_slices;    /* mixed: slices in c = A b and A^* dh      (default 7, 1..10)  */
     int resid_slices;    /* mixed: slices in the refinement residual (default 9, 1..10)  */
-    int refine_passes;   /* mixed: refinement passes                 (default 1, 0..4)   */
+    int refine_passes;   /* mixed: refinement passes (default 1, 0..8); with refine_tol > 0
+                            the largest number of passes                                 */
     int timing;          /* 1: record CUDA events around each phase (rtproj_get_timings)  */
     double rank_tol;     /* ERANK threshold; <= 0 selects 64 * l * 2^-52                  */
+    int dtype;           /* rtproj_dtype of A, B and the outputs (default RTPROJ_F64)     */
+    long long spin_limit_cycles;  /* bound, in SM clock cycles, on each grid-exchange wait of
+                            the pivoted QR and the Cholesky (default 4e9, about 2 s); when it
+                            expires the kernel latches RTPROJ_ETIMEOUT and every CTA returns.
+                            The tensor-core products keep their own fixed bound.          */
+    double refine_tol;   /* mixed: refine until the correction dh of every right-hand side
+                            satisfies ||dh|| <= refine_tol ||h|| (Remark 4.3), at most
+                            refine_passes passes; 0 (default) runs exactly refine_passes  */
 } rtproj_opts;
 
 /* Phases timed when opts.timing is set (indices into rtproj_get_timings' arrays). */
@@ -112,6 +140,16 @@ typedef struct {
     double r11, rmm;         /* |R_11| and |R_mm| of the pivoted QR of S^*                */
     double l11, lmm;         /* largest and smallest diagonal entries of chol(X)          */
     float ms_precondition;   /* device time of the last rtproj_precondition (ms)          */
+    double kappa_R;          /* r11 / rmm: estimates kappa(A G), about kappa(A) (Lemma 2.4) */
+    double kappa_pre;        /* l11 / lmm: lower estimate of kappa(P^{-1} A) = kappa(X)^(1/2) */
+    double norm_A;           /* ||A||_F, computed at create                               */
+    double resid_rel;        /* mixed form, last apply: max over right-hand sides of
+                                ||A s|| / (||A||_F ||b||) for the s that entered the last
+                                refinement pass (Section 5's delta, normalised); 0 when no
+                                pass ran                                                  */
+    double dh_rel;           /* mixed form, last apply: max over right-hand sides of
+                                ||dh|| / ||h|| of the last refinement correction          */
+    int passes;              /* refinement passes run by the last apply                   */
 } rtproj_info;
 
 /* Fills *opts with the defaults listed above. */
@@ -128,7 +166,7 @@ size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max
    bfloat16 slice planes, in both the row-major and the transposed layout (kept in the
    workspace), and synchronizes the stream once; the later calls of that mode read only
    the planes. The current CUDA device must be the one that holds A and the workspace. */
-rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A, int64_t lda,
+rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, int64_t lda,
                             int64_t l_max, int64_t k_max, void* workspace, size_t ws_bytes,
                             void* stream, const rtproj_opts* opts);
 
@@ -142,21 +180,21 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l);
 /* Null-space projection (Eq. 11; the seven steps of Section 4, then b - b~):
    Z = rows of Zb for the k rows of B (k <= k_max). Z may alias B exactly
    (Z == B, ldz == ldb) but must not partially overlap it. */
-rtproj_status rtproj_null_project(rtproj_t h, const double* B, int64_t ldb, int64_t k,
-                                  double* Z, int64_t ldz);
+rtproj_status rtproj_null_project(rtproj_t h, const void* B, int64_t ldb, int64_t k,
+                                  void* Z, int64_t ldz);
 
 /* Row-space projection b~ = A^* h (step 7 of Section 4), k x n into ROW. */
-rtproj_status rtproj_row_project(rtproj_t h, const double* B, int64_t ldb, int64_t k,
-                                 double* ROW, int64_t ldr);
+rtproj_status rtproj_row_project(rtproj_t h, const void* B, int64_t ldb, int64_t k,
+                                 void* ROW, int64_t ldr);
 
 /* Least-squares solutions h = argmin ||A^* h - b|| (Remark 4.1), k x m into X. */
-rtproj_status rtproj_lstsq(rtproj_t h, const double* B, int64_t ldb, int64_t k,
-                           double* X, int64_t ldx);
+rtproj_status rtproj_lstsq(rtproj_t h, const void* B, int64_t ldb, int64_t k,
+                           void* X, int64_t ldx);
 
 /* All three outputs of one apply; any output pointer may be NULL. */
-rtproj_status rtproj_project(rtproj_t h, const double* B, int64_t ldb, int64_t k,
-                             double* Z, int64_t ldz, double* ROW, int64_t ldr,
-                             double* X, int64_t ldx);
+rtproj_status rtproj_project(rtproj_t h, const void* B, int64_t ldb, int64_t k,
+                             void* Z, int64_t ldz, void* ROW, int64_t ldr,
+                             void* X, int64_t ldx);
 
 /* Sketch only: S = A G (Eq. 12) into the device buffer S (m x l, row-major, lds >= l),
    in the handle's mode (float64 products, or sketch_slices bfloat16 slices of A).
@@ -166,10 +204,11 @@ rtproj_status rtproj_sketch(rtproj_t h, uint64_t seed, int64_t l, double* S, int
 /* The float64 sketch S = A G of rtproj_sketch, for callers that cannot allocate device
    memory: applications whose device memory is owned by a pooling allocator or a fixed
    budget (a cudaMalloc would fail or fragment the pool), and loops that cannot afford the
-   device synchronization cudaMalloc implies. The paper has no counterpart; this is a
-   packaging of its sketch step (Eq. 12) that needs no workspace.
+   device synchronization cudaMalloc implies. The paper has no counterpart: it is a
+   packaging of the sketch that needs no workspace.
    A (m x n, row-major, lda >= n) and S (m x l, row-major, lds >= l) are device pointers,
-   m <= l <= n; omega is an rtproj_omega value; stream is a cudaStream_t passed as void*.
+   m <= l <= n; omega is an rtproj_omega value; stream is a cudaStream_t passed as void*
+   and must belong to the current device (RTPROJ_EINVAL otherwise).
    The split-K scratch is a fixed array inside the library: 32 MiB of device memory
    (4 Mi float64 entries), held on every GPU that loads the library until the process
    exits. Nothing is allocated. Returns RTPROJ_ENOMEM when m * l exceeds 4 Mi entries and
@@ -179,6 +218,16 @@ rtproj_status rtproj_sketch(rtproj_t h, uint64_t seed, int64_t l, double* S, int
    calls that overlap on the GPU race on it, so serialize them. */
 rtproj_status rtproj_sketch_noalloc(const double* A, int64_t m, int64_t n, int64_t lda, uint64_t seed,
                                     int64_t l, int omega, double* S, int64_t lds, void* stream);
+
+/* The test matrix G of Eq. 12 itself: entries G[i][j] (i < n, j < l) of distribution
+   omega (an rtproj_omega value) for seed, written as float64 into the device buffer G
+   (n x l, row-major, ldg >= l) on stream (a cudaStream_t passed as void*). The sketch
+   never stores G; this entry point exists to check step a1 on its own. Asynchronous;
+   RTPROJ_EINVAL for invalid arguments. */
+rtproj_status rtproj_generate_omega(uint64_t seed, int64_t n, int64_t l, int omega, double* G, int64_t ldg, void* stream);
+
+/* Replaces the handle's spin_limit_cycles (see rtproj_opts) for later calls; cycles >= 1. */
+rtproj_status rtproj_set_spin_limit(rtproj_t h, long long cycles);
 
 /* Copies the preconditioner state to HOST buffers (any may be NULL): R (m x m,
    row-major, upper triangular), perm (m entries: position j of the pivoted QR holds

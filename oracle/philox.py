@@ -25,6 +25,18 @@ it takes byte u, and maps it by the chosen distribution:
 * ``rademacher``: G_ij = +1 if u >= 128 else -1.
 
 Both maps are exact integer arithmetic, so the two sides agree bit for bit.
+
+* ``gaussian`` (the variates of Section 3's theory, Theorem 3.1, and of Tables 3-4):
+  entries 4q .. 4q+3 of column j come from the block (x, y, z, w) with counter
+  (q, j, 1, 0) by the Box-Muller transform (G. E. P. Box and M. E. Muller, "A note on
+  the generation of random normal deviates", Ann. Math. Stat. 29, 1958): with
+  u1 = ((x >> 9) + 1/2) 2^-23 in (0, 1) and u2 = (y >> 9) 2^-23 in [0, 1),
+  r = sqrt(-2 ln u1), entries 4q and 4q+1 are r cos(2 pi u2) and r sin(2 pi u2);
+  (z, w) give 4q+2 and 4q+3 the same way. Each variate is rounded to the nearest
+  multiple of 2^-12 (ties to even). The oracle evaluates the transform in float64; the
+  GPU in float32, so the two can round to neighbouring multiples when the variate lies
+  within float32's error of a midpoint: ``gaussian_ambiguous`` marks those entries
+  (a few per thousand), and everywhere else the two sides agree bit for bit.
 """
 from __future__ import annotations
 
@@ -36,9 +48,11 @@ W0 = 0x9E3779B9
 W1 = 0xBB67AE85
 MASK32 = 0xFFFFFFFF
 
-DISTRIBUTIONS = ("uniform", "rademacher")
+DISTRIBUTIONS = ("uniform", "rademacher", "gaussian")
+GAUSS_GRID = 4096.0          # Gaussian entries are multiples of 1/4096
 
-__all__ = ["philox4x32_10_scalar", "philox4x32_10", "omega_bytes", "omega", "DISTRIBUTIONS"]
+__all__ = ["philox4x32_10_scalar", "philox4x32_10", "omega_bytes", "omega", "gaussian_variates",
+           "gaussian_ambiguous", "DISTRIBUTIONS", "GAUSS_GRID"]
 
 
 def philox4x32_10_scalar(ctr, key):
@@ -95,7 +109,41 @@ def omega_bytes(seed: int, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
     return ((sel >> shift) & np.uint64(0xFF)).astype(np.uint8)
 
 
-def omega(seed: int, n: int, l: int, dist: str = "uniform", row0: int = 0, col0: int = 0,
+def gaussian_variates(seed: int, rows: np.ndarray, cols: np.ndarray) -> np.ndarray:
+    """The unrounded Box-Muller variates z for entries G[rows, cols] (float64 transform)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    rows, cols = np.broadcast_arrays(rows, cols)
+    seed = int(seed)
+    w = philox4x32_10(rows >> 2, cols, 1, 0, seed & MASK32, (seed >> 32) & MASK32)
+    second_pair = (rows & 2) != 0
+    a = np.where(second_pair, w[2], w[0])
+    b = np.where(second_pair, w[3], w[1])
+    nine = np.uint64(9)
+    u1 = ((a >> nine).astype(np.float64) + 0.5) * 2.0 ** -23
+    u2 = (b >> nine).astype(np.float64) * 2.0 ** -23
+    r = np.sqrt(-2.0 * np.log(u1))
+    theta = 2.0 * np.pi * u2
+    return np.where((rows & 1) == 0, r * np.cos(theta), r * np.sin(theta))
+
+
+def gaussian_ambiguous(seed: int, n: int, l: int, row0: int = 0, col0: int = 0,
+                       nrows: int | None = None, ncols: int | None = None) -> np.ndarray:
+    """Entries whose rounding to the 2^-12 grid a float32 evaluation of the transform may
+    decide the other way: 4096 z within 4096 |z| 2^-20 of a midpoint between grid points.
+    (float32 log, square root, sine/cosine and the product each err by at most about one
+    unit in the last place, 2^-23 relative, so the whole transform stays within
+    2^-21.5 |z|; the window is three times that.)"""
+    nrows = n - row0 if nrows is None else nrows
+    ncols = l - col0 if ncols is None else ncols
+    r = np.arange(row0, row0 + nrows, dtype=np.int64)[:, None]
+    c = np.arange(col0, col0 + ncols, dtype=np.int64)[None, :]
+    t = gaussian_variates(seed, r, c) * GAUSS_GRID
+    dist_to_mid = np.abs(t - (np.floor(t) + 0.5))
+    return dist_to_mid <= np.abs(t) * 2.0 ** -20 + 1e-9
+
+
+def omega(seed: int, n: int, l: int, dist: str = "gaussian", row0: int = 0, col0: int = 0,
           nrows: int | None = None, ncols: int | None = None) -> np.ndarray:
     """The block G[row0:row0+nrows, col0:col0+ncols] of the n x l test matrix (float64)."""
     if dist not in DISTRIBUTIONS:
@@ -104,6 +152,8 @@ def omega(seed: int, n: int, l: int, dist: str = "uniform", row0: int = 0, col0:
     ncols = l - col0 if ncols is None else ncols
     r = np.arange(row0, row0 + nrows, dtype=np.int64)[:, None]
     c = np.arange(col0, col0 + ncols, dtype=np.int64)[None, :]
+    if dist == "gaussian":
+        return np.rint(gaussian_variates(seed, r, c) * GAUSS_GRID) / GAUSS_GRID
     u = omega_bytes(seed, r, c).astype(np.float64)
     if dist == "uniform":
         return (2.0 * u - 255.0) / 256.0

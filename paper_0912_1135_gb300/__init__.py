@@ -5,9 +5,9 @@ Argument marshalling only: every step of the method runs in the CUDA kernels of
 device memory (the caller-owned workspace and outputs) and the CUDA stream. There is
 no CPU fallback: if the library is missing this module raises on first use.
 
-    >>> P = Projector(A)                 # A: cuda float64, m x n, row-major
+    >>> P = Projector(A)                 # A: cuda float64 or float32, m x n, row-major
     >>> P.precondition(seed=1, l=4 * m)  # sketch, pivoted QR, Gram, Cholesky
-    >>> Z = P.null_project(B)            # B: k x n (each row a right-hand side)
+    >>> Z = P.null_project(B)            # B: k x n (each row a right-hand side), A's dtype
 """
 from __future__ import annotations
 
@@ -18,10 +18,12 @@ import torch
 
 from . import _build
 
-__all__ = ["Projector", "RtprojError", "load_library", "library_path", "STATUS", "MODES", "OMEGAS"]
+__all__ = ["Projector", "RtprojError", "load_library", "library_path", "STATUS", "MODES", "OMEGAS",
+           "generate_omega", "launch_count"]
 
 MODES = {"fp64": 0, "mixed": 1}
-OMEGAS = {"uniform": 0, "rademacher": 1}
+OMEGAS = {"uniform": 0, "rademacher": 1, "gaussian": 2}
+DTYPES = {torch.float64: 0, torch.float32: 1}
 STATUS = {
     0: "RTPROJ_OK", 1: "RTPROJ_EINVAL", 2: "RTPROJ_ESTATE", 3: "RTPROJ_ERANK", 4: "RTPROJ_ENOTSPD",
     5: "RTPROJ_ENONFINITE", 6: "RTPROJ_ETIMEOUT", 7: "RTPROJ_ENOMEM", 8: "RTPROJ_ECUDA", 9: "RTPROJ_EUNSUPPORTED",
@@ -39,7 +41,8 @@ class Opts(ctypes.Structure):
         ("mode", ctypes.c_int), ("omega", ctypes.c_int), ("sketch_slices", ctypes.c_int),
         ("gram_slices", ctypes.c_int), ("gram2_slices", ctypes.c_int), ("apply_slices", ctypes.c_int),
         ("resid_slices", ctypes.c_int), ("refine_passes", ctypes.c_int), ("timing", ctypes.c_int),
-        ("rank_tol", ctypes.c_double),
+        ("rank_tol", ctypes.c_double), ("dtype", ctypes.c_int), ("spin_limit_cycles", ctypes.c_longlong),
+        ("refine_tol", ctypes.c_double),
     ]
 
 
@@ -47,7 +50,9 @@ class Info(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("preconditioned", ctypes.c_int), ("m", ctypes.c_int64), ("n", ctypes.c_int64),
         ("l", ctypes.c_int64), ("r11", ctypes.c_double), ("rmm", ctypes.c_double), ("l11", ctypes.c_double),
-        ("lmm", ctypes.c_double), ("ms_precondition", ctypes.c_float),
+        ("lmm", ctypes.c_double), ("ms_precondition", ctypes.c_float), ("kappa_R", ctypes.c_double),
+        ("kappa_pre", ctypes.c_double), ("norm_A", ctypes.c_double), ("resid_rel", ctypes.c_double),
+        ("dh_rel", ctypes.c_double), ("passes", ctypes.c_int),
     ]
 
 
@@ -74,6 +79,8 @@ EXPORTS = {
     "rtproj_get_timings": (ctypes.c_int, [_P, _P, _P]),
     "rtproj_launch_count": (ctypes.c_uint64, []),
     "rtproj_sketch_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, ctypes.c_uint64, _I64, ctypes.c_int, _P, _I64, _P]),
+    "rtproj_generate_omega": (ctypes.c_int, [ctypes.c_uint64, _I64, _I64, ctypes.c_int, _P, _I64, _P]),
+    "rtproj_set_spin_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
 }
 
 PHASES = ["sketch", "qr", "gram", "factor", "apply_a", "apply_m", "apply_at", "slice"]
@@ -111,7 +118,7 @@ def default_opts() -> Opts:
     return o
 
 
-def make_opts(mode="mixed", omega="uniform", **slices) -> Opts:
+def make_opts(mode="mixed", omega="gaussian", **slices) -> Opts:
     o = default_opts()
     o.mode = MODES[mode] if isinstance(mode, str) else int(mode)
     o.omega = OMEGAS[omega] if isinstance(omega, str) else int(omega)
@@ -130,18 +137,22 @@ class Projector:
     """One matrix A bound to a workspace and a stream (see ``include/rtproj.h``)."""
 
     def __init__(self, A: torch.Tensor, l_max: int | None = None, k_max: int = 64, mode: str = "mixed",
-                 omega: str = "uniform", stream: torch.cuda.Stream | None = None, **slices):
+                 omega: str = "gaussian", stream: torch.cuda.Stream | None = None, **slices):
         lib = load_library()
-        if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2 and A.stride(1) == 1):
-            raise TypeError("A must be a CUDA float64 matrix with unit column stride")
+        if not (isinstance(A, torch.Tensor) and A.is_cuda and A.dtype in DTYPES and A.dim() == 2
+                and A.stride(1) == 1 and A.stride(0) >= A.shape[1]):
+            raise TypeError("A must be a CUDA float64 or float32 matrix with unit column stride")
         self.A = A
+        self.dtype = A.dtype
         self.m, self.n = A.shape
         self.lda = A.stride(0)
         self.l_max = int(l_max if l_max is not None else min(self.n, 4 * self.m))
         self.k_max = int(k_max)
         self.device = A.device
         self.opts = make_opts(mode, omega, **slices)
+        self.opts.dtype = DTYPES[A.dtype]
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._enter(A)   # create reads A on the handle's stream
         nbytes = lib.rtproj_workspace_bytes(self.m, self.n, self.l_max, self.k_max, ctypes.byref(self.opts))
         if nbytes == 0:
             raise RtprojError(1, "rtproj_workspace_bytes")
@@ -178,16 +189,19 @@ class Projector:
     # -- preconditioner ----------------------------------------------------------------
     def precondition(self, seed: int, l: int | None = None):
         l = self.l_max if l is None else int(l)
+        self._enter()
         with torch.cuda.device(self.device):
             _check(load_library().rtproj_precondition(self._h, ctypes.c_uint64(seed), l), "rtproj_precondition")
         self.l = l
         return self
 
     def sketch(self, seed: int, l: int) -> torch.Tensor:
+        cur = self._enter()
         with torch.cuda.stream(self.stream):
             S = torch.empty((self.m, l), dtype=torch.float64, device=self.device)
         with torch.cuda.device(self.device):
             _check(load_library().rtproj_sketch(self._h, ctypes.c_uint64(seed), l, _dev_ptr(S), l), "rtproj_sketch")
+        self._leave(cur, S)
         return S
 
     def export_state(self):
@@ -216,27 +230,67 @@ class Projector:
     def clear_status(self):
         _check(load_library().rtproj_clear_status(self._h), "rtproj_clear_status")
 
+    def set_spin_limit(self, cycles: int):
+        """Bound (SM clock cycles) on each grid-exchange wait of the QR and the Cholesky."""
+        _check(load_library().rtproj_set_spin_limit(self._h, ctypes.c_longlong(int(cycles))), "rtproj_set_spin_limit")
+
     # -- apply -----------------------------------------------------------------------
     def _rhs(self, B: torch.Tensor) -> torch.Tensor:
-        if not (B.is_cuda and B.dtype == torch.float64 and B.stride(-1) == 1):
-            raise TypeError("B must be a CUDA float64 tensor with unit last stride")
-        return B if B.dim() == 2 else B.reshape(1, -1)
+        if not (isinstance(B, torch.Tensor) and B.dtype == self.dtype and B.device == self.device):
+            raise TypeError(f"B must be a {self.dtype} tensor on {self.device}")
+        if B.dim() == 1:
+            B = B.reshape(1, -1)
+        if B.dim() != 2 or B.shape[1] != self.n or B.stride(1) != 1 or B.stride(0) < self.n:
+            raise TypeError(f"B must be k x {self.n} with unit column stride (one right-hand side per row)")
+        if not (1 <= B.shape[0] <= self.k_max):
+            raise TypeError(f"B has {B.shape[0]} rows; this handle takes 1..{self.k_max}")
+        return B
+
+    def _out(self, out: torch.Tensor, k: int, cols: int, name: str):
+        if not (isinstance(out, torch.Tensor) and out.dtype == self.dtype and out.device == self.device
+                and out.dim() == 2 and tuple(out.shape) == (k, cols) and out.stride(1) == 1 and out.stride(0) >= cols):
+            raise TypeError(f"{name} must be a {k} x {cols} {self.dtype} tensor on {self.device} with unit column stride")
+        return out
+
+    def _enter(self, *inputs):
+        """Orders the handle's stream after the caller's current stream (which produced the
+        inputs) and keeps the inputs' memory from being reused before the handle's stream has
+        read them."""
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+            for t in inputs:
+                t.record_stream(self.stream)
+        return cur
+
+    def _leave(self, cur, *outputs):
+        """Orders the caller's current stream after the handle's stream (which wrote the
+        outputs), so the outputs can be read on either."""
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
+            for t in outputs:
+                if t is not None:
+                    t.record_stream(cur)
 
     def project(self, B: torch.Tensor, null: bool = True, row: bool = False, lstsq: bool = False,
                 out_null: torch.Tensor | None = None):
         B = self._rhs(B)
         k = B.shape[0]
+        if out_null is not None:
+            self._out(out_null, k, self.n, "out_null")
+        cur = self._enter(B)
         with torch.cuda.stream(self.stream):   # outputs belong to the handle's stream
-            Z = (out_null if out_null is not None else torch.empty((k, self.n), dtype=torch.float64,
+            Z = (out_null if out_null is not None else torch.empty((k, self.n), dtype=self.dtype,
                                                                    device=self.device)) if null else None
-            ROW = torch.empty((k, self.n), dtype=torch.float64, device=self.device) if row else None
-            X = torch.empty((k, self.m), dtype=torch.float64, device=self.device) if lstsq else None
+            ROW = torch.empty((k, self.n), dtype=self.dtype, device=self.device) if row else None
+            X = torch.empty((k, self.m), dtype=self.dtype, device=self.device) if lstsq else None
         ptr = lambda t: _dev_ptr(t) if t is not None else None
         ld = lambda t: t.stride(0) if t is not None else 0
         with torch.cuda.device(self.device):
             code = load_library().rtproj_project(self._h, _dev_ptr(B), B.stride(0), k, ptr(Z), ld(Z), ptr(ROW), ld(ROW),
                                                  ptr(X), ld(X))
         _check(code, "rtproj_project")
+        self._leave(cur, Z, ROW, X)
         return Z, ROW, X
 
     def null_project(self, B, out=None):
@@ -252,6 +306,19 @@ class Projector:
 def launch_count() -> int:
     """Kernels enqueued by librtproj since it was loaded."""
     return int(load_library().rtproj_launch_count())
+
+
+def generate_omega(seed: int, n: int, l: int, omega: str = "gaussian", device="cuda") -> torch.Tensor:
+    """The n x l test matrix G of Eq. 12 (float64), generated on the device as the sketch
+    generates it (the sketch itself never stores G)."""
+    dev = torch.device(device)
+    G = torch.empty((n, l), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    with torch.cuda.device(dev):
+        code = load_library().rtproj_generate_omega(ctypes.c_uint64(seed), n, l, OMEGAS[omega], _dev_ptr(G), l,
+                                                    ctypes.c_void_p(stream.cuda_stream))
+    _check(code, "rtproj_generate_omega")
+    return G
 
 
 def project_from_host(A_host: torch.Tensor, B_host: torch.Tensor, seed: int, l: int, device="cuda", **kw):

@@ -62,7 +62,22 @@ __global__ void __launch_bounds__(NT) gemm64_kernel(Gemm64Dev p) {
             }
             As[kk][ii] = v;
         }
-        if (p.omega_dist >= 0) {
+        if (p.omega_dist == RTPROJ_OMEGA_GAUSSIAN) {
+            // k0 is a multiple of 16: four Philox blocks give the 16 rows of column j.
+            if (t < BN) {
+                const int gj = j0 + t;
+#pragma unroll
+                for (int qd = 0; qd < BK / 4; ++qd) {
+                    int N[4] = {0, 0, 0, 0};
+                    if (gj < p.N) gauss_quad((uint32_t)((k0 >> 2) + qd), (uint32_t)gj, p.key0, p.key1, N);
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const int kk = 4 * qd + b;
+                        Bs[kk][t] = (gj < p.N && k0 + kk < kend) ? (double)N[b] * (1.0 / 4096.0) : 0.0;
+                    }
+                }
+            }
+        } else if (p.omega_dist >= 0) {
             // k0 is a multiple of 16: one Philox block covers the 16 rows of column j.
             if (t < BN) {
                 const int gj = j0 + t;
@@ -188,7 +203,7 @@ cudaError_t gemm64(const Gemm64& g, double* part, size_t part_elems, cudaStream_
     int splits = 1;
     if (g.K > 0) {
         const int tiles = tiles_m * tiles_n;
-        const int want = std::max(1, (4 * 152 + tiles - 1) / tiles);
+        const int want = std::max(1, (4 * sm_count() + tiles - 1) / tiles);
         // Few output tiles (the m x m by m x k products of the apply): splits down to one
         // 16-k step, so that the small FP64 products use every SM; otherwise at least four.
         const int maxk = tiles < 32 ? std::max(1, (g.K + BK - 1) / BK) : std::max(1, (g.K + 63) / 64);

@@ -24,6 +24,7 @@
 #include "rtproj_internal.cuh"
 
 #include <algorithm>
+#include <cstring>
 
 namespace rtp {
 namespace {
@@ -52,7 +53,7 @@ MixedLayout mixed_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, con
     L.eA = take((size_t)m * 4);
     L.AT = take((size_t)sa * n * ldm * 2);
     L.eAT = take((size_t)n * 4);
-    L.G = take((size_t)l_max * ldn * 2);
+    L.G = take((size_t)omega_planes(o.omega) * l_max * ldn * 2);
     L.eG = take((size_t)l_max * 4);
     L.Mp = take((size_t)m * m * 8);
     L.Ms = take((size_t)o.gram_slices * m * ldm * 2);
@@ -124,16 +125,6 @@ __global__ void axpy_kernel(double* y, const double* x, int64_t n) {
     if (idx < n) y[idx] += x[idx];
 }
 
-// OUT[r][c] = X[r][c] (sub = 0) or B[r][c] - X[r][c] (sub = 1), rows x cols.
-__global__ void rows_op_kernel(const double* X, int64_t ldx, const double* B, int64_t ldb, double* OUT, int64_t ldo,
-                               int rows, int cols, int sub) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)rows * cols) return;
-    const int r = (int)(idx / cols), c = (int)(idx % cols);
-    const double x = X[(int64_t)r * ldx + c];
-    OUT[(int64_t)r * ldo + c] = sub ? B[(int64_t)r * ldb + c] - x : x;
-}
-
 #define MX_CHECK(expr)                              \
     do {                                            \
         cudaError_t e_ = (expr);                    \
@@ -170,7 +161,7 @@ rtproj_status mixed_bind(rtproj_ctx* h, char* base, size_t bytes) {
     const int sa = s_all(o);
     h->As = stack(base, L.A, L.eA, m, n, sa, ldn);
     h->Ats = stack(base, L.AT, L.eAT, n, m, sa, ldm);
-    h->Gs = stack(base, L.G, L.eG, (int)h->l_max, n, 1, ldn);
+    h->Gs = stack(base, L.G, L.eG, (int)h->l_max, n, omega_planes(o.omega), ldn);
     h->Mprime = (double*)(base + L.Mp);
     h->Ms = stack(base, L.Ms, L.eM, m, m, o.gram_slices, ldm);
     h->Ws = stack(base, L.W, L.eW, m, n, o.gram2_slices, ldn);
@@ -197,8 +188,9 @@ rtproj_status mixed_prepare_a(rtproj_ctx* h) {
 }
 
 rtproj_status mixed_sketch(rtproj_ctx* h, uint64_t seed, int64_t l, double* S, int64_t lds) {
-    SliceStack G = rows_of(h->Gs, (int)l, 1);
-    G.max_digit = h->opts.omega == RTPROJ_OMEGA_RADEMACHER ? 1 : 255;
+    const int w = h->opts.omega;
+    SliceStack G = rows_of(h->Gs, (int)l, omega_planes(w));
+    G.max_digit = w == RTPROJ_OMEGA_RADEMACHER ? 1 : w == RTPROJ_OMEGA_GAUSSIAN ? 128 : 255;
     MX_CHECK(omega_plane(seed, h->opts.omega, (int)h->n, (int)l, G, h->stream));
     return gemm(h, first(h->As, h->opts.sketch_slices), G, h->opts.sketch_slices, S, lds, 1);
 }
@@ -253,12 +245,15 @@ rtproj_status middle_mixed(rtproj_ctx* h, const double* c, double* out, int k) {
 
 }  // namespace
 
-rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, double* Z, int64_t ldz, double* ROW,
-                            int64_t ldr, double* X, int64_t ldx) {
+rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, void* Z, int64_t ldz, void* ROW,
+                            int64_t ldr, void* X, int64_t ldx) {
     const rtproj_opts& o = h->opts;
     const int m = (int)h->m, n = (int)h->n;
     cudaStream_t s = h->stream;
     rtproj_status st;
+    // residual report: ||b_j|| once per apply, the maxima cleared
+    MX_CHECK(row_norms(B, ldb, k, n, h->bnorm, s));
+    MX_CHECK(cudaMemsetAsync(h->stats, 0, 16, s));
     // c = A b
     phase_begin(h, RTPROJ_PHASE_SLICE);
     const SliceStack Bk = rows_of(h->Bs, k, o.apply_slices);
@@ -282,9 +277,11 @@ rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, 
     st = gemm(h, first(h->Ats, o.resid_slices), Hr, o.resid_slices, h->sbuf, 1, n, -1.0, 1.0, B, 1, ldb);
     if (st != RTPROJ_OK) return st;
     phase_end(h, RTPROJ_PHASE_APPLY_AT);
-    const bool direct_z = Z && !ROW;
+    // the last pass may write Z directly when it is the only output and float64
+    const bool direct_z = Z && !ROW && h->dtype == RTPROJ_F64;
+    bool z_written = false;
+    int passes = 0;
     for (int pass = 0; pass < o.refine_passes; ++pass) {
-        const bool last = pass + 1 == o.refine_passes;
         // r = A s
         phase_begin(h, RTPROJ_PHASE_SLICE);
         const SliceStack Sk = rows_of(h->Ss, k, o.resid_slices);
@@ -301,31 +298,43 @@ rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, 
         const int64_t mk = (int64_t)m * k;
         axpy_kernel<<<(unsigned)((mk + 255) / 256), 256, 0, s>>>(h->hbuf, h->dhbuf, mk);
         note_launch();
+        // the pass's report: ||r_j|| = ||A s_j|| and ||dh_j|| / ||h_j||
+        MX_CHECK(cudaMemsetAsync(h->stats, 0, 16, s));
+        MX_CHECK(column_stats(h->cbuf, h->hbuf, h->dhbuf, m, k, h->bnorm, h->normA, h->stats, s));
         phase_end(h, RTPROJ_PHASE_APPLY_M);
+        passes = pass + 1;
+        bool last = passes == o.refine_passes;
+        if (o.refine_tol > 0.0 && !last) {
+            // Remark 4.3, to convergence: stop once every correction is below the tolerance
+            unsigned long long bits[2];
+            MX_CHECK(cudaMemcpyAsync(bits, h->stats, 16, cudaMemcpyDeviceToHost, s));
+            MX_CHECK(cudaStreamSynchronize(s));
+            double v[2];
+            memcpy(v, bits, 16);
+            if (v[1] <= o.refine_tol) last = true;
+        }
         // s = s - A^* dh
         phase_begin(h, RTPROJ_PHASE_SLICE);
         const SliceStack Hd = rows_of(h->Hs, k, o.apply_slices);
         MX_CHECK(slice_rows(h->dhbuf, 1, k, nullptr, h->As.e, Hd, h->status, s));
         phase_end(h, RTPROJ_PHASE_SLICE);
         phase_begin(h, RTPROJ_PHASE_APPLY_AT);
-        if (last && direct_z)
-            st = gemm(h, first(h->Ats, o.apply_slices), Hd, o.apply_slices, Z, 1, ldz, -1.0, 1.0, h->sbuf, 1, n);
-        else
+        if (last && direct_z) {
+            st = gemm(h, first(h->Ats, o.apply_slices), Hd, o.apply_slices, (double*)Z, 1, ldz, -1.0, 1.0, h->sbuf, 1,
+                      n);
+            z_written = true;
+        } else {
             st = gemm(h, first(h->Ats, o.apply_slices), Hd, o.apply_slices, h->sbuf, 1, n, -1.0, 1.0, h->sbuf, 1, n);
+        }
         if (st != RTPROJ_OK) return st;
         phase_end(h, RTPROJ_PHASE_APPLY_AT);
+        if (last) break;
     }
-    const int64_t kn = (int64_t)k * n;
-    const bool z_in_sbuf = !(direct_z && o.refine_passes > 0);
-    if (ROW) {
-        rows_op_kernel<<<(unsigned)((kn + 255) / 256), 256, 0, s>>>(h->sbuf, n, B, ldb, ROW, ldr, k, n, 1);
-        note_launch();
-    }
-    if (Z && z_in_sbuf) {
-        rows_op_kernel<<<(unsigned)((kn + 255) / 256), 256, 0, s>>>(h->sbuf, n, nullptr, 0, Z, ldz, k, n, 0);
-        note_launch();
-    }
-    if (X) MX_CHECK(transpose_copy(h->hbuf, k, X, ldx, m, k, s));
+    h->last_passes = passes;
+    // outputs in the caller's element type; ROW before Z, since Z may alias B
+    if (ROW) MX_CHECK(store_rows(h->sbuf, n, B, ldb, ROW, ldr, k, n, 1, h->dtype, s));
+    if (Z && !z_written) MX_CHECK(store_rows(h->sbuf, n, nullptr, 0, Z, ldz, k, n, 0, h->dtype, s));
+    if (X) MX_CHECK(store_transposed(h->hbuf, k, m, k, X, ldx, h->dtype, s));
     MX_CHECK(cudaGetLastError());
     return RTPROJ_OK;
 }

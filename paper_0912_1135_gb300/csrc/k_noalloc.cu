@@ -115,12 +115,17 @@ extern "C" rtproj_status rtproj_sketch_noalloc(const double* A, int64_t m, int64
     if (n > (int64_t)1 << 30) return RTPROJ_EUNSUPPORTED;
     const int64_t slab = m * l;
     if (slab > kScratchDoubles) return RTPROJ_ENOMEM;    // one partial slab must fit the fixed array
+    // the array's address is per device: the stream must run on the current device
+    int cur = 0, sdev = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return RTPROJ_ECUDA;
+    if (cudaStreamGetDevice((cudaStream_t)stream, &sdev) != cudaSuccess) return RTPROJ_EINVAL;
+    if (sdev != cur) return RTPROJ_EINVAL;
     double* part = nullptr;
     const rtproj_status st = scratch_on_current_device(&part);
     if (st != RTPROJ_OK) return st;
     const int tiles_m = (int)((m + NB_M - 1) / NB_M), tiles_n = (int)((l + NB_N - 1) / NB_N);
     const int tiles = tiles_m * tiles_n;
-    int64_t splits = std::max<int64_t>(1, (4 * 152 + tiles - 1) / tiles);
+    int64_t splits = std::max<int64_t>(1, (4 * (int64_t)rtp::sm_count() + tiles - 1) / tiles);
     splits = std::min<int64_t>(splits, std::max<int64_t>(1, (n + 255) / 256));
     splits = std::min<int64_t>(splits, kScratchDoubles / slab);
     int64_t kps = (n + splits - 1) / splits;

@@ -206,19 +206,18 @@ __device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v)
 }
 
 // Bounded wait until *p >= target (or the abort flag is raised). Returns false on abort.
-// The counter is polled back to back; the abort flag and the deadline every 64 polls.
+// The counter is polled back to back with the deadline checked after every failed poll;
+// the abort flag every 64 polls.
 __device__ bool wait_geq(const unsigned int* p, unsigned int target, int* abort_flag, int* status, long long timeout) {
     const long long t0 = clock64();
     for (unsigned int it = 1;; ++it) {
         if (ld_acquire(p) >= target) return true;
-        if ((it & 63) == 0) {
-            if (*(volatile int*)abort_flag) return false;
-            if (clock64() - t0 > timeout) {
-                atomicExch(abort_flag, 1);
-                set_status(status, RTPROJ_ETIMEOUT);
-                return false;
-            }
+        if (clock64() - t0 > timeout) {
+            atomicExch(abort_flag, 1);
+            set_status(status, RTPROJ_ETIMEOUT);
+            return false;
         }
+        if ((it & 63) == 0 && *(volatile int*)abort_flag) return false;
     }
 }
 
@@ -429,8 +428,43 @@ size_t pivoted_qr_work_doubles(int m, int l) {
     return steps > persistent ? steps : persistent;
 }
 
+// One CTA: perm must hold every index 0..m-1 once (m <= 4096: a bitmap in shared
+// memory); otherwise the identity replaces it. Then the rank test on |R_mm| / |R_11|.
+__global__ void __launch_bounds__(1024) qr_check_kernel(const double* R, int32_t* perm, int m, double tol, int* status) {
+    __shared__ unsigned int seen[128];
+    __shared__ int bad;
+    const int t = threadIdx.x;
+    if (t < 128) seen[t] = 0u;
+    if (t == 0) bad = 0;
+    __syncthreads();
+    for (int j = t; j < m; j += blockDim.x) {
+        const int v = perm[j];
+        if (v < 0 || v >= m) bad = 1;
+        else if (atomicOr(&seen[v >> 5], 1u << (v & 31)) & (1u << (v & 31))) bad = 1;
+    }
+    __syncthreads();
+    if (bad) {
+        for (int j = t; j < m; j += blockDim.x) perm[j] = j;
+        if (t == 0) set_status(status, RTPROJ_ETIMEOUT);   // only a QR that gave up leaves perm incomplete
+        return;
+    }
+    if (t == 0) {
+        const double r11 = fabs(R[0]);
+        const double rmm = fabs(R[(int64_t)(m - 1) * m + (m - 1)]);
+        if (!isfinite(r11) || !isfinite(rmm)) set_status(status, RTPROJ_ENONFINITE);
+        else if (!(rmm > tol * r11)) set_status(status, RTPROJ_ERANK);
+    }
+}
+
+cudaError_t qr_check(const double* R, int32_t* perm, int m, double tol, int* status, cudaStream_t s) {
+    if (m > 4096) return cudaErrorInvalidValue;
+    qr_check_kernel<<<1, 1024, 0, s>>>(R, perm, m, tol, status);
+    note_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
-                       double* work, int* status, cudaStream_t s) {
+                       double* work, int* status, cudaStream_t s, long long spin_limit) {
     // Persistent cooperative form when the columns fit in shared memory.
     int dev = 0, sms = 0, coop = 0, smem_optin = 0;
     cudaGetDevice(&dev);
@@ -456,7 +490,7 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 p.counter = ctr;
                 p.abort_flag = (int*)(ctr + 1);
                 p.status = status;
-                p.timeout = 4000000000ll;
+                p.timeout = spin_limit;
                 cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
                 if (e != cudaSuccess) return e;
                 void* args[] = {&p};

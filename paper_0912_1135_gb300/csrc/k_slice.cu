@@ -158,24 +158,71 @@ __global__ void __launch_bounds__(256) transpose_planes_kernel(const __nv_bfloat
 // G^* (l x n) as one digit plane: row j, column i holds the digit of G(i, j).
 // uniform: d = 2u - 255 (exponent -1, value d / 256); rademacher: d = +-1 (exponent 7).
 __global__ void omega_plane_kernel(uint32_t key0, uint32_t key1, int dist, int n, int l, __nv_bfloat16* d,
-                                   int64_t ld) {
+                                   int64_t ld, int64_t ps) {
     const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t blocks_per_row = ld / 16;
     if (gid >= blocks_per_row * l) return;
     const int j = (int)(gid / blocks_per_row);
     const int i0 = (int)(gid % blocks_per_row) * 16;
-    const uint4 w = philox4x32_10(make_uint4((uint32_t)(i0 >> 4), (uint32_t)j, 0u, 0u), key0, key1);
     alignas(16) __nv_bfloat16 out[16];
+    if (dist == RTPROJ_OMEGA_GAUSSIAN) {
+        // N = 4096 G = 256 d0 + d1 with d1 in [-128, 127]: two exact digit planes
+        // (exponent 3: G = 2^3 (d0 2^-7 + d1 2^-15))
+        alignas(16) __nv_bfloat16 lo[16];
 #pragma unroll
-    for (int b = 0; b < 16; ++b) {
-        const uint32_t u = block_byte(w, b);
-        int dv = dist == RTPROJ_OMEGA_RADEMACHER ? (u >= 128u ? 1 : -1) : (2 * (int)u - 255);
-        if (i0 + b >= n) dv = 0;
-        out[b] = __int2bfloat16_rn(dv);
+        for (int qd = 0; qd < 4; ++qd) {
+            int N[4];
+            gauss_quad((uint32_t)((i0 >> 2) + qd), (uint32_t)j, key0, key1, N);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int v = (i0 + 4 * qd + b < n) ? N[b] : 0;
+                const int d0 = (v + 128) >> 8;          // floor((v + 128) / 256)
+                out[4 * qd + b] = __int2bfloat16_rn(d0);
+                lo[4 * qd + b] = __int2bfloat16_rn(v - 256 * d0);
+            }
+        }
+        uint4* dst1 = reinterpret_cast<uint4*>(d + ps + (int64_t)j * ld + i0);
+        dst1[0] = reinterpret_cast<const uint4*>(lo)[0];
+        dst1[1] = reinterpret_cast<const uint4*>(lo)[1];
+    } else {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(i0 >> 4), (uint32_t)j, 0u, 0u), key0, key1);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            const uint32_t u = block_byte(w, b);
+            int dv = dist == RTPROJ_OMEGA_RADEMACHER ? (u >= 128u ? 1 : -1) : (2 * (int)u - 255);
+            if (i0 + b >= n) dv = 0;
+            out[b] = __int2bfloat16_rn(dv);
+        }
     }
     uint4* dst = reinterpret_cast<uint4*>(d + (int64_t)j * ld + i0);
     dst[0] = reinterpret_cast<const uint4*>(out)[0];
     dst[1] = reinterpret_cast<const uint4*>(out)[1];
+}
+
+// G itself (n x l, float64, row-major): one thread per 16 rows of one column.
+__global__ void omega_dense_kernel(uint32_t key0, uint32_t key1, int dist, int n, int l, double* G, int64_t ldg) {
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t blocks_per_col = (n + 15) / 16;
+    if (gid >= blocks_per_col * l) return;
+    const int j = (int)(gid % l);
+    const int i0 = (int)(gid / l) * 16;
+    double v[16];
+    if (dist == RTPROJ_OMEGA_GAUSSIAN) {
+#pragma unroll
+        for (int qd = 0; qd < 4; ++qd) {
+            int N[4];
+            gauss_quad((uint32_t)((i0 >> 2) + qd), (uint32_t)j, key0, key1, N);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) v[4 * qd + b] = (double)N[b] * (1.0 / 4096.0);
+        }
+    } else {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(i0 >> 4), (uint32_t)j, 0u, 0u), key0, key1);
+#pragma unroll
+        for (int b = 0; b < 16; ++b) v[b] = (double)omega_from_byte(block_byte(w, b), dist);
+    }
+#pragma unroll
+    for (int b = 0; b < 16; ++b)
+        if (i0 + b < n) G[(int64_t)(i0 + b) * ldg + j] = v[b];
 }
 
 __global__ void fill_int_kernel(int32_t* e, int n, int v) {
@@ -431,7 +478,7 @@ cudaError_t slice_rows(const double* X, int64_t x_rs, int64_t x_cs, const int32_
     // 16-byte vector stores need 8-entry aligned planes and rows
     const bool fast = x_cs == 1 && !rowidx && !cexp && st.ld % 8 == 0 && st.plane_stride % 8 == 0 &&
                       ((uintptr_t)st.d & 15) == 0 && ((uintptr_t)X & 7) == 0;
-    if (fast && st.rows < 2 * 152) {
+    if (fast && st.rows < 2 * sm_count()) {
         // few rows: spread every row over several CTAs
         const cudaError_t fe = fill_int(st.e, st.rows, SLF_ZERO_ROW, s);
         if (fe != cudaSuccess) return fe;
@@ -569,12 +616,23 @@ cudaError_t transpose_planes(const SliceStack& src, const SliceStack& dst, cudaS
 }
 
 cudaError_t omega_plane(uint64_t seed, int dist, int n, int l, const SliceStack& st, cudaStream_t s) {
-    if (st.ld % 16 || st.ld < n) return cudaErrorInvalidValue;
+    if (st.ld % 16 || st.ld < n || st.s < omega_planes(dist)) return cudaErrorInvalidValue;
     const int64_t total = (st.ld / 16) * (int64_t)l;
     omega_plane_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((uint32_t)(seed & 0xFFFFFFFFull),
-                                                                       (uint32_t)(seed >> 32), dist, n, l, st.d, st.ld);
+                                                                       (uint32_t)(seed >> 32), dist, n, l, st.d, st.ld,
+                                                                       st.plane_stride);
     note_launch();
-    fill_int_kernel<<<(l + 255) / 256, 256, 0, s>>>(st.e, l, dist == RTPROJ_OMEGA_RADEMACHER ? 7 : -1);
+    const int e = dist == RTPROJ_OMEGA_RADEMACHER ? 7 : dist == RTPROJ_OMEGA_GAUSSIAN ? 3 : -1;
+    fill_int_kernel<<<(l + 255) / 256, 256, 0, s>>>(st.e, l, e);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t omega_dense(uint64_t seed, int dist, int n, int l, double* G, int64_t ldg, cudaStream_t s) {
+    const int64_t total = (int64_t)((n + 15) / 16) * l;
+    if (total <= 0) return cudaSuccess;
+    omega_dense_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>((uint32_t)(seed & 0xFFFFFFFFull),
+                                                                       (uint32_t)(seed >> 32), dist, n, l, G, ldg);
     note_launch();
     return cudaGetLastError();
 }

@@ -323,15 +323,13 @@ __device__ bool chp_grid_sync(const CholPDev& p, unsigned int k, int* ok_s) {
         int ok = 1;
         for (unsigned int it = 1;; ++it) {
             if (chp_ld_acquire(p.counter) >= target) break;
-            if ((it & 63) == 0) {
-                if (*(volatile int*)p.abort_flag) { ok = 0; break; }
-                if (clock64() - t0 > p.timeout) {
-                    atomicExch(p.abort_flag, 1);
-                    set_status(p.status, RTPROJ_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
+            if (clock64() - t0 > p.timeout) {
+                atomicExch(p.abort_flag, 1);
+                set_status(p.status, RTPROJ_ETIMEOUT);
+                ok = 0;
+                break;
             }
+            if ((it & 63) == 0 && *(volatile int*)p.abort_flag) { ok = 0; break; }
         }
         *ok_s = ok;
     }
@@ -548,7 +546,8 @@ cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
 // the diagonal-block inverses, then one word for the column counter
 size_t trsm_work_doubles(int m) { return (size_t)((m + TRSM_BS - 1) / TRSM_BS) * TRSM_BS * TRSM_BS + 2; }
 
-cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s) {
+cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s,
+                     long long spin_limit) {
     // Persistent cooperative form; the per-panel launches below when it cannot run.
     int dev = 0, sms = 0, coop = 0;
     cudaGetDevice(&dev);
@@ -563,7 +562,7 @@ cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* sta
             p.counter = (unsigned int*)(part + CHP_NB * CHP_NB);
             p.abort_flag = (int*)(p.counter + 1);
             p.status = status;
-            p.timeout = 4000000000ll;
+            p.timeout = spin_limit;
             cudaError_t e = cudaMemsetAsync(p.counter, 0, 2 * sizeof(unsigned int), s);
             if (e != cudaSuccess) return e;
             void* args[] = {&p};

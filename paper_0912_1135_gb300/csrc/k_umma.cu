@@ -1173,7 +1173,7 @@ bool pipelined_disabled() {
 size_t sliced_gemm_scratch_bytes(int M, int N, int K) {
     (void)K;
     const size_t tiles = (size_t)((M + TM - 1) / TM) * ((N + TN - 1) / TN);
-    const size_t target = 2 * 152;
+    const size_t target = 2 * (size_t)sm_count();
     if (tiles >= target) return 0;
     const size_t splits = (target + tiles - 1) / tiles;
     return splits * (size_t)M * N * 16;
@@ -1193,7 +1193,8 @@ static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t s
     const int kchunk = chunk_for(g);
     int splits = 1;
     const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
-    if (tiles < 2 * 152) splits = std::min(max_splits, (2 * 152 + tiles - 1) / tiles);
+    const int sms = sm_count();
+    if (tiles < 2 * sms) splits = std::min(max_splits, (2 * sms + tiles - 1) / tiles);
     while (splits > 1 && (size_t)splits * M * N * 16 > scratch_bytes) --splits;
     int kps = (Kp + splits - 1) / splits;
     kps = (kps + kchunk - 1) / kchunk * kchunk;
@@ -1245,13 +1246,13 @@ static int chunk_for(const SlicedGemm& g) {
     return kc;
 }
 
-// Split-K factor for a persistent grid of 152 CTAs: the number of rounds of work units
+// Split-K factor for a persistent grid of one CTA per SM: the number of rounds of work units
 // (tiles x splits) times the K blocks of one unit, plus a fixed cost per round (pipeline
 // fill and output) and per split (the partial sums written and reduced), both counted in
 // K blocks of 64; the lowest cost wins, fewer splits on ties. A split count just past a
-// multiple of 152 units would add a nearly empty round.
+// multiple of the SM count would add a nearly empty round.
 static int choose_splits(int tiles, int M, int N, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
-    constexpr int kSMs = 152;
+    const int kSMs = sm_count();
     const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
     const double per_split = (double)M * N * 32.0 / (7.0e12 / 1.0e6);   // partials: microseconds
     int best = 1, best_kps = (Kp + kchunk - 1) / kchunk * kchunk;

@@ -18,6 +18,21 @@ std::atomic<uint64_t> g_launches{0};
 
 void rtp::note_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
+int rtp::sm_count() {
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < kMaxDev) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+    if (dev < kMaxDev) cache[dev].store(sms, std::memory_order_relaxed);
+    return sms;
+}
+
 namespace {
 
 void timer_flush(PhaseTimer& t) {
@@ -61,20 +76,28 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
     size_t status, S, qr_work, perm, R, RinvT, Lc, Lt, T1, dinv, W, part, cbuf, ebuf, hbuf, dhbuf, sbuf;
+    size_t A64, B64, normA, norm_part, bnorm, stats;
     size_t mixed_base, mixed_bytes;
     size_t total;
 };
 
 size_t mixed_workspace(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts& o);
 
+bool valid_omega(int w) {
+    return w == RTPROJ_OMEGA_UNIFORM || w == RTPROJ_OMEGA_RADEMACHER || w == RTPROJ_OMEGA_GAUSSIAN;
+}
+
 bool valid_opts(const rtproj_opts& o) {
     if (o.mode != RTPROJ_PLAIN_FP64 && o.mode != RTPROJ_MIXED_REFINED) return false;
-    if (o.omega != RTPROJ_OMEGA_UNIFORM && o.omega != RTPROJ_OMEGA_RADEMACHER) return false;
+    if (!valid_omega(o.omega)) return false;
     auto ok = [](int s) { return s >= 1 && s <= 10; };
     if (!ok(o.sketch_slices) || !ok(o.gram_slices) || !ok(o.gram2_slices) || !ok(o.apply_slices) ||
         !ok(o.resid_slices))
         return false;
-    if (o.refine_passes < 0 || o.refine_passes > 4) return false;
+    if (o.refine_passes < 0 || o.refine_passes > 8) return false;
+    if (o.dtype != RTPROJ_F64 && o.dtype != RTPROJ_F32) return false;
+    if (o.spin_limit_cycles < 1) return false;
+    if (!(o.refine_tol >= 0.0)) return false;
     return true;
 }
 
@@ -99,6 +122,15 @@ Layout make_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtp
     L.hbuf = take((size_t)m * k_max * 8);
     L.dhbuf = take((size_t)m * k_max * 8);
     L.sbuf = take((size_t)k_max * n * 8);
+    // float32 at the ABI: A widened for the float64 form (the mixed form widens into W,
+    // which it needs only after A has been sliced), right-hand sides widened per apply
+    const bool f32 = o.dtype == RTPROJ_F32;
+    L.A64 = take(f32 && o.mode == RTPROJ_PLAIN_FP64 ? (size_t)m * n * 8 : 0);
+    L.B64 = take(f32 ? (size_t)k_max * n * 8 : 0);
+    L.normA = take(8);
+    L.norm_part = take((size_t)norm_parts() * 8);
+    L.bnorm = take((size_t)k_max * 8);
+    L.stats = take(16);
     L.mixed_bytes = o.mode == RTPROJ_MIXED_REFINED ? mixed_workspace(m, n, l_max, k_max, o) : 0;
     L.mixed_base = take(L.mixed_bytes);
     L.total = off;
@@ -112,13 +144,6 @@ rtproj_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RTPROJ_OK :
         cudaError_t e_ = (expr);                        \
         if (e_ != cudaSuccess) return RTPROJ_ECUDA;     \
     } while (0)
-
-__global__ void rank_check_kernel(const double* R, int m, double tol, int* status) {
-    const double r11 = fabs(R[0]);
-    const double rmm = fabs(R[(int64_t)(m - 1) * m + (m - 1)]);
-    if (!isfinite(r11) || !isfinite(rmm)) set_status(status, RTPROJ_ENONFINITE);
-    else if (!(rmm > tol * r11)) set_status(status, RTPROJ_ERANK);
-}
 
 // ---------------------------------------------------------------------------------
 // Plain float64 form.
@@ -174,9 +199,15 @@ rtproj_status rtp::middle_fp64(rtproj_ctx* h, const double* c, double* out, int 
 
 namespace {
 
-rtproj_status project_fp64(rtproj_ctx* h, const double* B, int64_t ldb, int k, double* Z, int64_t ldz,
-                           double* ROW, int64_t ldr, double* X, int64_t ldx) {
+rtproj_status project_fp64(rtproj_ctx* h, const double* B, int64_t ldb, int k, void* Zv, int64_t ldz,
+                           void* ROWv, int64_t ldr, void* Xv, int64_t ldx) {
+    // float32 outputs: the row-space projection is formed in float64 (sbuf) and both
+    // outputs are stored from it; float64 outputs are written by the products directly
+    const bool f32 = h->dtype == RTPROJ_F32;
     const int m = (int)h->m, n = (int)h->n;
+    double* Z = f32 ? nullptr : (double*)Zv;
+    double* ROW = f32 ? ((Zv || ROWv) ? h->sbuf : nullptr) : (double*)ROWv;
+    const int64_t ld_row = f32 ? (int64_t)n : ldr;
     Gemm64 c;                                            // step 1: c = A b
     c.M = m; c.N = k; c.K = n;
     c.A = h->A; c.a_rs = h->lda; c.a_cs = 1;
@@ -204,11 +235,16 @@ rtproj_status project_fp64(rtproj_ctx* h, const double* B, int64_t ldb, int k, d
         r.M = k; r.N = n; r.K = m;
         r.A = h->hbuf; r.a_rs = 1; r.a_cs = k;
         r.B = h->A; r.b_rs = h->lda; r.b_cs = 1;
-        r.C = ROW; r.c_rs = ldr; r.c_cs = 1;
+        r.C = ROW; r.c_rs = ld_row; r.c_cs = 1;
         RT_CHECK(gemm64(r, h->part, h->part_elems, h->stream));
     }
     phase_end(h, RTPROJ_PHASE_APPLY_AT);
-    if (X) RT_CHECK(transpose_copy(h->hbuf, k, X, ldx, m, k, h->stream));
+    if (f32) {
+        if (Zv) RT_CHECK(store_rows(h->sbuf, n, B, ldb, Zv, ldz, k, n, 1, RTPROJ_F32, h->stream));
+        if (ROWv) RT_CHECK(store_rows(h->sbuf, n, nullptr, 0, ROWv, ldr, k, n, 0, RTPROJ_F32, h->stream));
+    }
+    if (Xv) RT_CHECK(store_transposed(h->hbuf, k, m, k, Xv, ldx, h->dtype, h->stream));
+    h->last_passes = 0;
     return RTPROJ_OK;
 }
 
@@ -224,8 +260,8 @@ rtproj_status mixed_prepare_a(rtproj_ctx* h);
 rtproj_status mixed_sketch(rtproj_ctx* h, uint64_t seed, int64_t l, double* S, int64_t lds);
 rtproj_status mixed_gram(rtproj_ctx* h);
 rtproj_status mixed_prepare_middle(rtproj_ctx* h);
-rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, double* Z, int64_t ldz,
-                            double* ROW, int64_t ldr, double* X, int64_t ldx);
+rtproj_status mixed_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, void* Z, int64_t ldz,
+                            void* ROW, int64_t ldr, void* X, int64_t ldx);
 }  // namespace rtp
 
 namespace {
@@ -239,7 +275,7 @@ extern "C" {
 void rtproj_default_opts(rtproj_opts* o) {
     if (!o) return;
     o->mode = RTPROJ_MIXED_REFINED;
-    o->omega = RTPROJ_OMEGA_UNIFORM;
+    o->omega = RTPROJ_OMEGA_GAUSSIAN;
     o->sketch_slices = 5;
     o->gram_slices = 7;
     o->gram2_slices = 3;
@@ -248,6 +284,9 @@ void rtproj_default_opts(rtproj_opts* o) {
     o->refine_passes = 1;
     o->timing = 0;
     o->rank_tol = 0.0;
+    o->dtype = RTPROJ_F64;
+    o->spin_limit_cycles = 4000000000ll;
+    o->refine_tol = 0.0;
 }
 
 size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts* opts) {
@@ -259,7 +298,7 @@ size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max
     return make_layout(m, n, l_max, k_max, o).total;
 }
 
-rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A, int64_t lda, int64_t l_max,
+rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, int64_t lda, int64_t l_max,
                             int64_t k_max, void* workspace, size_t ws_bytes, void* stream, const rtproj_opts* opts) {
     if (!out) return RTPROJ_EINVAL;
     *out = nullptr;
@@ -275,9 +314,11 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A
     rtproj_ctx* h = new (std::nothrow) rtproj_ctx();
     if (!h) return RTPROJ_ENOMEM;
     h->m = m; h->n = n; h->lda = lda; h->l_max = l_max; h->k_max = k_max;
-    h->A = A; h->ws = (char*)workspace; h->ws_bytes = ws_bytes;
+    h->A_user = A; h->ws = (char*)workspace; h->ws_bytes = ws_bytes;
     h->stream = (cudaStream_t)stream;
     h->opts = o;
+    h->dtype = o.dtype;
+    h->spin_limit = o.spin_limit_cycles;
     char* b = h->ws;
     h->status = (int*)(b + L.status);
     h->S = (double*)(b + L.S);
@@ -297,6 +338,29 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const double* A
     h->hbuf = (double*)(b + L.hbuf);
     h->dhbuf = (double*)(b + L.dhbuf);
     h->sbuf = (double*)(b + L.sbuf);
+    h->A64 = (double*)(b + L.A64);
+    h->B64 = (double*)(b + L.B64);
+    h->normA = (double*)(b + L.normA);
+    h->norm_part = (double*)(b + L.norm_part);
+    h->bnorm = (double*)(b + L.bnorm);
+    h->stats = (unsigned long long*)(b + L.stats);
+    // every product reads A as float64: a float32 A is widened once, here (exactly)
+    if (o.dtype == RTPROJ_F32) {
+        double* wide = o.mode == RTPROJ_MIXED_REFINED ? h->W : h->A64;
+        if (widen_rows((const float*)A, lda, (int)m, (int)n, wide, n, h->stream) != cudaSuccess) {
+            delete h;
+            return RTPROJ_ECUDA;
+        }
+        h->A = wide;
+        h->lda = n;
+    } else {
+        h->A = (const double*)A;
+    }
+    if (frobenius(h->A, h->lda, (int)m, (int)n, h->norm_part, h->normA, h->stream) != cudaSuccess ||
+        cudaMemsetAsync(h->stats, 0, 16, h->stream) != cudaSuccess) {
+        delete h;
+        return RTPROJ_ECUDA;
+    }
     if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
         delete h;
         return RTPROJ_ECUDA;
@@ -356,10 +420,9 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_end(h, RTPROJ_PHASE_SKETCH);
     // 2. S^* = Q R Pi (Eq. 13)
     phase_begin(h, RTPROJ_PHASE_QR);
-    RT_CHECK(pivoted_qr(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s));
+    RT_CHECK(pivoted_qr(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s, h->spin_limit));
     const double tol = h->opts.rank_tol > 0 ? h->opts.rank_tol : 64.0 * (double)l * std::ldexp(1.0, -52);
-    rank_check_kernel<<<1, 1, 0, s>>>(h->R, m, tol, h->status);
-    note_launch();
+    RT_CHECK(qr_check(h->R, h->perm, m, tol, h->status, s));
     phase_end(h, RTPROJ_PHASE_QR);
     // R^{-*} (the transpose of P^- of Eq. 15, up to Pi)
     phase_begin(h, RTPROJ_PHASE_FACTOR);
@@ -373,7 +436,7 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_end(h, RTPROJ_PHASE_GRAM);
     // 4. X = L L^* (in place of Y = X^{-1}, Eq. 16), T1 = L^{-1} R^{-*}
     phase_begin(h, RTPROJ_PHASE_FACTOR);
-    RT_CHECK(cholesky(h->Lc, m, h->part, h->part_elems, h->status, s));
+    RT_CHECK(cholesky(h->Lc, m, h->part, h->part_elems, h->status, s, h->spin_limit));
     // the solve reads L through its transpose, so that a warp's loads of T are coalesced
     RT_CHECK(transpose_copy(h->Lc, m, h->Lt, m, m, m, s));
     RT_CHECK(cudaMemcpyAsync(h->T1, h->RinvT, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));
@@ -393,29 +456,50 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     return RTPROJ_OK;
 }
 
-rtproj_status rtproj_project(rtproj_t h, const double* B, int64_t ldb, int64_t k, double* Z, int64_t ldz,
-                             double* ROW, int64_t ldr, double* X, int64_t ldx) {
+rtproj_status rtproj_project(rtproj_t h, const void* B, int64_t ldb, int64_t k, void* Z, int64_t ldz,
+                             void* ROW, int64_t ldr, void* X, int64_t ldx) {
     if (!h || !B || k < 1 || k > h->k_max || ldb < h->n) return RTPROJ_EINVAL;
     if (!Z && !ROW && !X) return RTPROJ_EINVAL;
     if ((Z && ldz < h->n) || (ROW && ldr < h->n) || (X && ldx < h->m)) return RTPROJ_EINVAL;
     if (!h->preconditioned) return RTPROJ_ESTATE;
-    if (h->opts.mode == RTPROJ_MIXED_REFINED) return mixed_project(h, B, ldb, (int)k, Z, ldz, ROW, ldr, X, ldx);
-    return project_fp64(h, B, ldb, (int)k, Z, ldz, ROW, ldr, X, ldx);
+    const double* Bd = (const double*)B;
+    int64_t ldbd = ldb;
+    if (h->dtype == RTPROJ_F32) {   // right-hand sides widened exactly; outputs stored as float32
+        RT_CHECK(widen_rows((const float*)B, ldb, (int)k, (int)h->n, h->B64, h->n, h->stream));
+        Bd = h->B64;
+        ldbd = h->n;
+    }
+    if (h->opts.mode == RTPROJ_MIXED_REFINED) return mixed_project(h, Bd, ldbd, (int)k, Z, ldz, ROW, ldr, X, ldx);
+    return project_fp64(h, Bd, ldbd, (int)k, Z, ldz, ROW, ldr, X, ldx);
 }
 
-rtproj_status rtproj_null_project(rtproj_t h, const double* B, int64_t ldb, int64_t k, double* Z, int64_t ldz) {
+rtproj_status rtproj_null_project(rtproj_t h, const void* B, int64_t ldb, int64_t k, void* Z, int64_t ldz) {
     if (!Z) return RTPROJ_EINVAL;
     return rtproj_project(h, B, ldb, k, Z, ldz, nullptr, 0, nullptr, 0);
 }
 
-rtproj_status rtproj_row_project(rtproj_t h, const double* B, int64_t ldb, int64_t k, double* ROW, int64_t ldr) {
+rtproj_status rtproj_row_project(rtproj_t h, const void* B, int64_t ldb, int64_t k, void* ROW, int64_t ldr) {
     if (!ROW) return RTPROJ_EINVAL;
     return rtproj_project(h, B, ldb, k, nullptr, 0, ROW, ldr, nullptr, 0);
 }
 
-rtproj_status rtproj_lstsq(rtproj_t h, const double* B, int64_t ldb, int64_t k, double* X, int64_t ldx) {
+rtproj_status rtproj_lstsq(rtproj_t h, const void* B, int64_t ldb, int64_t k, void* X, int64_t ldx) {
     if (!X) return RTPROJ_EINVAL;
     return rtproj_project(h, B, ldb, k, nullptr, 0, nullptr, 0, X, ldx);
+}
+
+rtproj_status rtproj_generate_omega(uint64_t seed, int64_t n, int64_t l, int omega, double* G, int64_t ldg, void* stream) {
+    if (!G || n < 1 || l < 1 || ldg < l || n > ((int64_t)1 << 30) || l > ((int64_t)1 << 30)) return RTPROJ_EINVAL;
+    if (!valid_omega(omega)) return RTPROJ_EINVAL;
+    RT_CHECK(omega_dense(seed, omega, (int)n, (int)l, G, ldg, (cudaStream_t)stream));
+    return RTPROJ_OK;
+}
+
+rtproj_status rtproj_set_spin_limit(rtproj_t h, long long cycles) {
+    if (!h || cycles < 1) return RTPROJ_EINVAL;
+    h->spin_limit = cycles;
+    h->opts.spin_limit_cycles = cycles;
+    return RTPROJ_OK;
 }
 
 rtproj_status rtproj_export_state(rtproj_t h, double* R, int32_t* perm, double* Lc) {
@@ -451,8 +535,20 @@ rtproj_status rtproj_get_info(rtproj_t h, rtproj_info* info) {
         for (int i = 0; i < m; ++i) { lmax = std::max(lmax, std::fabs(d[m + i])); lmin = std::min(lmin, std::fabs(d[m + i])); }
         info->l11 = lmax;
         info->lmm = lmin;
+        info->kappa_R = info->rmm > 0 ? info->r11 / info->rmm : INFINITY;
+        info->kappa_pre = lmin > 0 ? lmax / lmin : INFINITY;
         std::free(d);
     }
+    double nA = 0.0;
+    unsigned long long st2[2] = {0, 0};
+    RT_CHECK(cudaMemcpy(&nA, h->normA, 8, cudaMemcpyDeviceToHost));
+    RT_CHECK(cudaMemcpy(st2, h->stats, 16, cudaMemcpyDeviceToHost));
+    info->norm_A = nA;
+    double v[2];
+    std::memcpy(v, st2, 16);
+    info->resid_rel = v[0];
+    info->dh_rel = v[1];
+    info->passes = h->last_passes;
     return RTPROJ_OK;
 }
 

@@ -13,6 +13,10 @@ namespace rtp {
 // Counts kernels enqueued by this library (reported by rtproj_launch_count).
 void note_launch(int n = 1);
 
+// Streaming multiprocessors of the current device (queried once per device; 152 on
+// GB300). Grid sizes and split-K factors are derived from it.
+int sm_count();
+
 // Per-phase CUDA-event timing (opts.timing).
 struct PhaseTimer {
     static constexpr int kMax = 64;
@@ -60,6 +64,29 @@ __device__ __forceinline__ uint32_t block_byte(const uint4& w, int b) {
     return (word >> (8 * (b & 3))) & 0xFFu;
 }
 
+// Gaussian entries of G: the Box-Muller transform (Box & Muller, 1958) of two Philox
+// words a, b in float32 -- u1 = ((a >> 9) + 1/2) 2^-23 in (0, 1) and u2 = (b >> 9) 2^-23
+// in [0, 1), both exact; r = sqrt(-2 ln u1) <= sqrt(48 ln 2) < 5.77; the pair
+// (r cos 2 pi u2, r sin 2 pi u2) -- each rounded to the nearest multiple of 2^-12 (ties to
+// even). Returned as the integers N = 4096 G, |N| <= 23637.
+__device__ __forceinline__ void gauss_pair(uint32_t a, uint32_t b, int& n_cos, int& n_sin) {
+    const float u1 = ((float)(a >> 9) + 0.5f) * 1.1920928955078125e-07f;   // 2^-23
+    const float u2 = (float)(b >> 9) * 1.1920928955078125e-07f;
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    n_cos = __float2int_rn((r * cs) * 4096.0f);
+    n_sin = __float2int_rn((r * sn) * 4096.0f);
+}
+
+// The four Gaussian entries 4q .. 4q+3 of column j of G (as N = 4096 G) from the Philox
+// block at counter (q, j, 1, 0).
+__device__ __forceinline__ void gauss_quad(uint32_t q, uint32_t j, uint32_t k0, uint32_t k1, int (&N)[4]) {
+    const uint4 w = philox4x32_10(make_uint4(q, j, 1u, 0u), k0, k1);
+    gauss_pair(w.x, w.y, N[0], N[1]);
+    gauss_pair(w.z, w.w, N[2], N[3]);
+}
+
 // ---------------------------------------------------------------------------
 // float64 tiled GEMM on the FP64 pipe, split over K into partial slabs.
 //   P[z][i][j] = sum_{k in split z} A(i,k) * B(k,j)
@@ -93,10 +120,15 @@ cudaError_t zero_upper(double* X, int m, cudaStream_t s);
 // overwritten. On exit R (m x m, upper) and perm (m) hold the factorization
 // S^*[:, perm] = Q R. work: pivoted_qr_work_doubles(m, l) doubles. pivoted_qr uses the
 // persistent cooperative kernel when the columns fit in shared memory, else one pivot
-// kernel and one update kernel per step (pivoted_qr_steps).
+// kernel and one update kernel per step (pivoted_qr_steps). spin_limit bounds each
+// grid-exchange wait in clock cycles (RTPROJ_ETIMEOUT when it expires).
 size_t pivoted_qr_work_doubles(int m, int l);
 cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
-                       double* work, int* status, cudaStream_t s);
+                       double* work, int* status, cudaStream_t s, long long spin_limit);
+// After the QR: checks that perm is a permutation of 0..m-1 (replacing it by the identity
+// and latching RTPROJ_ETIMEOUT when a QR that gave up left it incomplete, so that no later
+// kernel indexes through it out of range) and that |R_mm| > tol |R_11| (RTPROJ_ERANK).
+cudaError_t qr_check(const double* R, int32_t* perm, int m, double tol, int* status, cudaStream_t s);
 cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
                              double* work, int* status, cudaStream_t s);
 
@@ -112,7 +144,8 @@ cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
                  bool rhs_lower = false);
 size_t trsm_work_doubles(int m);
 // In-place lower Cholesky of the m x m row-major X (strict upper part zeroed).
-cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s);
+cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s,
+                     long long spin_limit);
 
 // ---------------------------------------------------------------------------
 // Mixed mode: fixed-point bfloat16 slicing and the sliced tensor-core GEMM.
@@ -155,8 +188,13 @@ cudaError_t slice_rows_given_exp(const double* X, int64_t x_rs, const SliceStack
 cudaError_t slice_rows_dual(const double* X, int64_t x_rs, const SliceStack& st, const SliceStack& tst, int* status,
                             cudaStream_t s);
 cudaError_t transpose_planes(const SliceStack& src, const SliceStack& dst, cudaStream_t s);
-// Writes G^* (l x n, reduction over n) as one digit plane plus its row exponents (exact).
+// Writes G^* (l x n, reduction over n) as digit planes plus row exponents (exact): one
+// plane for the uniform and Rademacher entries, two for the Gaussian ones (st.s >= 2).
 cudaError_t omega_plane(uint64_t seed, int dist, int n, int l, const SliceStack& st, cudaStream_t s);
+// G itself as float64 (n x l, row-major), for checking step a1 on its own.
+cudaError_t omega_dense(uint64_t seed, int dist, int n, int l, double* G, int64_t ldg, cudaStream_t s);
+// Digit planes G^* needs for a distribution.
+inline int omega_planes(int dist) { return dist == RTPROJ_OMEGA_GAUSSIAN ? 2 : 1; }
 cudaError_t fill_int(int32_t* e, int n, int v, cudaStream_t s);
 
 // C[(crow?crow[i]:i)*c_rs + j*c_cs] = alpha * (A_stack x B_stack^T)[i][j] + beta * Cin[...]
@@ -185,6 +223,32 @@ void phase_begin(rtproj_ctx* h, int phase);
 void phase_end(rtproj_ctx* h, int phase);
 // Steps 2-6 of the apply in float64: out = Pi^* T1^* T1 Pi c (c, out: m x k, ld k).
 rtproj_status middle_fp64(rtproj_ctx* h, const double* c, double* out, int k);
+}  // namespace rtp
+
+// ---------------------------------------------------------------------------
+// Boundary helpers (k_boundary.cu): element types at the ABI, norms for the reports.
+// ---------------------------------------------------------------------------
+namespace rtp {
+// dst (rows x cols, ld ldd, float64) = src (float32, ld lds), exactly.
+cudaError_t widen_rows(const float* src, int64_t lds, int rows, int cols, double* dst, int64_t ldd, cudaStream_t s);
+// dst (rows x cols, element type dt, ld ldd) = B - X (sub) or X; X and B float64.
+cudaError_t store_rows(const double* X, int64_t ldx, const double* B, int64_t ldb, void* dst, int64_t ldd, int rows,
+                       int cols, int sub, int dt, cudaStream_t s);
+// dst (cols x rows of element type dt, ld ldd) = transpose of src (rows x cols float64, ld lds).
+cudaError_t store_transposed(const double* src, int64_t lds, int rows, int cols, void* dst, int64_t ldd, int dt,
+                             cudaStream_t s);
+// *out = ||X||_F for X (rows x cols float64, ld ldx); deterministic two-level sum. part: at
+// least norm_parts() doubles.
+int norm_parts();
+cudaError_t frobenius(const double* X, int64_t ldx, int rows, int cols, double* part, double* out, cudaStream_t s);
+// out[j] = ||row j of X|| for the k rows of X (k x n float64, ld ldx).
+cudaError_t row_norms(const double* X, int64_t ldx, int k, int n, double* out, cudaStream_t s);
+// For the m x k blocks r, h, dh (row-major, ld k; right-hand side j is column j):
+// stats[0] <- max(stats[0], max_j ||r_j|| / (normA ||b_j||)) and
+// stats[1] <- max(stats[1], max_j ||dh_j|| / ||h_j||), as bit patterns of non-negative
+// doubles (r or dh may be null to skip that maximum).
+cudaError_t column_stats(const double* r, const double* h, const double* dh, int m, int k, const double* bnorm,
+                         const double* normA, unsigned long long* stats, cudaStream_t s);
 }  // namespace rtp
 
 // ---------------------------------------------------------------------------
@@ -230,6 +294,19 @@ struct rtproj_ctx {
     double* Mprime = nullptr;    // m x m
     void* sg_scratch = nullptr;  // int64 split-K partials
     size_t sg_scratch_bytes = 0;
+
+    // boundary (k_boundary.cu)
+    int dtype = RTPROJ_F64;      // element type of A, B and the outputs at the ABI
+    const void* A_user = nullptr;
+    double* A64 = nullptr;       // float32 A widened (float64 form; the mixed form widens into W)
+    double* B64 = nullptr;       // k_max x n: float32 right-hand sides widened
+    double* normA = nullptr;     // ||A||_F (device scalar)
+    double* norm_part = nullptr; // partial sums of the Frobenius norm
+    double* bnorm = nullptr;     // k_max: ||b_j|| of the current apply
+    unsigned long long* stats = nullptr;   // [0] resid_rel, [1] dh_rel (bit patterns)
+    long long spin_limit = 4000000000ll;
+    int last_passes = 0;
+    double norm_A_host = 0.0;
 
     rtp::PhaseTimer timer;
     int64_t l = 0;

@@ -6,7 +6,7 @@ import pytest
 
 import workloads
 from oracle import closed_form, exact, metrics, paper_method, philox
-from tests.gpu_common import EPS, fp64_tol, rt_module, to_dev, torch_cuda
+from tests.gpu_common import EPS, assert_rows_close, fp64_tol, rt_module, to_dev, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -15,18 +15,28 @@ def _projector(rt, torch, A, l, k, **kw):
     return rt.Projector(to_dev(torch, A), l_max=l, k_max=k, mode="fp64", **kw)
 
 
-@pytest.mark.parametrize("dist", ["uniform", "rademacher"])
+def ambiguity_allowance(A, seed, n, l, dist):
+    """|A| times one 2^-12 step on the Gaussian entries whose rounding a float32 transform
+    may decide either way (oracle.philox.gaussian_ambiguous); zero for the exact maps."""
+    if dist != "gaussian":
+        return 0.0
+    amb = philox.gaussian_ambiguous(seed, n, l)
+    return np.abs(A) @ (amb / philox.GAUSS_GRID)
+
+
+@pytest.mark.parametrize("dist", ["uniform", "rademacher", "gaussian"])
 @pytest.mark.parametrize("m,n,l", [(64, 2048, 256), (37, 1000, 41), (5, 77, 19)])
 def test_sketch_matches_oracle(m, n, l, dist):
     torch = torch_cuda()
     rt = rt_module()
     A = workloads.haar_spectrum_matrix(m, n, 1e-6, 3)
+    seed = (1 << 40) + 17
     with _projector(rt, torch, A, l, 1, omega=dist) as P:
-        S = P.sketch(seed=(1 << 40) + 17, l=l).cpu().numpy()
-    G = philox.omega((1 << 40) + 17, n, l, dist)
+        S = P.sketch(seed=seed, l=l).cpu().numpy()
+    G = philox.omega(seed, n, l, dist)
     Sref = A @ G
     scale = np.abs(A) @ np.abs(G)
-    assert np.all(np.abs(S - Sref) <= 4 * n * EPS * scale + 1e-300)
+    assert np.all(np.abs(S - Sref) <= 4 * n * EPS * scale + ambiguity_allowance(A, seed, n, l, dist) + 1e-300)
 
 
 @pytest.mark.parametrize("m,n,l", [(64, 2048, 256), (37, 1000, 41)])
@@ -66,10 +76,11 @@ def test_apply_matches_exact_oracle(m, n, l, k, kappa):
         Z, ROW, H = P.project(to_dev(torch, B), null=True, row=True, lstsq=True)
         info = P.info()
     assert info["status"] == 0
-    tol = fp64_tol(kappa, m)
-    assert metrics.max_rel_err(Z.cpu().numpy(), Zx) < tol
-    assert metrics.max_rel_err(ROW.cpu().numpy(), ROWx) < tol
-    assert metrics.max_rel_err(H.cpu().numpy(), Hx) < tol * kappa
+    tol = fp64_tol(kappa)
+    assert_rows_close(Z.cpu().numpy(), Zx, tol, "Z")
+    assert_rows_close(ROW.cpu().numpy(), ROWx, tol * np.max(np.linalg.norm(Zx, axis=1) / np.linalg.norm(ROWx, axis=1)),
+                      "ROW")
+    assert_rows_close(H.cpu().numpy(), Hx, tol * kappa, "H")
 
 
 def test_separate_entry_points_agree_and_alias():
@@ -106,7 +117,7 @@ def test_square_matrix_and_paper_family():
     with _projector(rt, torch, A, 68, 4) as P:
         P.precondition(seed=2, l=68)
         Z = P.null_project(to_dev(torch, B)).cpu().numpy()
-    assert metrics.max_rel_err(Z, Zc) < fp64_tol(1e10, 64)
+    assert metrics.max_rel_err(Z, Zc) < fp64_tol(1e10)
 
 
 def test_status_codes():
@@ -123,9 +134,16 @@ def test_status_codes():
         P.precondition(seed=1, l=m - 1)
     assert e.value.code == 1                      # l < m
     P.precondition(seed=1, l=40)
-    with pytest.raises(rt.RtprojError) as e:
-        P.null_project(to_dev(torch, workloads.rhs(3, n, 52)))
-    assert e.value.code == 1                      # k > k_max
+    B3 = to_dev(torch, workloads.rhs(3, n, 52))
+    with pytest.raises(TypeError):
+        P.null_project(B3)                        # k > k_max: the binding refuses it ...
+    Zb = torch.empty_like(B3)
+    L = rt.load_library()
+    import ctypes
+    assert L.rtproj_null_project(P._h, ctypes.c_void_p(B3.data_ptr()), n, 3, ctypes.c_void_p(Zb.data_ptr()),
+                                 n) == 1          # ... and so does the C ABI (EINVAL)
+    assert L.rtproj_null_project(P._h, ctypes.c_void_p(B3.data_ptr()), n - 1, 2, ctypes.c_void_p(Zb.data_ptr()),
+                                 n) == 1          # ldb < n
     P.close()
     Ad = A.copy()
     Ad[5] = Ad[3]                                 # rank deficient
@@ -141,27 +159,3 @@ def test_status_codes():
         P.precondition(seed=1, l=40)
     assert e.value.code == 5
     P.close()
-
-
-def test_full_size_dense_sampled():
-    """512 x 65536, kappa = 1e10, 64 right-hand sides, l = 2048 (the launch the bench times),
-    checked on one sampled right-hand side against the exact oracle and on all 64 through
-    invariants that hold at any size."""
-    torch = torch_cuda()
-    rt = rt_module()
-    w = workloads.WORKLOADS["dense_512x65536"]
-    A = w.matrix()
-    B = w.rhs()
-    with _projector(rt, torch, A, w.l, w.k) as P:
-        P.precondition(seed=w.seed_omega, l=w.l)
-        Bt = to_dev(torch, B)
-        Z = P.null_project(Bt)
-        ZZ = P.null_project(Z.clone())
-        Z = Z.cpu().numpy()
-        ZZ = ZZ.cpu().numpy()
-    Zx, _, _ = exact.exact_project(A, B[:1])
-    assert metrics.max_rel_err(Z[:1], Zx) < fp64_tol(1e10, 512)
-    assert metrics.max_rel_err(ZZ, Z) < fp64_tol(1e10, 512)
-    # The float64 form rounds b - A^* h with |h| ~ kappa |b|: ||A z|| is then of order
-    # eps * kappa * ||A||_F ||b|| (Remark 4.3 is what removes this; see the mixed form).
-    assert metrics.normalised_residual(A, Z, B, normA=1.0) < 64 * EPS * 1e10

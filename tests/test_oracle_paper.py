@@ -96,16 +96,60 @@ def test_result_independent_of_sketch_seed_and_size():
     assert metrics.max_rel_err(Z1, Z2) < 100 * EPS * 1e4
 
 
-def test_refinement_reprojects_and_refines():
+def _refine_case():
     A, V, G = _setup(m=12, n=120, kappa=1e9, seed=6)
     B = workloads.rhs(3, 120, 35)
     Z0, _, H0, pc = paper_method.project(A, G, B)
-    Z1, ROW1, H1 = paper_method.refine(A, pc, B, H0, passes=1)
     Zx, _, Hx = exact.exact_project(A, B)
+    return A, B, Z0, H0, pc, Zx
+
+
+def _refine_pin(A, B, Z0, H0, pc, Zx, refine):
+    """One pass of Remark 4.3 must (i) cut ||A z|| by at least 1e4 (the unrefined
+    residual is about eps * kappa^2 / kappa relative to |A||b|; one pass with float64
+    residuals leaves about eps), (ii) lower the error against the exact projection, and
+    (iii) keep Z + ROW = B."""
+    Z1, ROW1, H1 = refine(A, pc, B, H0, passes=1)
+    r0 = np.max(exact.exact_residual(A, Z0))
+    r1 = np.max(exact.exact_residual(A, Z1))
     e0 = metrics.max_rel_err(Z0, Zx)
     e1 = metrics.max_rel_err(Z1, Zx)
-    assert e1 <= 2 * e0
-    assert np.max(exact.exact_residual(A, Z1)) <= 2 * np.max(exact.exact_residual(A, Z0)) + 1e-30
+    return r1 <= 1e-4 * r0 and e1 < e0 and np.allclose(Z1 + ROW1, B, atol=1e-13), (r0, r1, e0, e1)
+
+
+def test_refinement_contracts_the_residual():
+    A, B, Z0, H0, pc, Zx = _refine_case()
+    ok, vals = _refine_pin(A, B, Z0, H0, pc, Zx, paper_method.refine)
+    assert ok, vals
+    assert vals[0] > 1e-9          # the case really starts well above float64 rounding
+
+
+def test_refinement_planted_mistakes_fail_the_pin():
+    """A refine that returns its input, one that skips the update of s, and one that
+    forgets to add dh to h each fail the same pin."""
+    A, B, Z0, H0, pc, Zx = _refine_case()
+
+    def noop(A_, pc_, B_, H0_, passes=1):
+        return Z0, B_ - Z0, H0_
+
+    def no_s_update(A_, pc_, B_, H0_, passes=1):
+        H = np.array(H0_, copy=True).T
+        S = B_.T - A_.T @ H
+        for _ in range(passes):
+            H = H + paper_method._middle(pc_, A_ @ S)
+        return S.T, B_ - S.T, H.T
+
+    def s_from_stale_h(A_, pc_, B_, H0_, passes=1):
+        H = np.array(H0_, copy=True).T
+        S = B_.T - A_.T @ H
+        for _ in range(passes):
+            dH = paper_method._middle(pc_, A_ @ S)
+            S = B_.T - A_.T @ H            # h never moves: s is recomputed from h0
+        return S.T, B_ - S.T, H.T
+
+    for wrong in (noop, no_s_update, s_from_stale_h):
+        ok, vals = _refine_pin(A, B, Z0, H0, pc, Zx, wrong)
+        assert not ok, (wrong.__name__, vals)
 
 
 def test_closed_form_family_and_planted_permutation_mistake(monkeypatch):
