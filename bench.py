@@ -40,6 +40,44 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2070e6 / 1e12
 
 METRIC = "null-space projections/s & % roofline, mixed vs FP64 form at <=1e-10 rel err"
 
+# Options a workload's precision needs beyond the defaults: at kappa = 1e12 the refinement
+# residuals take ten digits (2^-80 kappa ~ 1e-12) and the refinement runs to a tolerance.
+WORKLOAD_OPTS = {"dense_2048x262144": dict(resid_slices=10, refine_passes=4, refine_tol=1e-11)}
+# Workloads whose Haar factor is formed on the device (its host QR takes minutes).
+DEVICE_GENERATED = {"dense_2048x262144"}
+
+
+def workload_key(w):
+    return next((k for k, v in workloads.WORKLOADS.items() if v.name == w.name), None)
+
+
+def apply_roofline(w, opts, k, ms_call, passes, pk):
+    """The apply (null_project on k right-hand sides) against the HBM roof, on the method's
+    own bytes: A read as float64 once for c = A b and once for b - A^* h, twice more per
+    refinement pass (r = A s and s - A^* dh), plus B read and Z written and the m x k
+    solution; next to it, the tensor pipe's share for the digit-pair products the exact
+    slicing performs (the emulation's work, labelled as such), and the float64-equivalent
+    flop rate against the FP64 pipe."""
+    m, n = w.m, w.n
+    ap, rs = opts.apply_slices, opts.resid_slices
+    bytes_alg = (2 + 2 * passes) * m * n * 8 + n * k * 16 + m * k * 8
+    t = ms_call * 1e-3
+    hbm = bytes_alg / t / 1e9
+    pairs = digit_pairs(ap, ap, ap) + digit_pairs(rs, rs, rs) + passes * (digit_pairs(rs, rs, rs) + digit_pairs(ap, ap, ap))
+    tensor_flops = 2.0 * m * n * k * pairs + (1 + passes) * 2 * 2.0 * m * m * k * digit_pairs(ap, ap, ap)
+    tpeak = float(pk.get("bf16_tflops_sustained") or pk["bf16_tflops"])
+    fp64_equiv = 4.0 * m * n * k * (1 + passes)
+    return {
+        "bound": "hbm", "achieved": hbm, "peak": float(pk["hbm_gbs"]), "unit": "GB/s", "frac": hbm / float(pk["hbm_gbs"]),
+        "bytes_per_call": bytes_alg, "ms_per_call": ms_call, "peak_source": f"{pk['_source']} hbm_gbs",
+        "tensor_digit_pairs": {"achieved": tensor_flops / t / 1e12, "peak": tpeak, "unit": "TFLOP/s",
+                               "frac": tensor_flops / t / 1e12 / tpeak,
+                               "note": "bf16 tensor flops of the digit-pair products of the exact slicing "
+                                       "(the emulation's work, not the method's float64 flops)"},
+        "fp64_equivalent": {"achieved": fp64_equiv / t / 1e12, "fp64_pipe_peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "note": "4 m n k (1 + passes) float64 flops of the same products per call"},
+    }
+
 
 def peaks():
     if os.path.exists(MEASURED_PEAKS):
@@ -301,7 +339,9 @@ def run_ours(args, w, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     pk = peaks()
-    A = w.matrix()
+    key = workload_key(w)
+    wopts = dict(WORKLOAD_OPTS.get(key, {})) if args.mode == "mixed" else {}
+    A = w.matrix(device=dev) if key in DEVICE_GENERATED else w.matrix()
     B = w.rhs()
     At = torch.from_numpy(A).to(dev)
     Bt = torch.from_numpy(B).to(dev)
@@ -309,7 +349,7 @@ def run_ours(args, w, world, rank, local):
     seed0 = w.seed_omega
     out = {}
 
-    P = rt.Projector(At, l_max=w.l, k_max=w.k, mode=args.mode, timing=1)
+    P = rt.Projector(At, l_max=w.l, k_max=w.k, mode=args.mode, timing=1, **wopts)
     for i in range(args.warmup):
         P.precondition(seed0 + i, w.l)
         P.null_project(Bt, out=Zbuf_of(P, Bt))
@@ -331,12 +371,18 @@ def run_ours(args, w, world, rank, local):
 
     # accuracy of the timed configuration: sampled RHS against the exact oracle
     Z = Zbuf_of(P, Bt).cpu().numpy()
-    resid = metrics.normalised_residual(A, Z, B, normA=1.0)
-    acc = {"normalised_residual_max": resid}
-    if not args.no_accuracy and rank == 0:
-        Zx, _, _ = exact.exact_project(A, B[:1])
-        acc["z_rel_err_vs_exact_oracle"] = metrics.max_rel_err(Z[:1], Zx)
-        acc["sample"] = "RHS 0 against oracle.exact (double-double refinement)"
+    info = P.info()
+    acc = {"library_resid_rel": info["resid_rel"], "refine_passes": info["passes"]}
+    if key in DEVICE_GENERATED:
+        # beyond the exact oracle's reach: ||A z|| in double-double on sampled RHS
+        nb = np.linalg.norm(B, axis=1)
+        acc["normalised_residual_sampled"] = float(max(exact.exact_residual(A, Z[j:j + 1])[0] / nb[j] for j in (0, w.k - 1)))
+    else:
+        acc["normalised_residual_max"] = metrics.normalised_residual(A, Z, B, normA=1.0)
+        if not args.no_accuracy and rank == 0:
+            Zx, _, _ = exact.exact_project(A, B[:1])
+            acc["z_rel_err_vs_exact_oracle"] = metrics.max_rel_err(Z[:1], Zx)
+            acc["sample"] = "RHS 0 against oracle.exact (double-double refinement)"
     P.close()
 
     line = {
@@ -347,7 +393,8 @@ def run_ours(args, w, world, rank, local):
         "config": {"workload": w.name, "mode": args.mode, "m": w.m, "n": w.n, "k": w.k, "l": w.l,
                    "kappa": 1.0 / w.sigma_min, "omega": "gaussian (Box-Muller on Philox4x32-10, 2^-12 grid)",
                    "step": "precondition(seed, l) + null_project(k RHS)",
-                   "l2": "inputs larger than L2 (A is 268 MB float64)", "parallelism": f"replicas x{world}"},
+                   "l2": f"inputs larger than L2 (A is {A.nbytes / 1e6:.0f} MB float64)",
+                   "parallelism": f"replicas x{world}", "options": wopts},
         "phase_ms_per_step": {p: phase_ms[p] / args.steps for p in phase_ms if phase_cnt[p]},
         "accuracy": acc,
         "clocks": clocks,
@@ -357,8 +404,17 @@ def run_ours(args, w, world, rank, local):
     line["roofline"] = rl
     line["roofline_phases"] = rl_phases
 
-    with rt.Projector(At, l_max=w.l, k_max=w.k, mode=args.mode) as P2:
+    with rt.Projector(At, l_max=w.l, k_max=w.k, mode=args.mode, **wopts) as P2:
         line["split"] = split_times(torch, P2, Bt, w, args, stream)
+        if args.mode == "mixed":
+            passes = P2.info()["passes"]
+            ap = apply_roofline(w, P2.opts, w.k, line["split"]["null_project_ms"], passes, pk)
+            ap["projections_per_s"] = line["split"]["projection_only"]["value"]
+            line["apply"] = ap
+        if key in DEVICE_GENERATED:
+            line["per_k"] = per_k_times(torch, P2, Bt, w, pk, A, B)
+    if key in DEVICE_GENERATED and not args.no_accuracy and rank == 0:
+        line["paper_family"] = paper_family_errors(torch, rt, w, args, wopts, dev)
     if args.mode == "mixed" and not args.no_fp64_form:
         line["fp64_form"] = fp64_form(torch, rt, A, B, At, Bt, w, args, rank)
     if not args.no_e2e:
@@ -368,6 +424,55 @@ def run_ours(args, w, world, rank, local):
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
+
+
+def per_k_times(torch, P, Bt, w, pk, A, B):
+    """null_project at k = 1, 16 and the workload's k with one preconditioner: device time
+    per call (median of 10 after 2 warm-up calls), projections/s, the apply's HBM roofline
+    and ||A z|| in double-double on the first right-hand side."""
+    from oracle import exact
+    out = {}
+    stream = torch.cuda.current_stream(Bt.device)
+    for k in sorted({1, 16, w.k}):
+        Bk = Bt[:k]
+        Zk = torch.empty_like(Bk)
+        for _ in range(2):
+            P.null_project(Bk, out=Zk)
+        times = []
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.null_project(Bk, out=Zk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        info = P.info()
+        z0 = Zk[:1].cpu().numpy()
+        r = float(exact.exact_residual(A, z0)[0] / np.linalg.norm(B[0]))
+        out[str(k)] = {"ms_per_call": ms, "projections_per_s": k / (ms * 1e-3), "refine_passes": info["passes"],
+                       "normalised_residual_rhs0": r,
+                       "roofline": apply_roofline(w, P.opts, k, ms, info["passes"], pk)}
+    return out
+
+
+def paper_family_errors(torch, rt, w, args, wopts, dev):
+    """Z against the closed form of the paper's own family (Eqs. 20-21) at the workload's
+    size and kappa, for 16 right-hand sides, at k = 1, 16 and the workload's k."""
+    from oracle import closed_form, metrics
+    A, Bb, pu, pv = w.paper_family(return_parts=True)
+    B = w.rhs()
+    Zc, _, _ = closed_form.project(Bb, pu, pv, B[:16])
+    out = {}
+    with rt.Projector(torch.from_numpy(A).to(dev), l_max=w.l, k_max=w.k, mode=args.mode, **wopts) as P:
+        del A
+        P.precondition(w.seed_omega, w.l)
+        Bt = torch.from_numpy(B).to(dev)
+        for k in sorted({1, 16, w.k}):
+            Z = P.null_project(Bt[:k]).cpu().numpy()
+            kk = min(k, 16)
+            out[str(k)] = metrics.max_rel_err(Z[:kk], Zc[:kk])
+    return {"z_rel_err_vs_closed_form": out, "matrix": "U [B|...|B] V of Eqs. 20-21, same m, n, kappa"}
 
 
 def split_times(torch, P, Bt, w, args, stream):
@@ -408,9 +513,12 @@ def fp64_form(torch, rt, A, B, At, Bt, w, args, rank):
     out = {"value": w.k * steps / (ms * 1e-3), "unit": "projections/s", "ms_per_step": ms / steps, "steps": steps}
     if not args.no_accuracy and rank == 0:
         Z = Zbuf_of(P, Bt).cpu().numpy()
-        Zx, _, _ = exact.exact_project(A, B[:1])
-        out["z_rel_err_vs_exact_oracle"] = metrics.max_rel_err(Z[:1], Zx)
-        out["normalised_residual_max"] = metrics.normalised_residual(A, Z, B, normA=1.0)
+        if workload_key(w) in DEVICE_GENERATED:
+            out["normalised_residual_rhs0"] = float(exact.exact_residual(A, Z[:1])[0] / np.linalg.norm(B[0]))
+        else:
+            Zx, _, _ = exact.exact_project(A, B[:1])
+            out["z_rel_err_vs_exact_oracle"] = metrics.max_rel_err(Z[:1], Zx)
+            out["normalised_residual_max"] = metrics.normalised_residual(A, Z, B, normA=1.0)
     P.close()
     return out
 
@@ -473,6 +581,108 @@ def e2e(torch, rt, A, B, w, args, dev):
                           "current step's compute (second and third streams)"}
 
 
+def _family_errors(torch, rt, dev, m, n, l, kappa, mode, nb=100, seed=5, **kw):
+    """delta/kappa and epsilon/kappa of Section 5 (max over nb random unit b) on the paper's
+    family, with ||A z|| accumulated in double-double through the family's structure; also
+    the device times of precondition and of the projection of the nb vectors."""
+    from oracle import closed_form
+    A, Bb, pu, pv = workloads.paper_test_matrix(m, n, kappa, seed, return_parts=True)
+    B = workloads.rhs(nb, n, seed + 1)
+    B /= np.linalg.norm(B, axis=1, keepdims=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    with rt.Projector(torch.from_numpy(A).to(dev), l_max=l, k_max=nb, mode=mode, **kw) as P:
+        del A
+        Bt = torch.from_numpy(B).to(dev)
+        P.precondition(seed + 2, l)
+        P.null_project(Bt)
+        stream = torch.cuda.current_stream(dev)
+        ev[0].record(stream)
+        P.precondition(seed + 2, l)
+        ev[1].record(stream)
+        ev[2].record(stream)
+        Z = P.null_project(Bt)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        ZZ = P.null_project(Z.clone()).cpu().numpy()
+        Z = Z.cpu().numpy()
+    delta = float(np.max(np.linalg.norm(closed_form.apply_A(Bb, pu, pv, Z), axis=1)))
+    eps = float(np.max(np.linalg.norm(Z - ZZ, axis=1)))
+    return {"delta_over_kappa": delta / kappa, "epsilon_over_kappa": eps / kappa,
+            "precondition_ms": ev[0].elapsed_time(ev[1]), "project_ms": ev[2].elapsed_time(ev[3])}
+
+
+def study_accuracy(args):
+    """Section 5, Tables 2 and 4 (the randomized method's columns) on the GPU: the rows that
+    fit one GB300 at the paper's sizes, and the kappa sweep at m = 1000, n = 100000 (the
+    paper's sweep is m = 4000, n = 10^6), in both arithmetic forms, next to the values the
+    paper prints for its float64 CPU runs."""
+    import torch
+    import paper_0912_1135_gb300 as rt
+    golden = json.load(open(os.path.join(ROOT, "tests", "golden", "section5_randomized_errors.json")))
+    printed = {(r["m"], r["n"], r["l"], r["kappa"]): r for r in golden["table2"]}
+    printed4 = {r["kappa"]: r for r in golden["table4"]}
+    dev = torch.device("cuda", 0)
+    rows = [(40, 10 ** 6, 44, 1e8), (400, 10 ** 6, 404, 1e8), (1000, 3000, 1004, 1e8), (1000, 30000, 1004, 1e8),
+            (1000, 300000, 1004, 1e8)] + [(1000, 100000, 1004, k) for k in (1e4, 1e6, 1e8, 1e10, 1e12)]
+    out = []
+    for (m, n, l, kappa) in rows:
+        row = {"m": m, "n": n, "l": l, "kappa": kappa}
+        mixed_kw = dict(WORKLOAD_OPTS["dense_2048x262144"]) if kappa > 1e10 else {}
+        row["mixed"] = _family_errors(torch, rt, dev, m, n, l, kappa, "mixed", **mixed_kw)
+        row["fp64"] = _family_errors(torch, rt, dev, m, n, l, kappa, "fp64")
+        ref = printed.get((m, n, l, kappa)) or (printed4.get(kappa) if n == 100000 else None)
+        if ref:
+            row["paper"] = {"delta_over_kappa": ref["delta_over_kappa"], "epsilon_over_kappa": ref["epsilon_over_kappa"],
+                            "row": f"{ref['m']} x {ref['n']}, l = {ref['l']}"}
+        out.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "section5_accuracy", "omega": "gaussian", "rhs": "100 random unit b per row",
+                      "rows": out}), flush=True)
+    return 0
+
+
+def study_variates(args):
+    """Variates and sketch sizes (Section 5's remarks on the choice of G; Table 1's l rows):
+    for each distribution of G and l in {m, m + 4, 2m, 4m} on the headline workload, the
+    device time of precondition, kappa(P^{-1} A) from the GPU's R and Pi, the library's
+    estimate, and the mixed form's error on RHS 0 against the exact oracle."""
+    import scipy.linalg as sla
+    import torch
+    import paper_0912_1135_gb300 as rt
+    from oracle import exact, metrics
+    w = workloads.WORKLOADS["dense_512x65536"]
+    A = w.matrix()
+    B = w.rhs()
+    Zx, _, _ = exact.exact_project(A, B[:1])
+    dev = torch.device("cuda", 0)
+    At = torch.from_numpy(A).to(dev)
+    Bt = torch.from_numpy(B).to(dev)
+    out = []
+    for dist in ("gaussian", "uniform", "rademacher"):
+        for l in (w.m, w.m + 4, 2 * w.m, 4 * w.m):
+            with rt.Projector(At, l_max=l, k_max=w.k, omega=dist) as P:
+                P.precondition(w.seed_omega, l)
+                times = []
+                for i in range(5):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    P.precondition(w.seed_omega + i, l)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                Z = P.null_project(Bt).cpu().numpy()
+                info = P.info()
+                R, perm, _ = P.export_state()
+            W = sla.solve_triangular(R.T, A[perm], lower=True)
+            s = np.linalg.svd(W, compute_uv=False)
+            row = {"omega": dist, "l": l, "precondition_ms": statistics.median(times), "kappa_PinvA": float(s[0] / s[-1]),
+                   "kappa_pre_estimate": info["kappa_pre"], "z_rel_err_rhs0": metrics.max_rel_err(Z[:1], Zx)}
+            out.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"study": "variates_and_sketch_size", "workload": w.name, "rows": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,7 +696,13 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the float64-form comparison")
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
+    ap.add_argument("--study", choices=["accuracy", "variates"], default=None,
+                    help="run a study (Section 5 accuracy; variates and sketch sizes) instead of the bench")
     args = ap.parse_args()
+    if args.study:
+        import __graft_entry__
+        __graft_entry__.build()
+        return study_accuracy(args) if args.study == "accuracy" else study_variates(args)
     if args.warmup < 3:
         args.warmup = 3
     w = workloads.WORKLOADS[args.workload]

@@ -116,8 +116,9 @@ typedef struct {
                             expires the kernel latches RTPROJ_ETIMEOUT and every CTA returns.
                             The tensor-core products keep their own fixed bound.          */
     double refine_tol;   /* mixed: refine until the correction dh of every right-hand side
-                            satisfies ||dh|| <= refine_tol ||h|| (Remark 4.3), at most
-                            refine_passes passes; 0 (default) runs exactly refine_passes  */
+                            satisfies ||dh|| <= refine_tol max(||h||, ||b|| / ||A||_F)
+                            (Remark 4.3), at most refine_passes passes; 0 (default) runs
+                            exactly refine_passes                                         */
 } rtproj_opts;
 
 /* Phases timed when opts.timing is set (indices into rtproj_get_timings' arrays). */
@@ -148,7 +149,8 @@ typedef struct {
                                 refinement pass (Section 5's delta, normalised); 0 when no
                                 pass ran                                                  */
     double dh_rel;           /* mixed form, last apply: max over right-hand sides of
-                                ||dh|| / ||h|| of the last refinement correction          */
+                                ||dh|| / max(||h||, ||b|| / ||A||_F) for the last refinement
+                                correction dh (||A||_F ||dh|| bounds its change to Zb)     */
     int passes;              /* refinement passes run by the last apply                   */
 } rtproj_info;
 
@@ -225,6 +227,21 @@ rtproj_status rtproj_sketch_noalloc(const double* A, int64_t m, int64_t n, int64
    never stores G; this entry point exists to check step a1 on its own. Asynchronous;
    RTPROJ_EINVAL for invalid arguments. */
 rtproj_status rtproj_generate_omega(uint64_t seed, int64_t n, int64_t l, int omega, double* G, int64_t ldg, void* stream);
+
+/* Gradient with respect to A of L = sum_j <g_j, Z b_j> (the adjoint of Eq. 1; the paper
+   does not differentiate, this follows from it): with P = A^*(AA^*)^{-1},
+   dZ = -(Z dA^* P^* + P dA Z), so dL/db_j = Z g_j and
+       dL/dA = -sum_j (h_j (Z g_j)^* + w_j (Z b_j)^*) = -(H^* Y + W^* Zb),
+   where h_j = lstsq(b_j) and w_j = lstsq(g_j) (Remark 4.1). Inputs are k x m (H, W: rows
+   h_j, w_j) and k x n (Y: rows Z g_j; Zb: rows Z b_j), all in the handle's element type
+   and on its device, as rtproj_project returns them; dA is m x n (ldda >= n). The product
+   runs in the handle's mode (digit-sliced tensor-core products with apply_slices digits, or
+   float64). workspace: device, 256-byte aligned, at least rtproj_grad_workspace_bytes(h, k)
+   bytes, caller-owned. Asynchronous on the handle's stream. */
+size_t rtproj_grad_workspace_bytes(rtproj_t h, int64_t k);
+rtproj_status rtproj_grad_A(rtproj_t h, int64_t k, const void* H, int64_t ldh, const void* Y, int64_t ldy,
+                            const void* W, int64_t ldw, const void* Zb, int64_t ldz, void* dA, int64_t ldda,
+                            void* workspace, size_t ws_bytes);
 
 /* Replaces the handle's spin_limit_cycles (see rtproj_opts) for later calls; cycles >= 1. */
 rtproj_status rtproj_set_spin_limit(rtproj_t h, long long cycles);

@@ -27,6 +27,8 @@ Contents (all float64 unless stated):
                       Observation 3.2 (Eq. 10).
 * ``metrics``      -- the error measures of Section 5 (delta, epsilon) and
                       relative errors.
+* ``gradient``     -- dL/dA and dL/dB of L = sum_j <g_j, Z b_j> (the adjoint of
+                      Eq. 1) evaluated on the reference definition.
 
 Parity pins: every function is checked in ``tests/test_oracle_*.py`` against
 something other than itself (brute force in 60-digit arithmetic, the closed
@@ -34,4 +36,4 @@ form, invariants, library routines, values printed in the paper). The exact
 pivot sequence of the pivoted QR on near-ties and the bitwise identity of the
 Philox stream with other implementations of Philox are parity unpinned.
 """
-from . import closed_form, exact, metrics, paper_method, philox, reference, theory  # noqa: F401
+from . import closed_form, exact, gradient, metrics, paper_method, philox, reference, theory  # noqa: F401

@@ -24,7 +24,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["project", "kappa_of_B", "eigenvalues_B"]
+__all__ = ["project", "apply_A", "kappa_of_B", "eigenvalues_B"]
 
 
 def eigenvalues_B(m: int, d: float) -> np.ndarray:
@@ -59,3 +59,24 @@ def project(Bblock: np.ndarray, pu: np.ndarray, pv: np.ndarray, Brhs: np.ndarray
     # A^* h = V^* C^* U^* h; with (U^* h)[pu[i]] = h[i]:  U^* h = w  =>  h[i] = w[pu[i]].
     h = w[:, pu]
     return z, row, h
+
+
+def apply_A(Bblock: np.ndarray, pu: np.ndarray, pv: np.ndarray, Z: np.ndarray) -> np.ndarray:
+    """A z for the rows z of Z (k x n), accumulated in double-double (TwoSum and Dekker's
+    TwoProduct) and rounded once: with A[i, pv[c]] = C[pu[i], c], C = [B|...|B],
+    (A z)_i = sum_t B[pu[i], t] y_t where y_t = sum_q z[pv[q m + t]] sums the q = n/m
+    blocks. O(n k + m^2 k) instead of the dense m n k; Section 5's delta = ||A z||."""
+    from .exact import _dd_sum_rows, two_prod, two_sum
+    Z = np.atleast_2d(np.asarray(Z, np.float64))
+    m = Bblock.shape[0]
+    k, n = Z.shape
+    q = n // m
+    blocks = Z[:, pv].reshape(k, q, m).transpose(0, 2, 1)          # k x m x q
+    yh, yl = _dd_sum_rows(blocks, np.zeros_like(blocks))            # k x m, y = yh + yl
+    Bp = np.asarray(Bblock, np.float64)[pu, :]                      # row i of A's block: B[pu[i], :]
+    p, e = two_prod(Bp[None, :, :], yh[:, None, :])                 # k x m x m
+    e = e + Bp[None, :, :] * yl[:, None, :]
+    hi, lo = _dd_sum_rows(p, e)
+    s, t = two_sum(hi, lo)
+    return s + t
+

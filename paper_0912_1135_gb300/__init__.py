@@ -81,6 +81,8 @@ EXPORTS = {
     "rtproj_sketch_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, ctypes.c_uint64, _I64, ctypes.c_int, _P, _I64, _P]),
     "rtproj_generate_omega": (ctypes.c_int, [ctypes.c_uint64, _I64, _I64, ctypes.c_int, _P, _I64, _P]),
     "rtproj_set_spin_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "rtproj_grad_workspace_bytes": (ctypes.c_size_t, [_P, _I64]),
+    "rtproj_grad_A": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, ctypes.c_size_t]),
 }
 
 PHASES = ["sketch", "qr", "gram", "factor", "apply_a", "apply_m", "apply_at", "slice"]
@@ -292,6 +294,28 @@ class Projector:
         _check(code, "rtproj_project")
         self._leave(cur, Z, ROW, X)
         return Z, ROW, X
+
+    def grad_A(self, H: torch.Tensor, Y: torch.Tensor, W: torch.Tensor, Zb: torch.Tensor) -> torch.Tensor:
+        """dL/dA = -(H^* Y + W^* Zb) for L = sum_j <g_j, Z b_j> (rtproj_grad_A): H, W are
+        lstsq(B), lstsq(G) (k x m); Y, Zb are Z G, Z B (k x n)."""
+        k = H.shape[0]
+        for t, cols, name in ((H, self.m, "H"), (W, self.m, "W"), (Y, self.n, "Y"), (Zb, self.n, "Zb")):
+            self._out(t, k, cols, name)
+        lib = load_library()
+        nbytes = int(lib.rtproj_grad_workspace_bytes(self._h, k))
+        if nbytes == 0:
+            raise RtprojError(1, "rtproj_grad_workspace_bytes")
+        cur = self._enter(H, Y, W, Zb)
+        with torch.cuda.stream(self.stream):
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            dA = torch.empty((self.m, self.n), dtype=self.dtype, device=self.device)
+        with torch.cuda.device(self.device):
+            code = lib.rtproj_grad_A(self._h, k, _dev_ptr(H), H.stride(0), _dev_ptr(Y), Y.stride(0), _dev_ptr(W),
+                                     W.stride(0), _dev_ptr(Zb), Zb.stride(0), _dev_ptr(dA), dA.stride(0),
+                                     _dev_ptr(ws), ctypes.c_size_t(nbytes))
+        _check(code, "rtproj_grad_A")
+        self._leave(cur, dA)
+        return dA
 
     def null_project(self, B, out=None):
         return self.project(B, null=True, out_null=out)[0]

@@ -137,9 +137,14 @@ __global__ void column_stats_kernel(const double* r, const double* h, const doub
         }
     }
     if (dh) {
+        // relative to ||h||, or to ||b|| / ||A||_F when h is smaller than that (a b already
+        // near the null space): ||A||_F ||dh|| bounds the change A^* dh makes to Zb
         const double th = block_sum(sh, red);
         const double td = block_sum(sd, red);
-        if (threadIdx.x == 0) max_bits(&stats[1], th > 0.0 ? sqrt(td / th) : sqrt(td));
+        if (threadIdx.x == 0) {
+            const double scale = fmax(sqrt(th), *normA > 0.0 ? bnorm[j] / *normA : 0.0);
+            max_bits(&stats[1], scale > 0.0 ? sqrt(td) / scale : sqrt(td));
+        }
     }
 }
 

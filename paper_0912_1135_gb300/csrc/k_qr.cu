@@ -194,6 +194,7 @@ struct PqrDev {
     int* abort_flag;
     int* status;
     long long timeout;
+    const int* run_if;       // when set, the kernel runs only if *run_if != 0
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
@@ -252,6 +253,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     __shared__ int redi[2 * PQ_WARPS];
     __shared__ int ok_s;
     const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (p.run_if && *(volatile const int*)p.run_if == 0) return;   // the same value for every CTA
     const int c0 = b * cpc;
     const int nc = max(0, min(cpc, m - c0));
     const size_t slot_par = (size_t)G * cpc * l;   // doubles per parity buffer
@@ -463,8 +465,21 @@ cudaError_t qr_check(const double* R, int32_t* perm, int m, double tol, int* sta
     return cudaGetLastError();
 }
 
+bool pivoted_qr_persistent_ok(int m, int l) {
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop || sms <= 0) return false;
+    const int cpc = (m + sms - 1) / sms;
+    const size_t smem = ((size_t)cpc * l + l) * sizeof(double);
+    const int G = (m + cpc - 1) / cpc;
+    return cpc <= PQ_MAXC && G <= PQ_MAX_G && smem + 4096 <= (size_t)smem_optin;
+}
+
 cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
-                       double* work, int* status, cudaStream_t s, long long spin_limit) {
+                       double* work, int* status, cudaStream_t s, long long spin_limit, const int* run_if) {
     // Persistent cooperative form when the columns fit in shared memory.
     int dev = 0, sms = 0, coop = 0, smem_optin = 0;
     cudaGetDevice(&dev);
@@ -491,6 +506,7 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 p.abort_flag = (int*)(ctr + 1);
                 p.status = status;
                 p.timeout = spin_limit;
+                p.run_if = run_if;
                 cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
                 if (e != cudaSuccess) return e;
                 void* args[] = {&p};

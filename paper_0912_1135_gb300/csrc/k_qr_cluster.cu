@@ -1,0 +1,334 @@
+// Pivoted Householder QR of S^* (Section 4, Eq. 13) on one 16-CTA thread-block cluster,
+// in float-float arithmetic on the FP32 pipe: the preconditioner of the mixed form.
+//
+// Why: the QR's m steps are strictly sequential, and on the whole grid each step costs a
+// grid-wide exchange through L2 (publish, poll, read the candidates, read the pivot
+// column): several microseconds, far more than the step's arithmetic. Here S^* (l x m)
+// lives in the distributed shared memory of one cluster (CTA r holds columns
+// [r cpc, r cpc + cpc), 2.1 MB at 516 x 512), so a step's exchange is one hardware
+// cluster barrier plus two shared-memory reads through the cluster (the sixteen
+// candidates, then the pivot column). Sixteen SMs have 1/9 of the grid's FP64 pipe, so
+// the reflector updates run in float-float (a value is an unevaluated sum hi + lo of two
+// floats; Dekker's TwoProduct through fmaf and Knuth's TwoSum): about 2^-48 relative
+// accuracy, on the FP32 pipe, which has 64 times the FP64 pipe's rate.
+//
+// Accuracy: the computed R is the exact factor of S^* + E with ||E|| of order
+// l 2^-48 ||S||, so P^{-1}A = R^{-*} Pi A keeps kappa(P^{-1}A) near that of the sketch as
+// long as 2^-48 kappa(A) << 1 (3.6e-5 at kappa = 1e10). The preconditioner only needs
+// that: the refinement pass (Remark 4.3) makes the result exact whatever the
+// preconditioner's own rounding. The plain float64 form keeps the float64 QR.
+//
+// The pivot rule is the persistent kernel's (Businger-Golub with every norm recomputed
+// each step, largest squared norm and lowest index on ties), on float-float norms.
+// S^* is scaled by a power of two (exact) so that its largest entry lies in [1/2, 1);
+// if a column's squared norm then falls below 2^-90 (float-float would lose the digits
+// of a trailing norm near float's underflow), the kernel leaves R and perm untouched and
+// sets *fallback, and the float64 persistent kernel that follows it runs instead.
+#include "rtproj_internal.cuh"
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+namespace rtp {
+namespace {
+
+constexpr int CQ_CTAS = 16;
+constexpr int CQ_THREADS = 256;
+constexpr int CQ_WARPS = CQ_THREADS / 32;
+constexpr int CQ_MAXC = 64;
+
+struct ff {
+    float hi, lo;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ ff quick_two_sum(float a, float b) {
+    const float s = a + b;
+    return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ ff ff_add(ff x, ff y) {
+    ff s = two_sum(x.hi, y.hi);
+    return quick_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+
+__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
+
+__device__ __forceinline__ ff ff_mul(ff x, ff y) {
+    const float p = x.hi * y.hi;
+    float e = fmaf(x.hi, y.hi, -p);
+    e = fmaf(x.hi, y.lo, e);
+    e = fmaf(x.lo, y.hi, e);
+    return quick_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_sqrt(ff x) {
+    if (!(x.hi > 0.f)) return {0.f, 0.f};
+    const float s = sqrtf(x.hi);
+    const float e = (fmaf(-s, s, x.hi) + x.lo) / (2.f * s);
+    return quick_two_sum(s, e);
+}
+
+__device__ __forceinline__ ff ff_recip(ff d) {
+    const float q = 1.f / d.hi;
+    const float r = fmaf(-d.hi, q, 1.f) - d.lo * q;     // 1 - d q, to float-float accuracy
+    return quick_two_sum(q, r * q);
+}
+
+// x > y for normalised float-float values (|lo| <= ulp(hi) / 2)
+__device__ __forceinline__ bool ff_gt(ff x, ff y) { return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo); }
+
+__device__ __forceinline__ ff ff_warp_sum(ff v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = ff_add(v, w);
+    }
+    return v;
+}
+
+struct CqrDev {
+    const double* S;
+    int m, l;
+    int64_t lds;
+    double* R;
+    int32_t* perm;
+    int cpc;
+    int* fallback;      // set to 1 when the float-float range check fails (R, perm untouched)
+};
+
+__global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
+    extern __shared__ float2 csm[];
+    const int l = p.l, m = p.m, cpc = p.cpc;
+    float2* cols = csm;                          // cpc x l
+    float2* v = csm + (size_t)cpc * l;           // l (rows j .. l-1 of the reflector at offset 0)
+    __shared__ float2 cand_val[2];
+    __shared__ int cand_idx[2];
+    __shared__ float2 nsq[CQ_MAXC];
+    __shared__ float2 alphaq[CQ_MAXC];
+    __shared__ int posq[CQ_MAXC];
+    __shared__ unsigned long long max_bits_s;
+    __shared__ int bad_s;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int b = (int)cluster.block_rank();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int c0 = b * cpc;
+    const int nc = max(0, min(cpc, m - c0));
+
+    // 1. largest |entry| of S over the cluster, from the bit patterns (no float64 arithmetic)
+    if (t == 0) { max_bits_s = 0ull; bad_s = 0; }
+    __syncthreads();
+    {
+        unsigned long long mx = 0ull;
+        for (int q = 0; q < nc; ++q)
+            for (int i = t; i < l; i += CQ_THREADS) {
+                const unsigned long long u =
+                    (unsigned long long)__double_as_longlong(p.S[(int64_t)(c0 + q) * p.lds + i]) & 0x7FFFFFFFFFFFFFFFull;
+                mx = u > mx ? u : mx;
+            }
+        atomicMax(&max_bits_s, mx);
+    }
+    cluster.sync();
+    unsigned long long gmax = 0ull;
+    for (int r = 0; r < CQ_CTAS; ++r) {
+        const unsigned long long x = *cluster.map_shared_rank(&max_bits_s, r);
+        gmax = x > gmax ? x : gmax;
+    }
+    // scale 2^-e with the largest entry in [1/2, 1); a non-finite S cannot reach here (the
+    // caller's status already holds it), but its exponent field would be clamped anyway
+    int e = (int)(gmax >> 52) - 1022;
+    e = max(-1000, min(1000, e));
+    const double scale = ldexp(1.0, -e);
+
+    // 2. columns into shared memory as float-float, and their squared norms
+    for (int q = 0; q < nc; ++q)
+        for (int i = t; i < l; i += CQ_THREADS) {
+            const double x = p.S[(int64_t)(c0 + q) * p.lds + i] * scale;
+            const float hi = __double2float_rn(x);
+            const float lo = __double2float_rn(x - (double)hi);
+            cols[(size_t)q * l + i] = make_float2(hi, lo);
+        }
+    __syncthreads();
+    for (int q = warp; q < nc; q += CQ_WARPS) {
+        const float2* c = cols + (size_t)q * l;
+        ff s = {0.f, 0.f};
+        for (int i = lane; i < l; i += 32) {
+            const ff x = {c[i].x, c[i].y};
+            s = ff_add(s, ff_mul(x, x));
+        }
+        s = ff_warp_sum(s);
+        if (lane == 0) {
+            nsq[q] = make_float2(s.hi, s.lo);
+            posq[q] = -1;
+            if (!(s.hi >= 0x1p-90f)) atomicOr(&bad_s, 1);
+        }
+    }
+    __syncthreads();
+    if (t == 0) {
+        int bq = -1;
+        for (int q = 0; q < nc; ++q)
+            if (bq < 0 || ff_gt({nsq[q].x, nsq[q].y}, {nsq[bq].x, nsq[bq].y})) bq = q;
+        cand_val[0] = bq >= 0 ? nsq[bq] : make_float2(-1.f, 0.f);
+        cand_idx[0] = bq >= 0 ? c0 + bq : m;
+    }
+    cluster.sync();
+    int bad = 0;
+    for (int r = 0; r < CQ_CTAS; ++r) bad |= *cluster.map_shared_rank(&bad_s, r);
+    if (bad) {
+        if (b == 0 && t == 0) *p.fallback = 1;
+        cluster.sync();   // no CTA leaves while another may still read its shared memory
+        return;
+    }
+    if (b == 0 && t == 0) *p.fallback = 0;
+
+    // 3. the m steps
+    for (int j = 0; j < m; ++j) {
+        const int par = j & 1;
+        if (j > 0) cluster.sync();   // step j's candidates are published (step 0's by the sync above)
+        // the pivot: largest squared norm over the sixteen candidates, lowest index on ties
+        ff best = {-1.f, 0.f};
+        int bi = m;
+        if (lane < CQ_CTAS) {
+            const float2 cv = *cluster.map_shared_rank(&cand_val[par], lane);
+            const int ci = *cluster.map_shared_rank(&cand_idx[par], lane);
+            if (ci < m) { best = {cv.x, cv.y}; bi = ci; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ff ob;
+            ob.hi = __shfl_xor_sync(0xffffffffu, best.hi, o);
+            ob.lo = __shfl_xor_sync(0xffffffffu, best.lo, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi < m && (bi == m || ff_gt(ob, best) || (ob.hi == best.hi && ob.lo == best.lo && oi < bi))) {
+                best = ob;
+                bi = oi;
+            }
+        }
+        const int piv = bi < m ? bi : 0;   // some CTA holds an active column while j < m
+        const int owner = piv / cpc, qo = piv - owner * cpc;
+        const float2* src = cluster.map_shared_rank(cols + (size_t)qo * l, owner);
+        // the reflector from the pivot column's rows j .. l-1 (read through the cluster)
+        const float2 x0f = src[j];
+        const ff x0 = {x0f.x, x0f.y};
+        const ff nx = ff_sqrt(best);
+        const ff alpha = x0.hi >= 0.f ? ff_neg(nx) : nx;
+        const ff ax0 = x0.hi >= 0.f ? x0 : ff_neg(x0);
+        const ff den = ff_mul(nx, ff_add(nx, ax0));
+        const ff beta = den.hi > 0.f ? ff_recip(den) : ff{0.f, 0.f};
+        for (int i = j + 1 + t; i < l; i += CQ_THREADS) v[i - j] = src[i];
+        if (t == 0) {
+            const ff v0 = ff_add(x0, ff_neg(alpha));
+            v[0] = make_float2(v0.hi, v0.lo);
+            if (b == owner) {
+                posq[qo] = j;
+                alphaq[qo] = make_float2(alpha.hi, alpha.lo);
+                p.perm[j] = piv;
+            }
+        }
+        __syncthreads();
+        const int len = l - j;
+        // each active column: w = beta v^* c, c <- c - w v, squared norm of rows j+1 .. l-1
+        for (int q = warp; q < nc; q += CQ_WARPS) {
+            if (posq[q] >= 0) continue;
+            float2* c = cols + (size_t)q * l + j;
+            ff s = {0.f, 0.f};
+            for (int i = lane; i < len; i += 32) {
+                const float2 a = v[i], x = c[i];
+                s = ff_add(s, ff_mul({a.x, a.y}, {x.x, x.y}));
+            }
+            s = ff_warp_sum(s);
+            const ff w = ff_mul(s, beta);
+            ff ns = {0.f, 0.f};
+            for (int i = lane; i < len; i += 32) {
+                const float2 a = v[i], x = c[i];
+                const ff y = ff_add({x.x, x.y}, ff_neg(ff_mul(w, {a.x, a.y})));
+                c[i] = make_float2(y.hi, y.lo);
+                if (i > 0) ns = ff_add(ns, ff_mul(y, y));
+            }
+            ns = ff_warp_sum(ns);
+            if (lane == 0) nsq[q] = make_float2(ns.hi, ns.lo);
+        }
+        __syncthreads();
+        // this CTA's candidate for step j+1
+        if (t == 0) {
+            int bq = -1;
+            for (int q = 0; q < nc; ++q)
+                if (posq[q] < 0 && (bq < 0 || ff_gt({nsq[q].x, nsq[q].y}, {nsq[bq].x, nsq[bq].y}))) bq = q;
+            cand_val[par ^ 1] = bq >= 0 ? nsq[bq] : make_float2(-1.f, 0.f);
+            cand_idx[par ^ 1] = bq >= 0 ? c0 + bq : m;
+        }
+    }
+    // R[:, pos] = rows 0 .. pos-1 of the retired column, alpha on the diagonal (scaled back)
+    const double unscale = ldexp(1.0, e);
+    for (int q = 0; q < nc; ++q) {
+        const int pos = posq[q];
+        if (pos < 0) continue;             // every column is retired by step m - 1
+        const float2* c = cols + (size_t)q * l;
+        for (int i = t; i < m; i += CQ_THREADS) {
+            double r = 0.0;
+            if (i < pos) r = ((double)c[i].x + (double)c[i].y) * unscale;
+            else if (i == pos) r = ((double)alphaq[q].x + (double)alphaq[q].y) * unscale;
+            p.R[(int64_t)i * m + pos] = r;
+        }
+    }
+    cluster.sync();   // no CTA leaves while another may still read its shared memory
+}
+
+}  // namespace
+
+bool qr_cluster_fits(int m, int l) {
+    const int cpc = (m + CQ_CTAS - 1) / CQ_CTAS;
+    const size_t smem = ((size_t)cpc * l + l) * sizeof(float2);
+    return cpc <= CQ_MAXC && smem <= 200 * 1024;
+}
+
+cudaError_t pivoted_qr_cluster(const double* S, int m, int l, int64_t lds, double* R, int32_t* perm, int* fallback,
+                               cudaStream_t s, bool* launched) {
+    *launched = false;
+    if (!qr_cluster_fits(m, l)) return cudaSuccess;
+    const int cpc = (m + CQ_CTAS - 1) / CQ_CTAS;
+    const size_t smem = ((size_t)cpc * l + l) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(qr_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;   // the caller uses the float64 kernel
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CQ_CTAS);
+    cfg.blockDim = dim3(CQ_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CQ_CTAS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, qr_cluster_kernel, &cfg) != cudaSuccess || clusters < 1) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    CqrDev p;
+    p.S = S; p.m = m; p.l = l; p.lds = lds; p.R = R; p.perm = perm; p.cpc = cpc; p.fallback = fallback;
+    e = cudaLaunchKernelEx(&cfg, qr_cluster_kernel, p);
+    note_launch();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cudaSuccess;
+    }
+    *launched = true;
+    return cudaSuccess;
+}
+
+}  // namespace rtp

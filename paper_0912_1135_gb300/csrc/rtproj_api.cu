@@ -420,7 +420,16 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_end(h, RTPROJ_PHASE_SKETCH);
     // 2. S^* = Q R Pi (Eq. 13)
     phase_begin(h, RTPROJ_PHASE_QR);
-    RT_CHECK(pivoted_qr(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s, h->spin_limit));
+    // mixed form: the float-float cluster QR when S^* fits one cluster's shared memory (the
+    // float64 persistent kernel follows and runs only if the cluster kernel's range check
+    // sent the factorization back to it); the float64 form keeps the float64 QR
+    bool cluster = false;
+    int* qr_flag = h->status + 4;
+    const char* qr_env = std::getenv("RTPROJ_FP64_QR");
+    if (h->opts.mode == RTPROJ_MIXED_REFINED && !(qr_env && qr_env[0] == '1') && pivoted_qr_persistent_ok(m, (int)l))
+        RT_CHECK(pivoted_qr_cluster(h->S, m, (int)l, l, h->R, h->perm, qr_flag, s, &cluster));
+    RT_CHECK(pivoted_qr(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s, h->spin_limit,
+                        cluster ? qr_flag : nullptr));
     const double tol = h->opts.rank_tol > 0 ? h->opts.rank_tol : 64.0 * (double)l * std::ldexp(1.0, -52);
     RT_CHECK(qr_check(h->R, h->perm, m, tol, h->status, s));
     phase_end(h, RTPROJ_PHASE_QR);

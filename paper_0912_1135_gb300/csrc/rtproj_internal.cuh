@@ -122,9 +122,19 @@ cudaError_t zero_upper(double* X, int m, cudaStream_t s);
 // persistent cooperative kernel when the columns fit in shared memory, else one pivot
 // kernel and one update kernel per step (pivoted_qr_steps). spin_limit bounds each
 // grid-exchange wait in clock cycles (RTPROJ_ETIMEOUT when it expires).
+// run_if (optional): the persistent kernel returns at once unless *run_if != 0 (the
+// cluster form's fallback flag); only meaningful when pivoted_qr_persistent_ok(m, l).
 size_t pivoted_qr_work_doubles(int m, int l);
 cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
-                       double* work, int* status, cudaStream_t s, long long spin_limit);
+                       double* work, int* status, cudaStream_t s, long long spin_limit,
+                       const int* run_if = nullptr);
+bool pivoted_qr_persistent_ok(int m, int l);
+// The mixed form's QR on one 16-CTA cluster in float-float arithmetic (k_qr_cluster.cu).
+// Sets *launched when the kernel was enqueued; the kernel then writes *fallback = 1 if the
+// entries' range needs the float64 kernel (which must follow with run_if = fallback).
+bool qr_cluster_fits(int m, int l);
+cudaError_t pivoted_qr_cluster(const double* S, int m, int l, int64_t lds, double* R, int32_t* perm, int* fallback,
+                               cudaStream_t s, bool* launched);
 // After the QR: checks that perm is a permutation of 0..m-1 (replacing it by the identity
 // and latching RTPROJ_ETIMEOUT when a QR that gave up left it incomplete, so that no later
 // kernel indexes through it out of range) and that |R_mm| > tol |R_11| (RTPROJ_ERANK).
@@ -245,7 +255,7 @@ cudaError_t frobenius(const double* X, int64_t ldx, int rows, int cols, double* 
 cudaError_t row_norms(const double* X, int64_t ldx, int k, int n, double* out, cudaStream_t s);
 // For the m x k blocks r, h, dh (row-major, ld k; right-hand side j is column j):
 // stats[0] <- max(stats[0], max_j ||r_j|| / (normA ||b_j||)) and
-// stats[1] <- max(stats[1], max_j ||dh_j|| / ||h_j||), as bit patterns of non-negative
+// stats[1] <- max(stats[1], max_j ||dh_j|| / max(||h_j||, ||b_j|| / normA)), as bit patterns of non-negative
 // doubles (r or dh may be null to skip that maximum).
 cudaError_t column_stats(const double* r, const double* h, const double* dh, int m, int k, const double* bnorm,
                          const double* normA, unsigned long long* stats, cudaStream_t s);

@@ -80,7 +80,8 @@ def test_apply_matches_exact_oracle(m, n, l, k, kappa):
     assert_rows_close(Z.cpu().numpy(), Zx, tol, "Z")
     assert_rows_close(ROW.cpu().numpy(), ROWx, tol * np.max(np.linalg.norm(Zx, axis=1) / np.linalg.norm(ROWx, axis=1)),
                       "ROW")
-    assert_rows_close(H.cpu().numpy(), Hx, tol * kappa, "H")
+    # h's error lands near eps kappa too (measured 0.5 to 1.3 eps kappa at kappa = 1e8, 1e10)
+    assert_rows_close(H.cpu().numpy(), Hx, 16 * tol, "H")
 
 
 def test_separate_entry_points_agree_and_alias():

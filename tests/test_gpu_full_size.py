@@ -41,9 +41,9 @@ def _run(rt, torch, w, A, B, mode):
         P.precondition(seed=w.seed_omega, l=w.l)
         Bt = to_dev(torch, B)
         Z, ROW, H = P.project(Bt, null=True, row=True, lstsq=True)
+        info = P.info()                                   # the report of this apply
         Zn = P.null_project(Bt)
         ZZ = P.null_project(Zn.clone())
-        info = P.info()
     return Z.cpu().numpy(), ROW.cpu().numpy(), H.cpu().numpy(), Zn.cpu().numpy(), ZZ.cpu().numpy(), info
 
 
@@ -76,7 +76,7 @@ def test_float64_form_full_size(data, exact_sample):
     tol = fp64_tol(KAPPA)
     assert_rows_close(Z[ROWS], Zx, tol, "Z")
     assert_rows_close(ROW[ROWS], ROWx, tol * np.max(np.linalg.norm(Zx, axis=1) / np.linalg.norm(ROWx, axis=1)), "ROW")
-    assert_rows_close(H[ROWS], Hx, tol * KAPPA, "H")
+    assert_rows_close(H[ROWS], Hx, 16 * tol, "H")
     assert metrics.max_rel_err(ZZ, Z) < tol
     # The float64 form rounds b - A^* h with |h| ~ kappa |b|: ||A z|| is then of order
     # eps * kappa * ||A||_F ||b|| (Remark 4.3 is what removes this; see the mixed form).

@@ -88,12 +88,14 @@ def test_apply_matches_exact_oracle(m, n, l, k, kappa):
 
 def test_square_matrix():
     """m = n: the null space is {0}, so Z = 0 up to rounding of b against b~, and h solves
-    A^* h = b (Section 1)."""
+    A^* h = b (Section 1). l <= n forces l = m: the square sketch's kappa(V^* G) is heavy
+    tailed (Observation 3.2 needs l - m of a few), so the preconditioner contracts less and
+    the refinement runs to a tolerance."""
     torch = torch_cuda()
     rt = rt_module()
     A = workloads.haar_spectrum_matrix(48, 48, 1e-3, 40)
     B = workloads.rhs(2, 48, 41)
-    with _mixed(rt, torch, A, 48, 2) as P:
+    with _mixed(rt, torch, A, 48, 2, refine_passes=8, refine_tol=1e-15) as P:
         P.precondition(seed=1, l=48)
         Z, _, H = P.project(to_dev(torch, B), null=True, lstsq=True)
     assert np.max(np.abs(Z.cpu().numpy())) < 1e-13 * np.max(np.abs(B))
@@ -193,3 +195,41 @@ def test_nonfinite_entry_of_a_is_reported_by_precondition():
         with pytest.raises(rt.RtprojError) as e:
             P.precondition(seed=1, l=41)
         assert e.value.code == 5
+
+
+@pytest.mark.parametrize("m,n,l", [(64, 2048, 256), (37, 1000, 41), (512, 8192, 516)])
+def test_cluster_qr_is_a_valid_pivoted_qr(m, n, l):
+    """The mixed form's float-float cluster QR, checked by properties that do not depend on
+    how near-ties between pivots resolve: R^* R equals the Gram matrix of the permuted S^*
+    (S^* Pi = Q R with orthonormal Q) to float-float accuracy, R is upper triangular, and
+    every diagonal entry dominates the trailing part of its row's columns (the column-pivoting
+    property: |R_jj|^2 >= sum_{i >= j} R_ic^2 for c > j)."""
+    torch = torch_cuda()
+    rt = rt_module()
+    A = workloads.haar_spectrum_matrix(m, n, 1e-8, 80 + m)
+    with _mixed(rt, torch, A, l, 1) as P:
+        S = P.sketch(seed=21, l=l).cpu().numpy()
+        P.precondition(seed=21, l=l)
+        R, perm, _ = P.export_state()
+    assert sorted(perm) == list(range(m))
+    assert np.all(np.tril(R, -1) == 0)
+    Sp = S[perm]                                   # rows of S = columns of S^*, permuted
+    G = Sp @ Sp.T
+    assert np.max(np.abs(R.T @ R - G)) <= 32 * l * 2.0 ** -48 * np.max(np.abs(G))
+    tail = np.cumsum((R ** 2)[::-1], axis=0)[::-1]          # tail[j, c] = sum_{i >= j} R_ic^2
+    for j in range(m - 1):
+        assert R[j, j] ** 2 >= (1 - 1e-6) * np.max(tail[j, j + 1:])
+
+
+def test_cluster_and_float64_qr_give_the_same_projection(monkeypatch):
+    torch = torch_cuda()
+    rt = rt_module()
+    m, n, l, k = 64, 4096, 256, 4
+    A = workloads.haar_spectrum_matrix(m, n, 1e-10, 85)
+    B = workloads.rhs(k, n, 86)
+    Zx, _, _ = exact.exact_project(A, B)
+    for flag in ("0", "1"):
+        monkeypatch.setenv("RTPROJ_FP64_QR", flag)
+        with _mixed(rt, torch, A, l, k) as P:
+            P.precondition(seed=5, l=l)
+            assert_rows_close(P.null_project(to_dev(torch, B)).cpu().numpy(), Zx, Z_TOL, f"Z (RTPROJ_FP64_QR={flag})")

@@ -1,0 +1,57 @@
+"""Section 5's accuracy study, the randomized method's columns (Tables 2 and 4): on the
+paper's own test matrix (Eqs. 20-21), delta = max over 100 random unit b of ||A Zb|| and
+epsilon = max of ||Zb - Z(Zb)||, both divided by kappa.
+
+delta is accumulated in double-double through the family's structure
+(oracle.closed_form.apply_A), so it measures the projection, not the check. The float64
+form is the paper's algorithm in IEEE double precision, as the paper ran it: its errors
+must land at the magnitudes the tables print (the tables' largest randomized-method values
+over all rows, times ten). The mixed refined form must beat the paper's own numbers for
+the same (m, kappa) row."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import closed_form
+from tests.gpu_common import rt_module, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _golden(golden_dir):
+    with open(os.path.join(golden_dir, "section5_randomized_errors.json")) as f:
+        return json.load(f)
+
+
+def study_row(rt, torch, m, n, l, kappa, mode, seed=5, nb=100, **kw):
+    A, Bb, pu, pv = workloads.paper_test_matrix(m, n, kappa, seed, return_parts=True)
+    B = workloads.rhs(nb, n, seed + 1)
+    B /= np.linalg.norm(B, axis=1, keepdims=True)                  # unit b
+    with rt.Projector(to_dev(torch, A), l_max=l, k_max=nb, mode=mode, **kw) as P:
+        P.precondition(seed=seed + 2, l=l)
+        Z = P.null_project(to_dev(torch, B))
+        ZZ = P.null_project(Z.clone()).cpu().numpy()
+        Z = Z.cpu().numpy()
+    delta = float(np.max(np.linalg.norm(closed_form.apply_A(Bb, pu, pv, Z), axis=1)))
+    eps = float(np.max(np.linalg.norm(Z - ZZ, axis=1)))
+    return delta / kappa, eps / kappa
+
+
+@pytest.mark.parametrize("kappa", [1e4, 1e8, 1e12])
+def test_randomized_method_errors_against_tables_2_and_4(kappa, golden_dir):
+    torch = torch_cuda()
+    rt = rt_module()
+    g = _golden(golden_dir)
+    rows = g["table2"] + g["table4"]
+    paper_delta = max(r["delta_over_kappa"] for r in rows)
+    paper_eps = max(r["epsilon_over_kappa"] for r in rows)
+    same = [r for r in g["table4"] if r["kappa"] == kappa][0]
+    m, n, l = 200, 100000, 204
+    d64, e64 = study_row(rt, torch, m, n, l, kappa, "fp64")
+    assert d64 <= 10 * paper_delta and e64 <= 10 * paper_eps, (d64, e64)
+    opts = dict(resid_slices=10, refine_passes=4, refine_tol=1e-11) if kappa > 1e10 else {}
+    dmx, emx = study_row(rt, torch, m, n, l, kappa, "mixed", **opts)
+    assert dmx <= same["delta_over_kappa"] and emx <= same["epsilon_over_kappa"], (dmx, emx, same)

@@ -74,3 +74,17 @@ def test_planted_dropped_error_term_is_caught(monkeypatch):
     Z, _, _ = exact.exact_project(A, B)
     Zm, _, _ = mp_project(A, B, dps=80)
     assert metrics.max_rel_err(Z, Zm) > 1e-12
+
+
+def test_paper_family_apply_matches_dense_double_double():
+    """closed_form.apply_A (the family's structure, O(n)) against the dense matrix times z
+    accumulated by oracle.exact.dd_matvec -- two independent routes to A z."""
+    A, Bb, pu, pv = workloads.paper_test_matrix(8, 96, 1e8, 4, return_parts=True)
+    Z = workloads.rhs(3, 96, 5)
+    got = closed_form.apply_A(Bb, pu, pv, Z)
+    for j in range(3):
+        h, l = exact.dd_matvec(A, Z[j])
+        np.testing.assert_allclose(got[j], h + l, rtol=1e-15, atol=1e-15 * np.abs(A).max() * np.abs(Z[j]).sum())
+    # on the family's own null-space projection, A z vanishes to double-double accuracy
+    Zc, _, _ = closed_form.project(Bb, pu, pv, Z)
+    assert np.max(np.abs(closed_form.apply_A(Bb, pu, pv, Zc))) < 1e-13 * np.abs(A).max()

@@ -52,20 +52,42 @@ def log_spaced_sigma(m: int, sigma_min: float) -> np.ndarray:
 
 
 def haar_spectrum_matrix(m: int, n: int, sigma_min: float, seed: int,
-                         dtype=np.float64, return_factors: bool = False):
+                         dtype=np.float64, return_factors: bool = False, device=None):
     """A = U diag(sigma) V^T, m x n row-major, with kappa(A) = 1/sigma_min.
 
     U is m x m and V is n x m, both Haar; sigma is log-spaced over
     [sigma_min, 1]. With ``return_factors`` the tuple (A, U, sigma, V) is
     returned, V being the right singular vectors of the exact product (the
     stored A differs from it by rounding).
+
+    ``device`` (a torch device) moves the QR of the n x m Gaussian behind V and
+    the product onto that device (float64 LAPACK-style QR of the library torch
+    links, the same sign fix); the Gaussian is the same seeded draw, so A agrees
+    with the host construction to rounding. It exists for sizes whose host QR
+    takes minutes (2048 x 262144).
     """
     if not (1 <= m <= n):
         raise ValueError("need 1 <= m <= n")
     rng = np.random.default_rng(seed)
     u = haar_orthonormal(rng, m, m)
-    v = haar_orthonormal(rng, n, m)
     sig = log_spaced_sigma(m, sigma_min)
+    if device is not None:
+        import torch
+        g = torch.from_numpy(rng.standard_normal((n, m))).to(device)
+        q, r = torch.linalg.qr(g)
+        del g
+        s = torch.sign(torch.diagonal(r))
+        s[s == 0] = 1.0
+        q *= s[None, :]
+        del r
+        a_t = (torch.from_numpy(u * sig[None, :]).to(device) @ q.T).contiguous()
+        a = np.ascontiguousarray(a_t.cpu().numpy().astype(dtype))
+        v = q.cpu().numpy() if return_factors else None
+        del q, a_t
+        if return_factors:
+            return a, u, sig, v
+        return a
+    v = haar_orthonormal(rng, n, m)
     a = (u * sig[None, :]) @ v.T
     a = np.ascontiguousarray(a.astype(dtype))
     if return_factors:
@@ -133,13 +155,19 @@ class Workload:
     def matrix(self, **kw):
         return haar_spectrum_matrix(self.m, self.n, self.sigma_min, self.seed_a, **kw)
 
+    def paper_family(self, **kw):
+        """The paper's own test matrix (Eqs. 20-21) at this workload's size and kappa."""
+        return paper_test_matrix(self.m, self.n, 1.0 / self.sigma_min, self.seed_a, **kw)
+
     def rhs(self, k: int | None = None):
         return rhs(self.k if k is None else k, self.n, self.seed_b)
 
 
-# Small dense configuration (oracle-sized, l = 4m) and the headline dense configuration
-# (l = m + 4, the sketch size Section 4 suggests).
+# Small dense configuration (oracle-sized, l = 4m), the headline dense configuration
+# (l = m + 4, the sketch size Section 4 suggests) and the precision-at-scale configuration
+# (A 4.3 GB, l = 2m + 32, up to 256 right-hand sides per call; also run at k = 1 and 16).
 WORKLOADS = {
     "dense_64x2048": Workload("dense_64x2048_kappa1e8_k16", 64, 2048, 1e-8, 16, 256, 1, 11, 21),
     "dense_512x65536": Workload("dense_512x65536_kappa1e10_k64", 512, 65536, 1e-10, 64, 516, 2, 12, 22),
+    "dense_2048x262144": Workload("dense_2048x262144_kappa1e12_k256", 2048, 262144, 1e-12, 256, 4128, 3, 13, 23),
 }
