@@ -119,6 +119,16 @@ typedef struct {
                             satisfies ||dh|| <= refine_tol max(||h||, ||b|| / ||A||_F)
                             (Remark 4.3), at most refine_passes passes; 0 (default) runs
                             exactly refine_passes                                         */
+    int scalable;        /* 1: reserve what rtproj_set_scaling needs (the float64 form keeps
+                            A diag(d) in the workspace; the mixed form forms it in the Gram
+                            matrix's buffer and needs nothing more). Default 0.             */
+    int async;           /* 1: rtproj_create and rtproj_precondition do not synchronize; the
+                            conditions they would return (non-finite A, ERANK, ENOTSPD,
+                            ETIMEOUT) stay latched in the device status word, which
+                            rtproj_get_info reports, and the apply runs regardless. Lets a
+                            serving loop overlap consecutive steps and lets precondition and
+                            the apply be captured in a CUDA graph (with refine_tol = 0).
+                            Default 0.                                                    */
 } rtproj_opts;
 
 /* Phases timed when opts.timing is set (indices into rtproj_get_timings' arrays). */
@@ -177,7 +187,7 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, 
    matrix X = P^{-1} A A^* P^{-*} (Eq. 14, steps a-e) factored by Cholesky in place of
    the explicit inverse Y = X^{-1} of Eq. 16. Synchronizes the stream once and returns
    the latched device status (RTPROJ_ERANK, RTPROJ_ENOTSPD, RTPROJ_ENONFINITE). */
-rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l);
+rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l);   /* see opts.async */
 
 /* Null-space projection (Eq. 11; the seven steps of Section 4, then b - b~):
    Z = rows of Zb for the k rows of B (k <= k_max). Z may alias B exactly
@@ -242,6 +252,15 @@ size_t rtproj_grad_workspace_bytes(rtproj_t h, int64_t k);
 rtproj_status rtproj_grad_A(rtproj_t h, int64_t k, const void* H, int64_t ldh, const void* Y, int64_t ldy,
                             const void* W, int64_t ldw, const void* Zb, int64_t ldz, void* dA, int64_t ldda,
                             void* workspace, size_t ws_bytes);
+
+/* Interior-point-style column scaling: from now on the handle's matrix is A diag(d), with
+   A the matrix given to rtproj_create (still borrowed) and d a DEVICE array of n float64
+   scalings (NULL restores A). The scaled matrix is formed on the device (each entry's
+   product rounded once), its Frobenius norm recomputed and, in the mixed form, sliced
+   again into both digit layouts; the preconditioner is dropped (call rtproj_precondition
+   next). Needs opts.scalable = 1 at create. Synchronizes like rtproj_create unless
+   opts.async; d is read on the handle's stream. */
+rtproj_status rtproj_set_scaling(rtproj_t h, const double* d);
 
 /* Replaces the handle's spin_limit_cycles (see rtproj_opts) for later calls; cycles >= 1. */
 rtproj_status rtproj_set_spin_limit(rtproj_t h, long long cycles);

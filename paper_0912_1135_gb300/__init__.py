@@ -42,7 +42,7 @@ class Opts(ctypes.Structure):
         ("gram_slices", ctypes.c_int), ("gram2_slices", ctypes.c_int), ("apply_slices", ctypes.c_int),
         ("resid_slices", ctypes.c_int), ("refine_passes", ctypes.c_int), ("timing", ctypes.c_int),
         ("rank_tol", ctypes.c_double), ("dtype", ctypes.c_int), ("spin_limit_cycles", ctypes.c_longlong),
-        ("refine_tol", ctypes.c_double),
+        ("refine_tol", ctypes.c_double), ("scalable", ctypes.c_int), ("async_", ctypes.c_int),   # async_: opts.async
     ]
 
 
@@ -81,6 +81,7 @@ EXPORTS = {
     "rtproj_sketch_noalloc": (ctypes.c_int, [_P, _I64, _I64, _I64, ctypes.c_uint64, _I64, ctypes.c_int, _P, _I64, _P]),
     "rtproj_generate_omega": (ctypes.c_int, [ctypes.c_uint64, _I64, _I64, ctypes.c_int, _P, _I64, _P]),
     "rtproj_set_spin_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "rtproj_set_scaling": (ctypes.c_int, [_P, _P]),
     "rtproj_grad_workspace_bytes": (ctypes.c_size_t, [_P, _I64]),
     "rtproj_grad_A": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, ctypes.c_size_t]),
 }
@@ -231,6 +232,18 @@ class Projector:
 
     def clear_status(self):
         _check(load_library().rtproj_clear_status(self._h), "rtproj_clear_status")
+
+    def set_scaling(self, d: torch.Tensor | None):
+        """The handle's matrix becomes A diag(d) (d: n float64 entries on the device; None
+        restores A); the preconditioner is dropped. Needs scalable=1 at construction."""
+        if d is not None and not (isinstance(d, torch.Tensor) and d.dtype == torch.float64 and d.device == self.device
+                                  and d.dim() == 1 and d.shape[0] == self.n and d.stride(0) == 1):
+            raise TypeError(f"d must be a contiguous float64 vector of {self.n} entries on {self.device}")
+        cur = self._enter(*(() if d is None else (d,)))
+        with torch.cuda.device(self.device):
+            _check(load_library().rtproj_set_scaling(self._h, _dev_ptr(d) if d is not None else None),
+                   "rtproj_set_scaling")
+        self._leave(cur)
 
     def set_spin_limit(self, cycles: int):
         """Bound (SM clock cycles) on each grid-exchange wait of the QR and the Cholesky."""

@@ -22,6 +22,19 @@ __global__ void widen_kernel(const float* __restrict__ src, int64_t lds, int row
     }
 }
 
+// dst = src diag(d) (d optional), widened to float64
+template <typename T>
+__global__ void form_rows_kernel(const T* __restrict__ src, int64_t lds, int rows, int cols, const double* __restrict__ d,
+                                 double* __restrict__ dst, int64_t ldd) {
+    const int64_t total = (int64_t)rows * cols;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = idx / cols, c = idx % cols;
+        const double x = (double)src[r * lds + c];
+        dst[r * ldd + c] = d ? x * d[c] : x;
+    }
+}
+
 template <typename T>
 __global__ void store_rows_kernel(const double* __restrict__ X, int64_t ldx, const double* __restrict__ B, int64_t ldb,
                                   T* __restrict__ dst, int64_t ldd, int rows, int cols, int sub) {
@@ -158,6 +171,18 @@ unsigned grid_for(int64_t total) {
 cudaError_t widen_rows(const float* src, int64_t lds, int rows, int cols, double* dst, int64_t ldd, cudaStream_t s) {
     if (rows <= 0 || cols <= 0) return cudaSuccess;
     widen_kernel<<<grid_for((int64_t)rows * cols), BT, 0, s>>>(src, lds, rows, cols, dst, ldd);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t form_rows(const void* src, int dt, int64_t lds, int rows, int cols, const double* d, double* dst, int64_t ldd,
+                      cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
+    const unsigned g = grid_for((int64_t)rows * cols);
+    if (dt == RTPROJ_F32)
+        form_rows_kernel<float><<<g, BT, 0, s>>>((const float*)src, lds, rows, cols, d, dst, ldd);
+    else
+        form_rows_kernel<double><<<g, BT, 0, s>>>((const double*)src, lds, rows, cols, d, dst, ldd);
     note_launch();
     return cudaGetLastError();
 }

@@ -182,6 +182,8 @@ rtproj_status mixed_prepare_a(rtproj_ctx* h) {
     phase_end(h, RTPROJ_PHASE_SLICE);
     // A is read only here in this form: remember whether it held non-finite entries, so
     // that precondition reports it without reading A again
+    MX_CHECK(cudaMemcpyAsync(h->a_status_dev, h->status, sizeof(int), cudaMemcpyDeviceToDevice, h->stream));
+    if (h->opts.async) return RTPROJ_OK;   // precondition folds a_status_dev into its status
     MX_CHECK(cudaMemcpyAsync(&h->a_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     MX_CHECK(cudaStreamSynchronize(h->stream));
     return RTPROJ_OK;

@@ -18,8 +18,10 @@
 // that: the refinement pass (Remark 4.3) makes the result exact whatever the
 // preconditioner's own rounding. The plain float64 form keeps the float64 QR.
 //
-// The pivot rule is the persistent kernel's (Businger-Golub with every norm recomputed
-// each step, largest squared norm and lowest index on ties), on float-float norms.
+// The pivot rule is Businger-Golub (largest remaining squared norm, lowest index on ties)
+// on float-float norms that are downdated from step to step and recomputed exactly when
+// the downdate has cancelled (as LAPACK does); the float64 kernel recomputes every norm
+// every step instead, so near-ties can resolve differently.
 // S^* is scaled by a power of two (exact) so that its largest entry lies in [1/2, 1);
 // if a column's squared norm then falls below 2^-90 (float-float would lose the digits
 // of a trailing norm near float's underflow), the kernel leaves R and perm untouched and
@@ -34,7 +36,7 @@ namespace rtp {
 namespace {
 
 constexpr int CQ_CTAS = 16;
-constexpr int CQ_THREADS = 256;
+constexpr int CQ_THREADS = 512;
 constexpr int CQ_WARPS = CQ_THREADS / 32;
 constexpr int CQ_MAXC = 64;
 
@@ -95,6 +97,51 @@ __device__ __forceinline__ ff ff_warp_sum(ff v) {
     return v;
 }
 
+// Warp-wide maximum of (value, index): largest value, lowest index on ties; an index of m
+// marks an empty entry. Every lane receives the result.
+__device__ __forceinline__ void cand_reduce(ff& best, int& bi, int m) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ff ob;
+        ob.hi = __shfl_xor_sync(0xffffffffu, best.hi, o);
+        ob.lo = __shfl_xor_sync(0xffffffffu, best.lo, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi < m && (bi == m || ff_gt(ob, best) || (ob.hi == best.hi && ob.lo == best.lo && oi < bi))) {
+            best = ob;
+            bi = oi;
+        }
+    }
+}
+
+// After the update of step j, column c (rows j .. l-1 at c[0 .. len)) loses row j from its
+// trailing norm: nsq <- nsq - c_j^2, or the exact sum over rows j+1 .. l-1 when the
+// downdate has cancelled below 2^-20 of the last exact value nsq_ref (then nsq_ref moves).
+__device__ __forceinline__ void downdate_norm(const float2* c, int len, int q, int lane, float2* nsq, float2* nsq_ref) {
+    const ff y = {c[0].x, c[0].y};
+    ff ns = ff_add({nsq[q].x, nsq[q].y}, ff_neg(ff_mul(y, y)));
+    const bool exact = !(ns.hi > nsq_ref[q].x * 0x1p-20f);
+    if (exact) {
+        ff s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+        int i = 1 + lane;
+        for (; i + 32 < len; i += 64) {
+            const ff x0 = {c[i].x, c[i].y}, x1 = {c[i + 32].x, c[i + 32].y};
+            s0 = ff_add(s0, ff_mul(x0, x0));
+            s1 = ff_add(s1, ff_mul(x1, x1));
+        }
+        if (i < len) {
+            const ff x0 = {c[i].x, c[i].y};
+            s0 = ff_add(s0, ff_mul(x0, x0));
+        }
+        ns = ff_warp_sum(ff_add(s0, s1));
+    }
+    __syncwarp();
+    if (lane == 0) {
+        nsq[q] = make_float2(ns.hi, ns.lo);
+        if (exact) nsq_ref[q] = make_float2(ns.hi, ns.lo);
+    }
+    __syncwarp();
+}
+
 struct CqrDev {
     const double* S;
     int m, l;
@@ -112,7 +159,8 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
     float2* v = csm + (size_t)cpc * l;           // l (rows j .. l-1 of the reflector at offset 0)
     __shared__ float2 cand_val[2];
     __shared__ int cand_idx[2];
-    __shared__ float2 nsq[CQ_MAXC];
+    __shared__ float2 nsq[CQ_MAXC];          // squared norm of rows j .. l-1 before step j
+    __shared__ float2 nsq_ref[CQ_MAXC];      // its value at the last exact computation
     __shared__ float2 alphaq[CQ_MAXC];
     __shared__ int posq[CQ_MAXC];
     __shared__ unsigned long long max_bits_s;
@@ -167,6 +215,7 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
         s = ff_warp_sum(s);
         if (lane == 0) {
             nsq[q] = make_float2(s.hi, s.lo);
+            nsq_ref[q] = make_float2(s.hi, s.lo);
             posq[q] = -1;
             if (!(s.hi >= 0x1p-90f)) atomicOr(&bad_s, 1);
         }
@@ -201,17 +250,7 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
             const int ci = *cluster.map_shared_rank(&cand_idx[par], lane);
             if (ci < m) { best = {cv.x, cv.y}; bi = ci; }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            ff ob;
-            ob.hi = __shfl_xor_sync(0xffffffffu, best.hi, o);
-            ob.lo = __shfl_xor_sync(0xffffffffu, best.lo, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (oi < m && (bi == m || ff_gt(ob, best) || (ob.hi == best.hi && ob.lo == best.lo && oi < bi))) {
-                best = ob;
-                bi = oi;
-            }
-        }
+        cand_reduce(best, bi, m);
         const int piv = bi < m ? bi : 0;   // some CTA holds an active column while j < m
         const int owner = piv / cpc, qo = piv - owner * cpc;
         const float2* src = cluster.map_shared_rank(cols + (size_t)qo * l, owner);
@@ -235,35 +274,68 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
         }
         __syncthreads();
         const int len = l - j;
-        // each active column: w = beta v^* c, c <- c - w v, squared norm of rows j+1 .. l-1
-        for (int q = warp; q < nc; q += CQ_WARPS) {
-            if (posq[q] >= 0) continue;
-            float2* c = cols + (size_t)q * l + j;
-            ff s = {0.f, 0.f};
-            for (int i = lane; i < len; i += 32) {
-                const float2 a = v[i], x = c[i];
-                s = ff_add(s, ff_mul({a.x, a.y}, {x.x, x.y}));
+        // each active column c: w = beta v^* c, c <- c - w v. A warp takes two columns at a
+        // time with two partial sums each (four independent float-float chains), then
+        // downdates the squared norm: ||c[j+1..]||^2 = ||c[j..]||^2 - c_j^2, recomputed
+        // exactly when it falls below 2^-20 of its last exact value (the downdate would
+        // have lost more than 20 of its 48 bits).
+        for (int q0 = warp * 2; q0 < nc; q0 += 2 * CQ_WARPS) {
+            const int qa = q0, qb = q0 + 1;
+            const bool da = posq[qa] < 0;
+            const bool db = qb < nc && posq[qb] < 0;
+            if (!da && !db) continue;
+            float2* ca = cols + (size_t)qa * l + j;
+            float2* cb = cols + (size_t)(db ? qb : qa) * l + j;
+            ff sa0 = {0.f, 0.f}, sa1 = {0.f, 0.f}, sb0 = {0.f, 0.f}, sb1 = {0.f, 0.f};
+            int i = lane;
+            for (; i + 32 < len; i += 64) {
+                const float2 a0 = v[i], a1 = v[i + 32];
+                const float2 x0a = ca[i], x1a = ca[i + 32], x0b = cb[i], x1b = cb[i + 32];
+                sa0 = ff_add(sa0, ff_mul({a0.x, a0.y}, {x0a.x, x0a.y}));
+                sa1 = ff_add(sa1, ff_mul({a1.x, a1.y}, {x1a.x, x1a.y}));
+                sb0 = ff_add(sb0, ff_mul({a0.x, a0.y}, {x0b.x, x0b.y}));
+                sb1 = ff_add(sb1, ff_mul({a1.x, a1.y}, {x1b.x, x1b.y}));
             }
-            s = ff_warp_sum(s);
-            const ff w = ff_mul(s, beta);
-            ff ns = {0.f, 0.f};
-            for (int i = lane; i < len; i += 32) {
-                const float2 a = v[i], x = c[i];
-                const ff y = ff_add({x.x, x.y}, ff_neg(ff_mul(w, {a.x, a.y})));
-                c[i] = make_float2(y.hi, y.lo);
-                if (i > 0) ns = ff_add(ns, ff_mul(y, y));
+            if (i < len) {
+                const float2 a0 = v[i], x0a = ca[i], x0b = cb[i];
+                sa0 = ff_add(sa0, ff_mul({a0.x, a0.y}, {x0a.x, x0a.y}));
+                sb0 = ff_add(sb0, ff_mul({a0.x, a0.y}, {x0b.x, x0b.y}));
             }
-            ns = ff_warp_sum(ns);
-            if (lane == 0) nsq[q] = make_float2(ns.hi, ns.lo);
+            const ff wa = ff_mul(ff_warp_sum(ff_add(sa0, sa1)), beta);
+            const ff wb = ff_mul(ff_warp_sum(ff_add(sb0, sb1)), beta);
+            for (i = lane; i < len; i += 32) {
+                const float2 a = v[i];
+                const ff af = {a.x, a.y};
+                if (da) {
+                    const float2 x = ca[i];
+                    const ff y = ff_add({x.x, x.y}, ff_neg(ff_mul(wa, af)));
+                    ca[i] = make_float2(y.hi, y.lo);
+                }
+                if (db) {
+                    const float2 x = cb[i];
+                    const ff y = ff_add({x.x, x.y}, ff_neg(ff_mul(wb, af)));
+                    cb[i] = make_float2(y.hi, y.lo);
+                }
+            }
+            __syncwarp();
+            if (da) downdate_norm(ca, len, qa, lane, nsq, nsq_ref);
+            if (db) downdate_norm(cb, len, qb, lane, nsq, nsq_ref);
         }
         __syncthreads();
-        // this CTA's candidate for step j+1
-        if (t == 0) {
-            int bq = -1;
-            for (int q = 0; q < nc; ++q)
-                if (posq[q] < 0 && (bq < 0 || ff_gt({nsq[q].x, nsq[q].y}, {nsq[bq].x, nsq[bq].y}))) bq = q;
-            cand_val[par ^ 1] = bq >= 0 ? nsq[bq] : make_float2(-1.f, 0.f);
-            cand_idx[par ^ 1] = bq >= 0 ? c0 + bq : m;
+        // this CTA's candidate for step j+1 (warp 0: two columns per lane, then shuffles)
+        if (warp == 0) {
+            ff cv = {-1.f, 0.f};
+            int ci = m;
+            for (int q = lane; q < nc; q += 32)
+                if (posq[q] < 0) {
+                    const ff x = {nsq[q].x, nsq[q].y};
+                    if (ci == m || ff_gt(x, cv)) { cv = x; ci = c0 + q; }
+                }
+            cand_reduce(cv, ci, m);
+            if (lane == 0) {
+                cand_val[par ^ 1] = make_float2(cv.hi, cv.lo);
+                cand_idx[par ^ 1] = ci;
+            }
         }
     }
     // R[:, pos] = rows 0 .. pos-1 of the retired column, alpha on the diagonal (scaled back)

@@ -566,7 +566,13 @@ cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* sta
             cudaError_t e = cudaMemsetAsync(p.counter, 0, 2 * sizeof(unsigned int), s);
             if (e != cudaSuccess) return e;
             void* args[] = {&p};
-            e = cudaLaunchCooperativeKernel((const void*)chol_persistent_kernel, dim3(sms), dim3(CHP_THREADS), args, 0, s);
+            // a grid sized to the work: about two trailing tiles per CTA for small matrices
+            // (so that a batch of small instances does not hold the whole GPU), one CTA per
+            // SM from m = 256 up
+            const int nt = (m + CHP_TILE - 1) / CHP_TILE;
+            const int G = std::max(2, std::min(sms * per_sm, std::min(sms, nt * (nt + 1) / 4)));
+            e = cudaLaunchCooperativeKernel((const void*)chol_persistent_kernel, dim3(m >= 256 ? sms : G),
+                                            dim3(CHP_THREADS), args, 0, s);
             note_launch();
             if (e == cudaSuccess) return zero_upper(X, m, s);
             cudaGetLastError();   // clear and fall back

@@ -788,7 +788,8 @@ __device__ __forceinline__ bool issue_kblock(Ring& ra, uint32_t a_lo0, uint32_t 
 // Configurations with a compile-time issue path (digit planes of A, levels, B rows per
 // level); issue_cfg is the position in this list plus one.
 struct IssueCfg { int sa, terms, tn; };
-constexpr IssueCfg kIssueCfgs[] = {{7, 7, 32}, {9, 9, 32}, {3, 3, 64}, {1, 5, 64}, {5, 5, 64}, {7, 7, 64}};
+constexpr IssueCfg kIssueCfgs[] = {{7, 7, 32}, {9, 9, 32}, {3, 3, 64}, {1, 5, 64}, {5, 5, 64}, {7, 7, 64},
+                                   {2, 5, 64}};   // the last: the Gaussian sketch (two G planes, five of A)
 
 // Running record of max |v| for the row exponent, in two integer operations per value:
 // the largest sign-cleared upper word (sign, exponent field, top 20 mantissa bits) and the
@@ -1063,7 +1064,8 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     case 3: ok = issue_kblock<3, 3, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
                     case 4: ok = issue_kblock<1, 5, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
                     case 5: ok = issue_kblock<5, 5, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
-                    default: ok = issue_kblock<7, 7, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    case 6: ok = issue_kblock<7, 7, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
+                    default: ok = issue_kblock<2, 5, 64>(ra, a_lo0, b_lo, desc_hi, dbase, acc0, fullA, emptyA, abort_v, p); break;
                     }
                 } else
                 for (int pa0 = 0; pa0 < p.sa; pa0 += A_PPS) {

@@ -95,6 +95,8 @@ bool valid_opts(const rtproj_opts& o) {
         !ok(o.resid_slices))
         return false;
     if (o.refine_passes < 0 || o.refine_passes > 8) return false;
+    if (o.async != 0 && o.async != 1) return false;
+    if (o.scalable != 0 && o.scalable != 1) return false;
     if (o.dtype != RTPROJ_F64 && o.dtype != RTPROJ_F32) return false;
     if (o.spin_limit_cycles < 1) return false;
     if (!(o.refine_tol >= 0.0)) return false;
@@ -125,7 +127,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtp
     // float32 at the ABI: A widened for the float64 form (the mixed form widens into W,
     // which it needs only after A has been sliced), right-hand sides widened per apply
     const bool f32 = o.dtype == RTPROJ_F32;
-    L.A64 = take(f32 && o.mode == RTPROJ_PLAIN_FP64 ? (size_t)m * n * 8 : 0);
+    L.A64 = take((f32 || o.scalable) && o.mode == RTPROJ_PLAIN_FP64 ? (size_t)m * n * 8 : 0);
     L.B64 = take(f32 ? (size_t)k_max * n * 8 : 0);
     L.normA = take(8);
     L.norm_part = take((size_t)norm_parts() * 8);
@@ -138,6 +140,26 @@ Layout make_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtp
 }
 
 rtproj_status cuda_status(cudaError_t e) { return e == cudaSuccess ? RTPROJ_OK : RTPROJ_ECUDA; }
+
+// The matrix every product reads, as float64: the caller's float64 A itself, or -- for a
+// float32 A or a column scaling d -- A (diag(d)) formed once into W's region (the mixed
+// form needs A only while slicing it, before any Gram product) or into A64 (the float64
+// form reads it at every product). Then ||A||_F.
+rtproj_status form_a(rtproj_ctx* h, const double* d) {
+    const int m = (int)h->m, n = (int)h->n;
+    h->scaled = d != nullptr;
+    if (h->dtype == RTPROJ_F32 || d) {
+        double* wide = h->opts.mode == RTPROJ_MIXED_REFINED ? h->W : h->A64;
+        if (form_rows(h->A_user, h->dtype, h->lda_user, m, n, d, wide, n, h->stream) != cudaSuccess) return RTPROJ_ECUDA;
+        h->A = wide;
+        h->lda = n;
+    } else {
+        h->A = (const double*)h->A_user;
+        h->lda = h->lda_user;
+    }
+    if (frobenius(h->A, h->lda, m, n, h->norm_part, h->normA, h->stream) != cudaSuccess) return RTPROJ_ECUDA;
+    return RTPROJ_OK;
+}
 
 #define RT_CHECK(expr)                                  \
     do {                                                \
@@ -287,6 +309,8 @@ void rtproj_default_opts(rtproj_opts* o) {
     o->dtype = RTPROJ_F64;
     o->spin_limit_cycles = 4000000000ll;
     o->refine_tol = 0.0;
+    o->async = 0;
+    o->scalable = 0;
 }
 
 size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts* opts) {
@@ -314,13 +338,14 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, 
     rtproj_ctx* h = new (std::nothrow) rtproj_ctx();
     if (!h) return RTPROJ_ENOMEM;
     h->m = m; h->n = n; h->lda = lda; h->l_max = l_max; h->k_max = k_max;
-    h->A_user = A; h->ws = (char*)workspace; h->ws_bytes = ws_bytes;
+    h->A_user = A; h->lda_user = lda; h->ws = (char*)workspace; h->ws_bytes = ws_bytes;
     h->stream = (cudaStream_t)stream;
     h->opts = o;
     h->dtype = o.dtype;
     h->spin_limit = o.spin_limit_cycles;
     char* b = h->ws;
     h->status = (int*)(b + L.status);
+    h->a_status_dev = h->status + 8;
     h->S = (double*)(b + L.S);
     h->qr_work = (double*)(b + L.qr_work);
     h->perm = (int32_t*)(b + L.perm);
@@ -344,20 +369,7 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, 
     h->norm_part = (double*)(b + L.norm_part);
     h->bnorm = (double*)(b + L.bnorm);
     h->stats = (unsigned long long*)(b + L.stats);
-    // every product reads A as float64: a float32 A is widened once, here (exactly)
-    if (o.dtype == RTPROJ_F32) {
-        double* wide = o.mode == RTPROJ_MIXED_REFINED ? h->W : h->A64;
-        if (widen_rows((const float*)A, lda, (int)m, (int)n, wide, n, h->stream) != cudaSuccess) {
-            delete h;
-            return RTPROJ_ECUDA;
-        }
-        h->A = wide;
-        h->lda = n;
-    } else {
-        h->A = (const double*)A;
-    }
-    if (frobenius(h->A, h->lda, (int)m, (int)n, h->norm_part, h->normA, h->stream) != cudaSuccess ||
-        cudaMemsetAsync(h->stats, 0, 16, h->stream) != cudaSuccess) {
+    if (form_a(h, nullptr) != RTPROJ_OK || cudaMemsetAsync(h->stats, 0, 16, h->stream) != cudaSuccess) {
         delete h;
         return RTPROJ_ECUDA;
     }
@@ -390,6 +402,19 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, 
     return RTPROJ_OK;
 }
 
+rtproj_status rtproj_set_scaling(rtproj_t h, const double* d) {
+    if (!h) return RTPROJ_EINVAL;
+    if (!h->opts.scalable) return RTPROJ_EUNSUPPORTED;
+    h->preconditioned = 0;
+    RT_CHECK(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream));
+    rtproj_status st = form_a(h, d);
+    if (st == RTPROJ_OK && h->opts.mode == RTPROJ_MIXED_REFINED) {
+        h->a_status = RTPROJ_OK;
+        st = mixed_prepare_a(h);
+    }
+    return st;
+}
+
 rtproj_status rtproj_sketch(rtproj_t h, uint64_t seed, int64_t l, double* S, int64_t lds) {
     if (!h || !S || l < h->m || l > h->l_max || lds < l) return RTPROJ_EINVAL;
     rtproj_status st = h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_sketch(h, seed, l, S, lds)
@@ -406,10 +431,13 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     h->preconditioned = 0;
     h->l = l;
     RT_CHECK(cudaEventRecord(h->ev0, s));
-    RT_CHECK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
     if (h->opts.mode == RTPROJ_MIXED_REFINED) {
         if (h->a_status != RTPROJ_OK) return (rtproj_status)h->a_status;   // found when A was sliced
+        // the status word starts from what slicing A found (non-finite entries), so that the
+        // asynchronous mode still reports it
+        RT_CHECK(cudaMemcpyAsync(h->status, h->a_status_dev, sizeof(int), cudaMemcpyDeviceToDevice, s));
     } else {
+        RT_CHECK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
         RT_CHECK(check_finite(h->A, h->lda, m, (int)h->n, h->status, s));
     }
     // 1. S = A G (Eq. 12)
@@ -456,6 +484,10 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
         if (st != RTPROJ_OK) return st;
     }
     RT_CHECK(cudaEventRecord(h->ev1, s));
+    if (h->opts.async) {
+        h->preconditioned = 1;   // conditions found on the device stay latched for rtproj_get_info
+        return RTPROJ_OK;
+    }
     RT_CHECK(cudaStreamSynchronize(s));
     int dev_status = 0;
     RT_CHECK(cudaMemcpy(&dev_status, h->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -531,6 +563,12 @@ rtproj_status rtproj_get_info(rtproj_t h, rtproj_info* info) {
     info->status = st;
     info->preconditioned = h->preconditioned;
     info->m = h->m; info->n = h->n; info->l = h->l;
+    if (h->opts.async && h->preconditioned) {
+        // the asynchronous precondition did not wait for its events; they are complete now
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev0, h->ev1) == cudaSuccess) h->ms_pre = ms;
+        else cudaGetLastError();
+    }
     info->ms_precondition = h->ms_pre;
     if (h->l > 0) {
         const int m = (int)h->m;

@@ -241,6 +241,11 @@ rtproj_status middle_fp64(rtproj_ctx* h, const double* c, double* out, int k);
 namespace rtp {
 // dst (rows x cols, ld ldd, float64) = src (float32, ld lds), exactly.
 cudaError_t widen_rows(const float* src, int64_t lds, int rows, int cols, double* dst, int64_t ldd, cudaStream_t s);
+// dst (rows x cols float64, ld ldd) = src diag(d) (d optional, n entries), src of element
+// type dt (ld lds): the matrix the products read, widened and scaled exactly... up to the
+// one rounding of each product x d_c.
+cudaError_t form_rows(const void* src, int dt, int64_t lds, int rows, int cols, const double* d, double* dst, int64_t ldd,
+                      cudaStream_t s);
 // dst (rows x cols, element type dt, ld ldd) = B - X (sub) or X; X and B float64.
 cudaError_t store_rows(const double* X, int64_t ldx, const double* B, int64_t ldb, void* dst, int64_t ldd, int rows,
                        int cols, int sub, int dt, cudaStream_t s);
@@ -308,6 +313,8 @@ struct rtproj_ctx {
     // boundary (k_boundary.cu)
     int dtype = RTPROJ_F64;      // element type of A, B and the outputs at the ABI
     const void* A_user = nullptr;
+    int64_t lda_user = 0;
+    bool scaled = false;         // the products read A diag(d) (rtproj_set_scaling)
     double* A64 = nullptr;       // float32 A widened (float64 form; the mixed form widens into W)
     double* B64 = nullptr;       // k_max x n: float32 right-hand sides widened
     double* normA = nullptr;     // ||A||_F (device scalar)
@@ -322,6 +329,7 @@ struct rtproj_ctx {
     int64_t l = 0;
     int preconditioned = 0;
     int a_status = 0;            // mixed form: status of slicing A at create (non-finite entries)
+    int* a_status_dev = nullptr; // the same, kept on the device (asynchronous mode)
     float ms_pre = 0.f;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };

@@ -1,9 +1,11 @@
 """Precision at scale: A 2048 x 262144 float64 (4.3 GB), sigma log-spaced over [1e-12, 1],
 sketch size l = 2m + 32 = 4128, applies at k = 1, 16 and 256 right-hand sides.
 
-At kappa = 1e12 the refinement's residual products need ten digits (2^-80 kappa ~ 1e-12)
-and the correction contracts by about 2^-56 kappa per pass, so refinement runs to a
-tolerance (Remark 4.3) instead of one fixed pass. The exact projection of a Haar matrix of
+At kappa = 1e12 the sketch needs six digits so that its own error (2^-48 relative) stays
+below the smallest singular value (1e-12 relative), the rank test's threshold must sit below
+1/kappa, the refinement's residual products need ten digits (2^-80 kappa ~ 1e-12), and the
+correction contracts by about 2^-56 kappa per pass, so refinement runs to a tolerance
+(Remark 4.3) instead of one fixed pass. The exact projection of a Haar matrix of
 this size is out of the oracle's reach, so Z is checked against the closed form of the
 paper's own family (Eqs. 20-21) at the same size and kappa (exact at any kappa), and on the
 Haar matrix through ||A z|| accumulated in double-double (oracle.exact.exact_residual) on
@@ -18,7 +20,9 @@ from tests.gpu_common import assert_rows_close, rt_module, to_dev, torch_cuda
 pytestmark = pytest.mark.gpu
 
 KEY = "dense_2048x262144"
-OPTS = dict(resid_slices=10, refine_passes=4, refine_tol=1e-11)
+# six sketch digits (2^-48 relative error, below sigma_min / sigma_max = 1e-12), a rank
+# threshold below 1/kappa, ten residual digits, refinement to a tolerance
+OPTS = dict(sketch_slices=6, resid_slices=10, refine_passes=4, refine_tol=1e-11, rank_tol=1e-14)
 Z_TOL = 1e-10
 RESID_TOL = 1e-12
 

@@ -52,6 +52,7 @@ def test_randomized_method_errors_against_tables_2_and_4(kappa, golden_dir):
     m, n, l = 200, 100000, 204
     d64, e64 = study_row(rt, torch, m, n, l, kappa, "fp64")
     assert d64 <= 10 * paper_delta and e64 <= 10 * paper_eps, (d64, e64)
-    opts = dict(resid_slices=10, refine_passes=4, refine_tol=1e-11) if kappa > 1e10 else {}
+    opts = dict(sketch_slices=6, resid_slices=10, refine_passes=4, refine_tol=1e-11, rank_tol=1e-14) \
+        if kappa > 1e10 else {}
     dmx, emx = study_row(rt, torch, m, n, l, kappa, "mixed", **opts)
     assert dmx <= same["delta_over_kappa"] and emx <= same["epsilon_over_kappa"], (dmx, emx, same)
