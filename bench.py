@@ -630,7 +630,8 @@ def study_accuracy(args):
     out = []
     for (m, n, l, kappa) in rows:
         row = {"m": m, "n": n, "l": l, "kappa": kappa}
-        mixed_kw = dict(WORKLOAD_OPTS["dense_2048x262144"]) if kappa > 1e10 else {}
+        mixed_kw = dict(WORKLOAD_OPTS["dense_2048x262144"]) if kappa > 1e10 else dict(refine_passes=4,
+                                                                                          refine_tol=1e-12)
         row["mixed"] = _family_errors(torch, rt, dev, m, n, l, kappa, "mixed", **mixed_kw)
         row["fp64"] = _family_errors(torch, rt, dev, m, n, l, kappa, "fp64")
         ref = printed.get((m, n, l, kappa)) or (printed4.get(kappa) if n == 100000 else None)

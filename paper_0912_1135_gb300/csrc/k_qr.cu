@@ -242,12 +242,19 @@ __device__ __forceinline__ void publish_best(const PqrDev& p, int b, int G, int 
     red_release_add(p.counter, 1u);
 }
 
+// GLOBAL_COLS: the columns stay in S in global memory (they do not fit in shared memory,
+// e.g. 2048 x 4128): each CTA updates its own columns in place, readers take the pivot
+// column straight from S through L2 (no staging copies), and the retired column's diagonal
+// entry is kept in shared memory so that no reader sees a half-written pivot column.
+template <bool GLOBAL_COLS>
 __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) {
     extern __shared__ double smem_d[];
     const int l = p.l, m = p.m, cpc = p.cpc;
-    double* cols = smem_d;                 // cpc x l
-    double* v = cols + (size_t)cpc * l;    // l
+    const int64_t cs = GLOBAL_COLS ? p.lds : (int64_t)l;                        // column stride
+    double* cols = GLOBAL_COLS ? p.S + (int64_t)blockIdx.x * cpc * p.lds : smem_d;  // cpc x l
+    double* v = GLOBAL_COLS ? smem_d : cols + (size_t)cpc * l;               // l
     __shared__ double nsq[PQ_MAXC];        // squared norm of rows j+1 .. l-1 (exact, this step)
+    __shared__ double alphaq[PQ_MAXC];     // GLOBAL_COLS: the retired column's diagonal entry
     __shared__ int posq[PQ_MAXC];          // step at which the column was retired, -1 while active
     __shared__ unsigned long long redb[2 * PQ_WARPS];
     __shared__ int redi[2 * PQ_WARPS];
@@ -258,15 +265,16 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     const int nc = max(0, min(cpc, m - c0));
     const size_t slot_par = (size_t)G * cpc * l;   // doubles per parity buffer
 
-    for (int q = 0; q < nc; ++q)
-        for (int i = t; i < l; i += PQ_THREADS) {
-            const double x = p.S[(int64_t)(c0 + q) * p.lds + i];
-            cols[(size_t)q * l + i] = x;
-            p.slots[((size_t)b * cpc + q) * l + i] = x;           // step 0's staging copy
-        }
+    if (!GLOBAL_COLS)
+        for (int q = 0; q < nc; ++q)
+            for (int i = t; i < l; i += PQ_THREADS) {
+                const double x = p.S[(int64_t)(c0 + q) * p.lds + i];
+                cols[(size_t)q * l + i] = x;
+                p.slots[((size_t)b * cpc + q) * l + i] = x;           // step 0's staging copy
+            }
     __syncthreads();
     for (int q = warp; q < nc; q += PQ_WARPS) {
-        const double* c = cols + (size_t)q * l;
+        const double* c = cols + (size_t)q * cs;
         double s0 = 0.0, s1 = 0.0;
         int i = lane;
         for (; i + 32 < l; i += 64) {
@@ -316,8 +324,9 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         if (ii >= m) { alive = false; break; }             // cannot happen while columns remain
         const int piv = ii;
         const double nsq_piv = __longlong_as_double((long long)bb);
-        // 2. the reflector from the pivot column's staging slot (rows j .. l-1)
-        const double* slot = p.slots + (size_t)par * slot_par + (size_t)piv * l;
+        // 2. the reflector from the pivot column's staging slot (rows j .. l-1), or from the
+        //    pivot column itself when the columns stay in global memory
+        const double* slot = GLOBAL_COLS ? p.S + (int64_t)piv * p.lds : p.slots + (size_t)par * slot_par + (size_t)piv * l;
         // the slot's loads are issued before the scalar chain so that their latency and the
         // square root and division overlap (PQ_VLOAD entries per thread in registers)
         double vr[PQ_VLOAD];
@@ -341,7 +350,8 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         for (int i = j + t + PQ_VLOAD * PQ_THREADS; i < l; i += PQ_THREADS) v[i - j] = __ldcg(slot + i);
         if (t == 0 && piv >= c0 && piv < c0 + nc) {
             const int q = piv - c0;
-            cols[(size_t)q * l + j] = alpha;
+            if (GLOBAL_COLS) alphaq[q] = alpha;
+            else cols[(size_t)q * l + j] = alpha;
             posq[q] = j;
             p.perm[j] = piv;
         }
@@ -352,7 +362,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         double* next = p.slots + (size_t)(par ^ 1) * slot_par;
         for (int q = warp; q < nc; q += PQ_WARPS) {
             if (posq[q] >= 0) continue;
-            double* c = cols + (size_t)q * l + j;
+            double* c = cols + (size_t)q * cs + j;
             double wa = 0.0, wb = 0.0;
             int i = lane;
             for (; i + 32 < len; i += 64) {
@@ -366,13 +376,13 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             for (i = 1 + lane; i < len; i += 64) {
                 const double x = fma(-w, v[i], c[i]);
                 c[i] = x;
-                dst[i] = x;
+                if (!GLOBAL_COLS) dst[i] = x;
                 s0 = fma(x, x, s0);
                 const int i2 = i + 32;
                 if (i2 < len) {
                     const double y = fma(-w, v[i2], c[i2]);
                     c[i2] = y;
-                    dst[i2] = y;
+                    if (!GLOBAL_COLS) dst[i2] = y;
                     s1 = fma(y, y, s1);
                 }
             }
@@ -390,8 +400,10 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     // R[:, pos] = first pos+1 entries of the retired column
     for (int q = 0; q < nc; ++q) {
         const int pos = posq[q];
-        const double* c = cols + (size_t)q * l;
-        for (int i = t; i < m; i += PQ_THREADS) p.R[(int64_t)i * m + pos] = i <= pos ? c[i] : 0.0;
+        if (pos < 0) continue;
+        const double* c = cols + (size_t)q * cs;
+        for (int i = t; i < m; i += PQ_THREADS)
+            p.R[(int64_t)i * m + pos] = i < pos ? c[i] : i == pos ? (GLOBAL_COLS ? alphaq[q] : c[i]) : 0.0;
     }
 }
 
@@ -480,25 +492,30 @@ bool pivoted_qr_persistent_ok(int m, int l) {
 
 cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
                        double* work, int* status, cudaStream_t s, long long spin_limit, const int* run_if) {
-    // Persistent cooperative form when the columns fit in shared memory.
+    // Persistent cooperative form: columns in shared memory when they fit, else in place in
+    // S (global memory); per-step kernels when neither can launch.
     int dev = 0, sms = 0, coop = 0, smem_optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (coop && sms > 0) {
-        int cpc = (m + sms - 1) / sms;
-        const size_t smem = ((size_t)cpc * l + l) * sizeof(double);
+        const int cpc = (m + sms - 1) / sms;
         const int G = (m + cpc - 1) / cpc;
+        const size_t smem_shared = ((size_t)cpc * l + l) * sizeof(double);
+        const size_t smem_global = (size_t)l * sizeof(double);
+        const bool in_smem = smem_shared + 4096 <= (size_t)smem_optin;
+        const size_t smem = in_smem ? smem_shared : smem_global;
+        const void* kern = in_smem ? (const void*)qr_persistent_kernel<false> : (const void*)qr_persistent_kernel<true>;
         if (cpc <= PQ_MAXC && G <= PQ_MAX_G && smem + 4096 <= (size_t)smem_optin) {
-            cudaFuncSetAttribute(qr_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_persistent_kernel, PQ_THREADS, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PQ_THREADS, smem);
             if (per_sm >= 1 && G <= per_sm * sms) {
                 PqrDev p;
                 p.S = S; p.m = m; p.l = l; p.lds = lds; p.R = R; p.perm = perm; p.cpc = cpc;
                 double* w = work;
-                p.slots = w;                    w += (size_t)2 * G * cpc * l;
+                p.slots = w;                    w += in_smem ? (size_t)2 * G * cpc * l : 0;
                 p.bval = w;                     w += 2 * (size_t)G;
                 p.bidx = (int*)w;               w += G;          // 2G ints
                 unsigned int* ctr = (unsigned int*)w;            // counter, abort
@@ -510,8 +527,7 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
                 if (e != cudaSuccess) return e;
                 void* args[] = {&p};
-                e = cudaLaunchCooperativeKernel((const void*)qr_persistent_kernel, dim3(G), dim3(PQ_THREADS), args,
-                                                smem, s);
+                e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(PQ_THREADS), args, smem, s);
                 note_launch();
                 if (e == cudaSuccess) return cudaGetLastError();
                 cudaGetLastError();   // clear and fall back

@@ -21,7 +21,9 @@
 // The pivot rule is Businger-Golub (largest remaining squared norm, lowest index on ties)
 // on float-float norms that are downdated from step to step and recomputed exactly when
 // the downdate has cancelled (as LAPACK does); the float64 kernel recomputes every norm
-// every step instead, so near-ties can resolve differently.
+// every step instead, so near-ties can resolve differently. As in LAPACK, the downdated
+// norms only choose the pivot: each reflector is formed from the pivot column's own norm,
+// summed afresh, so that it stays orthogonal to float-float accuracy.
 // S^* is scaled by a power of two (exact) so that its largest entry lies in [1/2, 1);
 // if a column's squared norm then falls below 2^-90 (float-float would lose the digits
 // of a trailing norm near float's underflow), the kernel leaves R and perm untouched and
@@ -163,6 +165,7 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
     __shared__ float2 nsq_ref[CQ_MAXC];      // its value at the last exact computation
     __shared__ float2 alphaq[CQ_MAXC];
     __shared__ int posq[CQ_MAXC];
+    __shared__ float2 red_ff[CQ_WARPS];      // per-warp partial sums (the pivot column's norm)
     __shared__ unsigned long long max_bits_s;
     __shared__ int bad_s;
     cg::cluster_group cluster = cg::this_cluster();
@@ -254,23 +257,36 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
         const int piv = bi < m ? bi : 0;   // some CTA holds an active column while j < m
         const int owner = piv / cpc, qo = piv - owner * cpc;
         const float2* src = cluster.map_shared_rank(cols + (size_t)qo * l, owner);
-        // the reflector from the pivot column's rows j .. l-1 (read through the cluster)
-        const float2 x0f = src[j];
-        const ff x0 = {x0f.x, x0f.y};
-        const ff nx = ff_sqrt(best);
+        // the pivot column's rows j .. l-1 (read through the cluster) and the exact squared
+        // norm of them: the downdated norms only choose the pivot; the reflector needs the
+        // column's own norm, or I - beta v v^* would not be orthogonal to float-float accuracy
+        ff part = {0.f, 0.f};
+        for (int i = j + t; i < l; i += CQ_THREADS) {
+            const float2 x = src[i];
+            v[i - j] = x;
+            part = ff_add(part, ff_mul({x.x, x.y}, {x.x, x.y}));
+        }
+        part = ff_warp_sum(part);
+        if (lane == 0) red_ff[warp] = make_float2(part.hi, part.lo);
+        if (t == 0 && b == owner) {
+            posq[qo] = j;
+            p.perm[j] = piv;
+        }
+        __syncthreads();
+        ff nsq_piv = {red_ff[0].x, red_ff[0].y};
+#pragma unroll
+        for (int w = 1; w < CQ_WARPS; ++w) nsq_piv = ff_add(nsq_piv, {red_ff[w].x, red_ff[w].y});
+        const ff x0 = {v[0].x, v[0].y};
+        const ff nx = ff_sqrt(nsq_piv);
         const ff alpha = x0.hi >= 0.f ? ff_neg(nx) : nx;
         const ff ax0 = x0.hi >= 0.f ? x0 : ff_neg(x0);
         const ff den = ff_mul(nx, ff_add(nx, ax0));
         const ff beta = den.hi > 0.f ? ff_recip(den) : ff{0.f, 0.f};
-        for (int i = j + 1 + t; i < l; i += CQ_THREADS) v[i - j] = src[i];
+        __syncthreads();                       // every thread has read v[0] = x_j
         if (t == 0) {
             const ff v0 = ff_add(x0, ff_neg(alpha));
             v[0] = make_float2(v0.hi, v0.lo);
-            if (b == owner) {
-                posq[qo] = j;
-                alphaq[qo] = make_float2(alpha.hi, alpha.lo);
-                p.perm[j] = piv;
-            }
+            if (b == owner) alphaq[qo] = make_float2(alpha.hi, alpha.lo);
         }
         __syncthreads();
         const int len = l - j;

@@ -7,7 +7,7 @@ delta is accumulated in double-double through the family's structure
 form is the paper's algorithm in IEEE double precision, as the paper ran it: its errors
 must land at the magnitudes the tables print (the tables' largest randomized-method values
 over all rows, times ten). The mixed refined form must beat the paper's own numbers for
-the same (m, kappa) row."""
+the same (m, kappa) row, with its refinement run to a tolerance."""
 import json
 import os
 
@@ -52,7 +52,9 @@ def test_randomized_method_errors_against_tables_2_and_4(kappa, golden_dir):
     m, n, l = 200, 100000, 204
     d64, e64 = study_row(rt, torch, m, n, l, kappa, "fp64")
     assert d64 <= 10 * paper_delta and e64 <= 10 * paper_eps, (d64, e64)
+    # the refinement runs to a tolerance (Remark 4.3): at l = m + 4 on this structured family
+    # the preconditioner contracts the error by only about 1e-4 per pass
     opts = dict(sketch_slices=6, resid_slices=10, refine_passes=4, refine_tol=1e-11, rank_tol=1e-14) \
-        if kappa > 1e10 else {}
+        if kappa > 1e10 else dict(refine_passes=4, refine_tol=1e-12)
     dmx, emx = study_row(rt, torch, m, n, l, kappa, "mixed", **opts)
     assert dmx <= same["delta_over_kappa"] and emx <= same["epsilon_over_kappa"], (dmx, emx, same)
