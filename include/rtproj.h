@@ -103,7 +103,7 @@ typedef struct {
     int omega;           /* rtproj_omega (default RTPROJ_OMEGA_GAUSSIAN)                  */
     int sketch_slices;   /* mixed: slices of A in S = A G            (default 5, 1..10)  */
     int gram_slices;     /* mixed: slices in W = P^{-1} A            (default 7, 1..10)  */
-    int gram2_slices;    /* mixed: slices in X = W W^*               (default 3, 1..10)  */
+    int gram2_slices;    /* mixed: slices in X = W W^*               (default 4, 1..10)  */
     int apply_slices;    /* mixed: slices in c = A b and A^* dh      (default 7, 1..10)  */
     int resid_slices;    /* mixed: slices in the refinement residual (default 9, 1..10)  */
     int refine_passes;   /* mixed: refinement passes (default 1, 0..8); with refine_tol > 0
@@ -122,6 +122,11 @@ typedef struct {
     int scalable;        /* 1: reserve what rtproj_set_scaling needs (the float64 form keeps
                             A diag(d) in the workspace; the mixed form forms it in the Gram
                             matrix's buffer and needs nothing more). Default 0.             */
+    int qr_form;         /* mixed form's pivoted QR: 0 (default) the float64 persistent kernel
+                            (one grid exchange per step); 1 the float-float kernel on one
+                            16-CTA cluster (exchange through distributed shared memory) when
+                            S^* fits its shared memory, else 0. Both give a valid pivoted QR;
+                            on GB300 form 0 measured faster (2.6 against 3.4 ms at 512 x 516). */
     int async;           /* 1: rtproj_create and rtproj_precondition do not synchronize; the
                             conditions they would return (non-finite A, ERANK, ENOTSPD,
                             ETIMEOUT) stay latched in the device status word, which

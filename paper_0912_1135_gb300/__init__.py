@@ -42,7 +42,8 @@ class Opts(ctypes.Structure):
         ("gram_slices", ctypes.c_int), ("gram2_slices", ctypes.c_int), ("apply_slices", ctypes.c_int),
         ("resid_slices", ctypes.c_int), ("refine_passes", ctypes.c_int), ("timing", ctypes.c_int),
         ("rank_tol", ctypes.c_double), ("dtype", ctypes.c_int), ("spin_limit_cycles", ctypes.c_longlong),
-        ("refine_tol", ctypes.c_double), ("scalable", ctypes.c_int), ("async_", ctypes.c_int),   # async_: opts.async
+        ("refine_tol", ctypes.c_double), ("scalable", ctypes.c_int), ("qr_form", ctypes.c_int),
+        ("async_", ctypes.c_int),   # async_: opts.async
     ]
 
 

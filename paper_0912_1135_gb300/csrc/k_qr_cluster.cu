@@ -22,8 +22,11 @@
 // on float-float norms that are downdated from step to step and recomputed exactly when
 // the downdate has cancelled (as LAPACK does); the float64 kernel recomputes every norm
 // every step instead, so near-ties can resolve differently. As in LAPACK, the downdated
-// norms only choose the pivot: each reflector is formed from the pivot column's own norm,
-// summed afresh, so that it stays orthogonal to float-float accuracy.
+// norms only choose each CTA's candidate: the candidate is published with its column's
+// norm summed afresh, so that the reflector stays orthogonal to float-float accuracy and
+// the choice between CTAs is made on exact norms. Candidates are pushed into every CTA's
+// shared memory by remote stores before the step's barrier, so that after it every read
+// of them is local.
 // S^* is scaled by a power of two (exact) so that its largest entry lies in [1/2, 1);
 // if a column's squared norm then falls below 2^-90 (float-float would lose the digits
 // of a trailing norm near float's underflow), the kernel leaves R and perm untouched and
@@ -159,13 +162,12 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
     const int l = p.l, m = p.m, cpc = p.cpc;
     float2* cols = csm;                          // cpc x l
     float2* v = csm + (size_t)cpc * l;           // l (rows j .. l-1 of the reflector at offset 0)
-    __shared__ float2 cand_val[2];
-    __shared__ int cand_idx[2];
+    __shared__ float2 cand_val[2][CQ_CTAS];  // by step parity: every CTA's candidate (pushed to all)
+    __shared__ int cand_idx[2][CQ_CTAS];
     __shared__ float2 nsq[CQ_MAXC];          // squared norm of rows j .. l-1 before step j
     __shared__ float2 nsq_ref[CQ_MAXC];      // its value at the last exact computation
     __shared__ float2 alphaq[CQ_MAXC];
     __shared__ int posq[CQ_MAXC];
-    __shared__ float2 red_ff[CQ_WARPS];      // per-warp partial sums (the pivot column's norm)
     __shared__ unsigned long long max_bits_s;
     __shared__ int bad_s;
     cg::cluster_group cluster = cg::this_cluster();
@@ -224,12 +226,18 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
         }
     }
     __syncthreads();
-    if (t == 0) {
-        int bq = -1;
-        for (int q = 0; q < nc; ++q)
-            if (bq < 0 || ff_gt({nsq[q].x, nsq[q].y}, {nsq[bq].x, nsq[bq].y})) bq = q;
-        cand_val[0] = bq >= 0 ? nsq[bq] : make_float2(-1.f, 0.f);
-        cand_idx[0] = bq >= 0 ? c0 + bq : m;
+    if (warp == 0) {
+        ff cv = {-1.f, 0.f};
+        int ci = m;
+        for (int q = lane; q < nc; q += 32) {
+            const ff x = {nsq[q].x, nsq[q].y};
+            if (ci == m || ff_gt(x, cv)) { cv = x; ci = c0 + q; }
+        }
+        cand_reduce(cv, ci, m);
+        if (lane < CQ_CTAS) {     // the step-0 norms are exact
+            *cluster.map_shared_rank(&cand_val[0][b], lane) = make_float2(cv.hi, cv.lo);
+            *cluster.map_shared_rank(&cand_idx[0][b], lane) = ci;
+        }
     }
     cluster.sync();
     int bad = 0;
@@ -245,48 +253,37 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
     for (int j = 0; j < m; ++j) {
         const int par = j & 1;
         if (j > 0) cluster.sync();   // step j's candidates are published (step 0's by the sync above)
-        // the pivot: largest squared norm over the sixteen candidates, lowest index on ties
+        // the pivot: largest squared norm over the sixteen candidates (pushed here by every
+        // CTA), lowest index on ties; each candidate carries its column's exact squared norm
         ff best = {-1.f, 0.f};
         int bi = m;
         if (lane < CQ_CTAS) {
-            const float2 cv = *cluster.map_shared_rank(&cand_val[par], lane);
-            const int ci = *cluster.map_shared_rank(&cand_idx[par], lane);
+            const float2 cv = cand_val[par][lane];
+            const int ci = cand_idx[par][lane];
             if (ci < m) { best = {cv.x, cv.y}; bi = ci; }
         }
         cand_reduce(best, bi, m);
         const int piv = bi < m ? bi : 0;   // some CTA holds an active column while j < m
         const int owner = piv / cpc, qo = piv - owner * cpc;
         const float2* src = cluster.map_shared_rank(cols + (size_t)qo * l, owner);
-        // the pivot column's rows j .. l-1 (read through the cluster) and the exact squared
-        // norm of them: the downdated norms only choose the pivot; the reflector needs the
-        // column's own norm, or I - beta v v^* would not be orthogonal to float-float accuracy
-        ff part = {0.f, 0.f};
-        for (int i = j + t; i < l; i += CQ_THREADS) {
-            const float2 x = src[i];
-            v[i - j] = x;
-            part = ff_add(part, ff_mul({x.x, x.y}, {x.x, x.y}));
-        }
-        part = ff_warp_sum(part);
-        if (lane == 0) red_ff[warp] = make_float2(part.hi, part.lo);
-        if (t == 0 && b == owner) {
-            posq[qo] = j;
-            p.perm[j] = piv;
-        }
-        __syncthreads();
-        ff nsq_piv = {red_ff[0].x, red_ff[0].y};
-#pragma unroll
-        for (int w = 1; w < CQ_WARPS; ++w) nsq_piv = ff_add(nsq_piv, {red_ff[w].x, red_ff[w].y});
-        const ff x0 = {v[0].x, v[0].y};
-        const ff nx = ff_sqrt(nsq_piv);
+        // the reflector from the pivot column's rows j .. l-1 (read through the cluster) and
+        // its exact squared norm
+        const float2 x0f = src[j];
+        const ff x0 = {x0f.x, x0f.y};
+        const ff nx = ff_sqrt(best);
         const ff alpha = x0.hi >= 0.f ? ff_neg(nx) : nx;
         const ff ax0 = x0.hi >= 0.f ? x0 : ff_neg(x0);
         const ff den = ff_mul(nx, ff_add(nx, ax0));
         const ff beta = den.hi > 0.f ? ff_recip(den) : ff{0.f, 0.f};
-        __syncthreads();                       // every thread has read v[0] = x_j
+        for (int i = j + 1 + t; i < l; i += CQ_THREADS) v[i - j] = src[i];
         if (t == 0) {
             const ff v0 = ff_add(x0, ff_neg(alpha));
             v[0] = make_float2(v0.hi, v0.lo);
-            if (b == owner) alphaq[qo] = make_float2(alpha.hi, alpha.lo);
+            if (b == owner) {
+                posq[qo] = j;
+                alphaq[qo] = make_float2(alpha.hi, alpha.lo);
+                p.perm[j] = piv;
+            }
         }
         __syncthreads();
         const int len = l - j;
@@ -338,7 +335,9 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
             if (db) downdate_norm(cb, len, qb, lane, nsq, nsq_ref);
         }
         __syncthreads();
-        // this CTA's candidate for step j+1 (warp 0: two columns per lane, then shuffles)
+        // this CTA's candidate for step j+1 (warp 0): the active column with the largest
+        // downdated norm, published with its exact squared norm over rows j+1 .. l-1 (which
+        // the reflector of step j+1 needs) into every CTA's shared memory
         if (warp == 0) {
             ff cv = {-1.f, 0.f};
             int ci = m;
@@ -348,9 +347,24 @@ __global__ void __launch_bounds__(CQ_THREADS, 1) qr_cluster_kernel(CqrDev p) {
                     if (ci == m || ff_gt(x, cv)) { cv = x; ci = c0 + q; }
                 }
             cand_reduce(cv, ci, m);
-            if (lane == 0) {
-                cand_val[par ^ 1] = make_float2(cv.hi, cv.lo);
-                cand_idx[par ^ 1] = ci;
+            if (ci < m) {
+                const float2* c = cols + (size_t)(ci - c0) * l;
+                ff s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+                int i = j + 1 + lane;
+                for (; i + 32 < l; i += 64) {
+                    const ff a = {c[i].x, c[i].y}, d = {c[i + 32].x, c[i + 32].y};
+                    s0 = ff_add(s0, ff_mul(a, a));
+                    s1 = ff_add(s1, ff_mul(d, d));
+                }
+                if (i < l) {
+                    const ff a = {c[i].x, c[i].y};
+                    s0 = ff_add(s0, ff_mul(a, a));
+                }
+                cv = ff_warp_sum(ff_add(s0, s1));
+            }
+            if (lane < CQ_CTAS) {
+                *cluster.map_shared_rank(&cand_val[par ^ 1][b], lane) = make_float2(cv.hi, cv.lo);
+                *cluster.map_shared_rank(&cand_idx[par ^ 1][b], lane) = ci;
             }
         }
     }

@@ -97,6 +97,7 @@ bool valid_opts(const rtproj_opts& o) {
     if (o.refine_passes < 0 || o.refine_passes > 8) return false;
     if (o.async != 0 && o.async != 1) return false;
     if (o.scalable != 0 && o.scalable != 1) return false;
+    if (o.qr_form != 0 && o.qr_form != 1) return false;
     if (o.dtype != RTPROJ_F64 && o.dtype != RTPROJ_F32) return false;
     if (o.spin_limit_cycles < 1) return false;
     if (!(o.refine_tol >= 0.0)) return false;
@@ -300,7 +301,7 @@ void rtproj_default_opts(rtproj_opts* o) {
     o->omega = RTPROJ_OMEGA_GAUSSIAN;
     o->sketch_slices = 5;
     o->gram_slices = 7;
-    o->gram2_slices = 3;
+    o->gram2_slices = 4;
     o->apply_slices = 7;
     o->resid_slices = 9;
     o->refine_passes = 1;
@@ -311,6 +312,7 @@ void rtproj_default_opts(rtproj_opts* o) {
     o->refine_tol = 0.0;
     o->async = 0;
     o->scalable = 0;
+    o->qr_form = 0;
 }
 
 size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts* opts) {
@@ -448,13 +450,12 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_end(h, RTPROJ_PHASE_SKETCH);
     // 2. S^* = Q R Pi (Eq. 13)
     phase_begin(h, RTPROJ_PHASE_QR);
-    // mixed form: the float-float cluster QR when S^* fits one cluster's shared memory (the
-    // float64 persistent kernel follows and runs only if the cluster kernel's range check
-    // sent the factorization back to it); the float64 form keeps the float64 QR
+    // opts.qr_form = 1 (mixed form): the float-float cluster QR when S^* fits one cluster's
+    // shared memory (the float64 persistent kernel follows and runs only if the cluster
+    // kernel's range check sent the factorization back to it); otherwise the float64 QR
     bool cluster = false;
     int* qr_flag = h->status + 4;
-    const char* qr_env = std::getenv("RTPROJ_FP64_QR");
-    if (h->opts.mode == RTPROJ_MIXED_REFINED && !(qr_env && qr_env[0] == '1') && pivoted_qr_persistent_ok(m, (int)l))
+    if (h->opts.mode == RTPROJ_MIXED_REFINED && h->opts.qr_form == 1 && pivoted_qr_persistent_ok(m, (int)l))
         RT_CHECK(pivoted_qr_cluster(h->S, m, (int)l, l, h->R, h->perm, qr_flag, s, &cluster));
     RT_CHECK(pivoted_qr(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s, h->spin_limit,
                         cluster ? qr_flag : nullptr));

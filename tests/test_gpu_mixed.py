@@ -207,7 +207,7 @@ def test_cluster_qr_is_a_valid_pivoted_qr(m, n, l):
     torch = torch_cuda()
     rt = rt_module()
     A = workloads.haar_spectrum_matrix(m, n, 1e-8, 80 + m)
-    with _mixed(rt, torch, A, l, 1) as P:
+    with _mixed(rt, torch, A, l, 1, qr_form=1) as P:
         S = P.sketch(seed=21, l=l).cpu().numpy()
         P.precondition(seed=21, l=l)
         R, perm, _ = P.export_state()
@@ -221,15 +221,15 @@ def test_cluster_qr_is_a_valid_pivoted_qr(m, n, l):
         assert R[j, j] ** 2 >= (1 - 1e-6) * np.max(tail[j, j + 1:])
 
 
-def test_cluster_and_float64_qr_give_the_same_projection(monkeypatch):
+def test_cluster_and_float64_qr_give_the_same_projection():
     torch = torch_cuda()
     rt = rt_module()
     m, n, l, k = 64, 4096, 256, 4
     A = workloads.haar_spectrum_matrix(m, n, 1e-10, 85)
     B = workloads.rhs(k, n, 86)
     Zx, _, _ = exact.exact_project(A, B)
-    for flag in ("0", "1"):
-        monkeypatch.setenv("RTPROJ_FP64_QR", flag)
-        with _mixed(rt, torch, A, l, k) as P:
+    for form in (0, 1):
+        with _mixed(rt, torch, A, l, k, qr_form=form) as P:
             P.precondition(seed=5, l=l)
-            assert_rows_close(P.null_project(to_dev(torch, B)).cpu().numpy(), Zx, Z_TOL, f"Z (RTPROJ_FP64_QR={flag})")
+            assert P.info()["kappa_R"] > 1e8                 # rank revealing: R_11 / R_mm ~ kappa
+            assert_rows_close(P.null_project(to_dev(torch, B)).cpu().numpy(), Zx, Z_TOL, f"Z (qr_form={form})")
