@@ -257,6 +257,28 @@ def time_steps(torch, P, Bt, seed, l, steps, stream):
     return ev0.elapsed_time(ev1)
 
 
+def time_steps_pipelined(torch, Ps, Bt, seed, l, steps, stream, Zs):
+    """The same steps on len(Ps) handles bound to the same A, each on its own stream and in
+    the asynchronous mode: step i runs on handle i mod len(Ps), so a step's apply (tensor
+    cores) overlaps the next step's precondition, whose pivoted QR and Cholesky are bound by
+    the latency of their sequential steps and leave the SMs' pipes mostly idle."""
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for P in Ps:
+        P.stream.wait_stream(stream)
+    for i in range(steps):
+        P = Ps[i % len(Ps)]
+        P.precondition(seed + i, l)
+        P.null_project(Bt, out=Zs[i % len(Ps)])
+    for P in Ps:
+        stream.wait_stream(P.stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
 _ZBUF = {}
 
 
@@ -307,7 +329,7 @@ def phase_work(mode, w, o):
 # `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu-baseline --no-accuracy --no-fp64-form`
 # on the 512 x 65536 workload (mixed form); to be replaced by None whenever that kernel
 # changes. Only the float64 QR's figure applies to both forms (the same kernel).
-PROFILED_TRAFFIC = {("dense_512x65536", "qr_persistent_kernel"): 2158336 + 156672}
+PROFILED_TRAFFIC = {("dense_512x65536", "qr_persistent_kernel"): 2160128 + 217600}
 
 
 def roofline_entry(mode, phase_ms, phase_cnt, steps, w, pk, opts):
@@ -358,14 +380,32 @@ def run_ours(args, w, world, rank, local):
         P.null_project(Bt, out=Zbuf_of(P, Bt))
     torch.cuda.synchronize()
     P.timings()
+    pipe = []
+    if args.pipeline > 1:
+        pipe = [rt.Projector(At, l_max=w.l, k_max=w.k, mode=args.mode, stream=torch.cuda.Stream(dev), async_=1,
+                             **wopts) for _ in range(args.pipeline)]
+        Zs = [torch.empty_like(Bt) for _ in pipe]
+        time_steps_pipelined(torch, pipe, Bt, seed0, w.l, args.warmup, stream, Zs)
     launches0 = rt.launch_count()
     sampler = ClockSampler(local)
     sampler.start()
     barrier(world)
-    ms = time_steps(torch, P, Bt, seed0 + 1000, w.l, args.steps, stream)
+    if pipe:
+        ms = time_steps_pipelined(torch, pipe, Bt, seed0 + 1000, w.l, args.steps, stream, Zs)
+    else:
+        ms = time_steps(torch, P, Bt, seed0 + 1000, w.l, args.steps, stream)
     barrier(world)
     clocks = sampler.stop()
     launches = rt.launch_count() - launches0
+    if pipe:
+        bad = sum(1 for Q in pipe if Q.info()["status"] != 0)
+        if bad:
+            raise RuntimeError(f"{bad} pipelined handles latched a nonzero status")
+        Zbuf_of(P, Bt).copy_(Zs[(args.steps - 1) % len(pipe)])
+        for Q in pipe:
+            Q.close()
+        # the per-phase breakdown comes from the same steps run one after another
+        time_steps(torch, P, Bt, seed0 + 1000, w.l, args.steps, stream)
     tim = P.timings()
     ms_max = max_over_ranks(ms, world)
     value = job_throughput(world, w.k, args.steps, ms_max)
@@ -396,6 +436,8 @@ def run_ours(args, w, world, rank, local):
         "config": {"workload": w.name, "mode": args.mode, "m": w.m, "n": w.n, "k": w.k, "l": w.l,
                    "kappa": 1.0 / w.sigma_min, "omega": "gaussian (Box-Muller on Philox4x32-10, 2^-12 grid)",
                    "step": "precondition(seed, l) + null_project(k RHS)",
+                   "pipeline": (f"{args.pipeline} handles on {args.pipeline} streams: a step's apply overlaps the next "
+                                "step's precondition") if args.pipeline > 1 else "one handle, steps in order",
                    "l2": f"inputs larger than L2 (A is {A.nbytes / 1e6:.0f} MB float64)",
                    "parallelism": f"replicas x{world}", "options": wopts},
         "phase_ms_per_step": {p: phase_ms[p] / args.steps for p in phase_ms if phase_cnt[p]},
@@ -803,6 +845,8 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the float64-form comparison")
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
+    ap.add_argument("--pipeline", type=int, default=1,
+                    help="handles (and streams) the timed steps rotate over; > 1 overlaps consecutive steps")
     ap.add_argument("--study", choices=["accuracy", "variates", "batch"], default=None,
                     help="run a study (Section 5 accuracy; variates and sketch sizes) instead of the bench")
     args = ap.parse_args()

@@ -1337,7 +1337,10 @@ cudaError_t sliced_gemm_impl(const SlicedGemm& g0, void* scratch, size_t scratch
     // possible: maximise min(b_stages, a_stages / sa).
     const size_t b_stage = (size_t)g.b.s * tn * KB * 2;
     const size_t fixed = 1024 + (2 * W_MAX_A_STAGES + 2 * W_MAX_B_STAGES + 4) * 8 + 16;
-    const size_t budget = 220 * 1024 - fixed;
+    // 200 KB, not the 227 KB a CTA may take: an SM then also holds one CTA of the pivoted QR
+    // (about 23 KB), so that a step's products can run while the next step's latency-bound
+    // QR occupies the SMs
+    const size_t budget = 200 * 1024 - fixed;
     int best_bs = 0, best_as = 0;
     double best_depth = -1.0;
     const int a_slots_per_kb = (g.a.s + A_PPS - 1) / A_PPS;
