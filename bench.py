@@ -845,7 +845,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the float64-form comparison")
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
-    ap.add_argument("--pipeline", type=int, default=1,
+    ap.add_argument("--pipeline", type=int, default=2,
                     help="handles (and streams) the timed steps rotate over; > 1 overlaps consecutive steps")
     ap.add_argument("--study", choices=["accuracy", "variates", "batch"], default=None,
                     help="run a study (Section 5 accuracy; variates and sketch sizes) instead of the bench")
