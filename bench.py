@@ -551,7 +551,11 @@ def fp64_form(torch, rt, A, B, At, Bt, w, args, rank):
     from oracle import exact, metrics
     steps = 3
     P = rt.Projector(At, l_max=w.l, k_max=w.k, mode="fp64")
-    P.precondition(w.seed_omega, w.l)
+    try:
+        P.precondition(w.seed_omega, w.l)
+    except rt.RtprojError as e:
+        P.close()
+        return {"error": str(e)}
     P.null_project(Bt, out=Zbuf_of(P, Bt))
     stream = torch.cuda.current_stream(At.device)
     ms = time_steps(torch, P, Bt, w.seed_omega + 2000, w.l, steps, stream)
@@ -682,8 +686,11 @@ def study_accuracy(args):
         row = {"m": m, "n": n, "l": l, "kappa": kappa}
         mixed_kw = dict(WORKLOAD_OPTS["dense_2048x262144"]) if kappa > 1e10 else dict(refine_passes=4,
                                                                                           refine_tol=1e-12)
-        row["mixed"] = _family_errors(torch, rt, dev, m, n, l, kappa, "mixed", **mixed_kw)
-        row["fp64"] = _family_errors(torch, rt, dev, m, n, l, kappa, "fp64")
+        for form, kw in (("mixed", mixed_kw), ("fp64", {})):
+            try:
+                row[form] = _family_errors(torch, rt, dev, m, n, l, kappa, form, **kw)
+            except rt.RtprojError as e:
+                row[form] = {"error": str(e)}
         ref = printed.get((m, n, l, kappa)) or (printed4.get(kappa) if n == 100000 else None)
         if ref:
             row["paper"] = {"delta_over_kappa": ref["delta_over_kappa"], "epsilon_over_kappa": ref["epsilon_over_kappa"],
@@ -715,7 +722,12 @@ def study_variates(args):
     for dist in ("gaussian", "uniform", "rademacher"):
         for l in (w.m, w.m + 4, 2 * w.m, 4 * w.m):
             with rt.Projector(At, l_max=l, k_max=w.k, omega=dist) as P:
-                P.precondition(w.seed_omega, l)
+                try:
+                    P.precondition(w.seed_omega, l)
+                except rt.RtprojError as e:
+                    out.append({"omega": dist, "l": l, "error": str(e)})
+                    print(json.dumps(out[-1]), file=sys.stderr, flush=True)
+                    continue
                 times = []
                 for i in range(5):
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -832,6 +844,89 @@ def study_batch(args):
     return 0
 
 
+def _sparse_row(torch, rt, dev, m, n, l, kappa, low_rank, nb=100, seed=5, refine=(8, 1e-15)):
+    """One row of Section 5's tables with the sparse operator form: the test matrix of
+    Eq. 21 in compressed sparse row form (plus the rank-10 term of Eq. 22 when low_rank),
+    precondition and projection device-timed (one vector, and nb vectors at once), and
+    delta/kappa, epsilon/kappa over nb random unit b (||A z|| through the family's
+    structure in double-double, the low-rank part in float64)."""
+    from oracle import closed_form
+    rp, ci, v, b, pu, pv = workloads.paper_test_csr(m, n, kappa, seed)
+    U = V = None
+    if low_rank:
+        U, V = workloads.paper_low_rank(m, n, seed + 3)
+    B = workloads.rhs(nb, n, seed + 1)
+    B /= np.linalg.norm(B, axis=1, keepdims=True)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    out = {"m": m, "n": n, "l": l, "kappa": kappa, "nnz": int(len(v)), "low_rank": 10 if low_rank else 0}
+    with rt.SparseProjector(t(rp), t(ci), t(v), n, U=t(U) if low_rank else None, V=t(V) if low_rank else None,
+                            l_max=l, k_max=nb, refine_passes=refine[0], refine_tol=refine[1]) as P:
+        Bt = t(B)
+        P.precondition(seed + 2, l)
+        P.null_project(Bt[:1])
+        stream = torch.cuda.current_stream(dev)
+        ev[0].record(stream)
+        P.precondition(seed + 2, l)
+        ev[1].record(stream)
+        ev[2].record(stream)
+        P.null_project(Bt[:1])
+        ev[3].record(stream)
+        ev[4].record(stream)
+        Z = P.null_project(Bt)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+        inf = P.info()
+        ZZ = P.null_project(Z.clone()).cpu().numpy()
+        Z = Z.cpu().numpy()
+    AZ = closed_form.apply_A(b, pu, pv, Z)
+    if low_rank:
+        AZ = AZ + (U @ (V @ Z.T)).T
+    delta = float(np.max(np.linalg.norm(AZ, axis=1)))
+    eps = float(np.max(np.linalg.norm(Z - ZZ, axis=1)))
+    out.update({"t_pre_s": ev[0].elapsed_time(ev[1]) * 1e-3, "t_pro_s": ev[2].elapsed_time(ev[3]) * 1e-3,
+                "t_pro_per_vector_batched_s": ev[4].elapsed_time(ev[5]) * 1e-3 / nb,
+                "delta_over_kappa": delta / kappa, "epsilon_over_kappa": eps / kappa,
+                "passes": inf["passes"], "kappa_pre": inf["kappa_pre"], "status": inf["status"]})
+    if not low_rank:
+        Zc, _, _ = closed_form.project(b, pu, pv, B)
+        out["z_err_vs_closed_form"] = float(np.max(np.linalg.norm(Z - Zc, axis=1)))
+    return out
+
+
+def study_sparse(args):
+    """Section 5, Tables 1-2 and 5-6, in the paper's own setting: A applied as a sparse
+    operator (five nonzeros per column), and its sum with a rank-10 term, at the paper's
+    sizes, next to the paper's printed timings (one 2009 CPU core) and errors."""
+    import torch
+    import paper_0912_1135_gb300 as rt
+    gd = os.path.join(ROOT, "tests", "golden")
+    tim = json.load(open(os.path.join(gd, "section5_timings.json")))
+    err = json.load(open(os.path.join(gd, "section5_randomized_errors.json")))
+    key = lambda r: (r["m"], r["n"], r["l"], r["kappa"])
+    t1 = {key(r): r for r in tim["table1"]}
+    t2 = {key(r): r for r in err["table2"]}
+    t5 = {key(r): r for r in tim["table5"]}
+    t6 = {key(r): r for r in tim["table6"]}
+    dev = torch.device("cuda", 0)
+    rows = []
+    for low_rank, tt, te in ((False, t1, t2), (True, t5, t6)):
+        for k in tt:
+            m, n, l, kappa = k
+            try:
+                r = _sparse_row(torch, rt, dev, m, n, l, kappa, low_rank)
+            except rt.RtprojError as e:
+                r = {"m": m, "n": n, "l": l, "kappa": kappa, "low_rank": 10 if low_rank else 0, "error": str(e)}
+            r["paper"] = {"t_pre_s": tt[k]["t_pre"], "t_pro_s": tt[k]["t_pro"],
+                          "delta_over_kappa": te[k]["delta_over_kappa"], "epsilon_over_kappa": te[k]["epsilon_over_kappa"]}
+            rows.append(r)
+            print(json.dumps(r), file=sys.stderr, flush=True)
+            torch.cuda.empty_cache()
+    print(json.dumps({"study": "section5_sparse_operator", "omega": "gaussian", "rhs": "100 random unit b per row",
+                      "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -847,13 +942,14 @@ def main():
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
     ap.add_argument("--pipeline", type=int, default=2,
                     help="handles (and streams) the timed steps rotate over; > 1 overlaps consecutive steps")
-    ap.add_argument("--study", choices=["accuracy", "variates", "batch"], default=None,
+    ap.add_argument("--study", choices=["accuracy", "variates", "batch", "sparse"], default=None,
                     help="run a study (Section 5 accuracy; variates and sketch sizes) instead of the bench")
     args = ap.parse_args()
     if args.study:
         import __graft_entry__
         __graft_entry__.build()
-        return {"accuracy": study_accuracy, "variates": study_variates, "batch": study_batch}[args.study](args)
+        return {"accuracy": study_accuracy, "variates": study_variates, "batch": study_batch,
+                "sparse": study_sparse}[args.study](args)
     if args.warmup < 3:
         args.warmup = 3
     w = workloads.WORKLOADS[args.workload]

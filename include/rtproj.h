@@ -109,7 +109,9 @@ typedef struct {
     int refine_passes;   /* mixed: refinement passes (default 1, 0..8); with refine_tol > 0
                             the largest number of passes                                 */
     int timing;          /* 1: record CUDA events around each phase (rtproj_get_timings)  */
-    double rank_tol;     /* ERANK threshold; <= 0 selects 64 * l * 2^-52                  */
+    double rank_tol;     /* ERANK threshold; <= 0 selects 8 u, u the sketch's relative
+                            precision: 2^-52 in the float64 and sparse forms, 2^(-8 s) for
+                            the mixed form's s = sketch_slices digits of A              */
     int dtype;           /* rtproj_dtype of A, B and the outputs (default RTPROJ_F64)     */
     long long spin_limit_cycles;  /* bound, in SM clock cycles, on each grid-exchange wait of
                             the pivoted QR and the Cholesky (default 4e9, about 2 s); when it
@@ -186,6 +188,36 @@ size_t rtproj_workspace_bytes(int64_t m, int64_t n, int64_t l_max, int64_t k_max
 rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, int64_t lda,
                             int64_t l_max, int64_t k_max, void* workspace, size_t ws_bytes,
                             void* stream, const rtproj_opts* opts);
+
+/* A sparse A, optionally plus a low-rank term: A = S + U V (Section 5: the sparse test
+   matrix of Eq. 21 and its sum with a rank-10 term, Eq. 22). S is m x n in compressed
+   sparse row form on the device: row_ptr (m + 1 int64, row_ptr[0] = 0, non-decreasing,
+   row_ptr[m] = nnz), col_idx (nnz int32 in [0, n), any order within a row, duplicates
+   summed) and val (nnz float64). U (m x r, row-major, ld r) and V (r x n, row-major,
+   ld n) are float64 device matrices, r = 0 (U, V null) for S alone, 0 <= r <= min(m, 64);
+   k_max <= 65535.
+   All of them are borrowed: they must stay alive and unchanged until rtproj_destroy.
+   The handle runs the float64 arithmetic of the dense float64 form on the products that
+   build the preconditioner (S_k = A G with G generated per nonzero; X column by column
+   as in steps a-e after Eq. 15: D = A^* P^-, E = A D, X = R^{-*} Pi E) and sums every
+   product with A or A^* of the apply and its refinement passes (Remark 4.3; opts
+   refine_passes and refine_tol) in double-double, so that the refinement converges to
+   the projection of the stored matrix. A product with A costs O(nnz + r (m + n)).
+   opts.mode, the slice counts and qr_form do not apply; dtype must be RTPROJ_F64 and
+   scalable 0 (else RTPROJ_EUNSUPPORTED). rtproj_create_sparse synchronizes the stream:
+   it reads row_ptr on the host (RTPROJ_EINVAL if malformed), builds a column-compressed
+   copy in the workspace and checks col_idx (RTPROJ_EINVAL) and val, U, V
+   (RTPROJ_ENONFINITE) on the device. The later calls are those of a dense handle
+   (precondition, the applies, sketch, get_info, export_state, destroy); set_scaling
+   returns RTPROJ_EUNSUPPORTED. */
+size_t rtproj_sparse_workspace_bytes(int64_t m, int64_t n, int64_t nnz, int64_t r, int64_t l_max,
+                                     int64_t k_max, const rtproj_opts* opts);
+rtproj_status rtproj_create_sparse(rtproj_t* out, int64_t m, int64_t n, int64_t nnz,
+                                   const int64_t* row_ptr, const int32_t* col_idx,
+                                   const double* val, int64_t r, const double* U,
+                                   const double* V, int64_t l_max, int64_t k_max,
+                                   void* workspace, size_t ws_bytes, void* stream,
+                                   const rtproj_opts* opts);
 
 /* Builds the preconditioner from seed and l (m <= l <= min(n, l_max); Section 4):
    the sketch S = A G (Eq. 12), the pivoted QR S^* = Q R Pi (Eq. 13), and the Gram

@@ -18,7 +18,7 @@ import torch
 
 from . import _build
 
-__all__ = ["Projector", "RtprojError", "load_library", "library_path", "STATUS", "MODES", "OMEGAS",
+__all__ = ["Projector", "SparseProjector", "RtprojError", "load_library", "library_path", "STATUS", "MODES", "OMEGAS",
            "generate_omega", "launch_count"]
 
 MODES = {"fp64": 0, "mixed": 1}
@@ -85,6 +85,9 @@ EXPORTS = {
     "rtproj_set_scaling": (ctypes.c_int, [_P, _P]),
     "rtproj_grad_workspace_bytes": (ctypes.c_size_t, [_P, _I64]),
     "rtproj_grad_A": (ctypes.c_int, [_P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, _I64, _P, ctypes.c_size_t]),
+    "rtproj_sparse_workspace_bytes": (ctypes.c_size_t, [_I64, _I64, _I64, _I64, _I64, _I64, ctypes.POINTER(Opts)]),
+    "rtproj_create_sparse": (ctypes.c_int, [ctypes.POINTER(_P), _I64, _I64, _I64, _P, _P, _P, _I64, _P, _P, _I64, _I64,
+                                            _P, ctypes.c_size_t, _P, ctypes.POINTER(Opts)]),
 }
 
 PHASES = ["sketch", "qr", "gram", "factor", "apply_a", "apply_m", "apply_at", "slice"]
@@ -339,6 +342,66 @@ class Projector:
 
     def lstsq(self, B):
         return self.project(B, null=False, lstsq=True)[2]
+
+
+class SparseProjector(Projector):
+    """A = S + U V with S sparse (compressed sparse row, on the device) and an optional
+    low-rank term U V (``rtproj_create_sparse``): the products with A cost O(nnz + r(m + n))
+    and the apply's residuals are summed in double-double. The arrays are borrowed for the
+    handle's lifetime (kept referenced here). The other methods are those of Projector;
+    set_scaling is not supported."""
+
+    def __init__(self, row_ptr: torch.Tensor, col_idx: torch.Tensor, val: torch.Tensor, n: int,
+                 U: torch.Tensor | None = None, V: torch.Tensor | None = None, l_max: int | None = None,
+                 k_max: int = 64, omega: str = "gaussian", stream: torch.cuda.Stream | None = None, **opts):
+        lib = load_library()
+        dev = val.device
+        ok = (row_ptr.is_cuda and row_ptr.dtype == torch.int64 and row_ptr.dim() == 1 and row_ptr.is_contiguous()
+              and col_idx.is_cuda and col_idx.dtype == torch.int32 and col_idx.dim() == 1 and col_idx.is_contiguous()
+              and val.is_cuda and val.dtype == torch.float64 and val.dim() == 1 and val.is_contiguous()
+              and row_ptr.device == dev and col_idx.device == dev and col_idx.numel() == val.numel())
+        if not ok:
+            raise TypeError("row_ptr (int64), col_idx (int32) and val (float64) must be contiguous CUDA vectors "
+                            "on one device, col_idx and val of equal length")
+        self.m, self.n = row_ptr.numel() - 1, int(n)
+        r = 0
+        if U is not None or V is not None:
+            if U is None or V is None:
+                raise TypeError("U and V go together")
+            r = U.shape[1] if U.dim() == 2 else -1
+            if not (U.is_cuda and U.dtype == torch.float64 and U.device == dev and U.is_contiguous()
+                    and tuple(U.shape) == (self.m, r) and V.is_cuda and V.dtype == torch.float64
+                    and V.device == dev and V.is_contiguous() and tuple(V.shape) == (r, self.n)):
+                raise TypeError(f"U must be {self.m} x r and V r x {self.n}, contiguous float64 on {dev}")
+        self._keep = (row_ptr, col_idx, val, U, V)
+        self.A = None
+        self.dtype = torch.float64
+        self.lda = 0
+        self.nnz, self.rank_lr = val.numel(), r
+        self.l_max = int(l_max if l_max is not None else min(self.n, 4 * self.m))
+        self.k_max = int(k_max)
+        self.device = dev
+        self.opts = make_opts("fp64", omega, **opts)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._enter(*[t for t in self._keep if t is not None])
+        nbytes = lib.rtproj_sparse_workspace_bytes(self.m, self.n, self.nnz, r, self.l_max, self.k_max,
+                                                   ctypes.byref(self.opts))
+        if nbytes == 0:
+            raise RtprojError(1, "rtproj_sparse_workspace_bytes")
+        with torch.cuda.stream(self.stream):
+            self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=dev)
+        h = ctypes.c_void_p()
+        ptr = lambda t: _dev_ptr(t) if t is not None else None
+        with torch.cuda.device(dev):
+            code = lib.rtproj_create_sparse(ctypes.byref(h), self.m, self.n, self.nnz, _dev_ptr(row_ptr),
+                                            _dev_ptr(col_idx), _dev_ptr(val), r, ptr(U), ptr(V), self.l_max,
+                                            self.k_max, _dev_ptr(self.workspace), ctypes.c_size_t(int(nbytes)),
+                                            ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(self.opts))
+        _check(code, "rtproj_create_sparse")
+        self._h = h
+
+    def set_scaling(self, d):
+        raise RtprojError(9, "set_scaling on a sparse handle")
 
 
 def launch_count() -> int:

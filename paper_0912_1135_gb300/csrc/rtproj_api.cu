@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 using namespace rtp;
 
@@ -291,6 +292,63 @@ namespace {
 size_t mixed_workspace(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts& o) {
     return rtp::mixed_bytes(m, n, l_max, k_max, o);
 }
+
+constexpr int64_t kMaxLowRank = 64;
+constexpr int64_t kMaxNnz = (int64_t)1 << 40;
+
+// A new handle over the caller's workspace with the float64 form's layout L bound.
+rtproj_ctx* bind_handle(int64_t m, int64_t n, int64_t l_max, int64_t k_max, void* workspace, size_t ws_bytes,
+                        void* stream, const rtproj_opts& o, const Layout& L) {
+    rtproj_ctx* h = new (std::nothrow) rtproj_ctx();
+    if (!h) return nullptr;
+    h->m = m; h->n = n; h->l_max = l_max; h->k_max = k_max;
+    h->ws = (char*)workspace; h->ws_bytes = ws_bytes;
+    h->stream = (cudaStream_t)stream;
+    h->opts = o;
+    h->dtype = o.dtype;
+    h->spin_limit = o.spin_limit_cycles;
+    char* b = h->ws;
+    h->status = (int*)(b + L.status);
+    h->a_status_dev = h->status + 8;
+    h->S = (double*)(b + L.S);
+    h->qr_work = (double*)(b + L.qr_work);
+    h->perm = (int32_t*)(b + L.perm);
+    h->R = (double*)(b + L.R);
+    h->RinvT = (double*)(b + L.RinvT);
+    h->Lc = (double*)(b + L.Lc);
+    h->Lt = (double*)(b + L.Lt);
+    h->T1 = (double*)(b + L.T1);
+    h->dinv = (double*)(b + L.dinv);
+    h->W = (double*)(b + L.W);
+    h->part = (double*)(b + L.part);
+    h->part_elems = kPartElems;
+    h->cbuf = (double*)(b + L.cbuf);
+    h->ebuf = (double*)(b + L.ebuf);
+    h->hbuf = (double*)(b + L.hbuf);
+    h->dhbuf = (double*)(b + L.dhbuf);
+    h->sbuf = (double*)(b + L.sbuf);
+    h->A64 = (double*)(b + L.A64);
+    h->B64 = (double*)(b + L.B64);
+    h->normA = (double*)(b + L.normA);
+    h->norm_part = (double*)(b + L.norm_part);
+    h->bnorm = (double*)(b + L.bnorm);
+    h->stats = (unsigned long long*)(b + L.stats);
+    return h;
+}
+
+// The handle's events (and phase timers), the cleared report maxima and status word.
+rtproj_status finish_handle(rtproj_ctx* h) {
+    if (cudaMemsetAsync(h->stats, 0, 16, h->stream) != cudaSuccess) return RTPROJ_ECUDA;
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) return RTPROJ_ECUDA;
+    if (h->opts.timing) {
+        h->timer.enabled = true;
+        for (int i = 0; i < PhaseTimer::kMax; ++i)
+            if (cudaEventCreate(&h->timer.b[i]) != cudaSuccess || cudaEventCreate(&h->timer.e[i]) != cudaSuccess)
+                return RTPROJ_ECUDA;
+    }
+    if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) return RTPROJ_ECUDA;
+    return RTPROJ_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -337,68 +395,87 @@ rtproj_status rtproj_create(rtproj_t* out, int64_t m, int64_t n, const void* A, 
     if (((uintptr_t)workspace) % kAlign) return RTPROJ_EINVAL;
     const Layout L = make_layout(m, n, l_max, k_max, o);
     if (ws_bytes < L.total) return RTPROJ_ENOMEM;
-    rtproj_ctx* h = new (std::nothrow) rtproj_ctx();
+    rtproj_ctx* h = bind_handle(m, n, l_max, k_max, workspace, ws_bytes, stream, o, L);
     if (!h) return RTPROJ_ENOMEM;
-    h->m = m; h->n = n; h->lda = lda; h->l_max = l_max; h->k_max = k_max;
-    h->A_user = A; h->lda_user = lda; h->ws = (char*)workspace; h->ws_bytes = ws_bytes;
-    h->stream = (cudaStream_t)stream;
-    h->opts = o;
-    h->dtype = o.dtype;
-    h->spin_limit = o.spin_limit_cycles;
-    char* b = h->ws;
-    h->status = (int*)(b + L.status);
-    h->a_status_dev = h->status + 8;
-    h->S = (double*)(b + L.S);
-    h->qr_work = (double*)(b + L.qr_work);
-    h->perm = (int32_t*)(b + L.perm);
-    h->R = (double*)(b + L.R);
-    h->RinvT = (double*)(b + L.RinvT);
-    h->Lc = (double*)(b + L.Lc);
-    h->Lt = (double*)(b + L.Lt);
-    h->T1 = (double*)(b + L.T1);
-    h->dinv = (double*)(b + L.dinv);
-    h->W = (double*)(b + L.W);
-    h->part = (double*)(b + L.part);
-    h->part_elems = kPartElems;
-    h->cbuf = (double*)(b + L.cbuf);
-    h->ebuf = (double*)(b + L.ebuf);
-    h->hbuf = (double*)(b + L.hbuf);
-    h->dhbuf = (double*)(b + L.dhbuf);
-    h->sbuf = (double*)(b + L.sbuf);
-    h->A64 = (double*)(b + L.A64);
-    h->B64 = (double*)(b + L.B64);
-    h->normA = (double*)(b + L.normA);
-    h->norm_part = (double*)(b + L.norm_part);
-    h->bnorm = (double*)(b + L.bnorm);
-    h->stats = (unsigned long long*)(b + L.stats);
-    if (form_a(h, nullptr) != RTPROJ_OK || cudaMemsetAsync(h->stats, 0, 16, h->stream) != cudaSuccess) {
-        delete h;
-        return RTPROJ_ECUDA;
-    }
-    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
-        delete h;
-        return RTPROJ_ECUDA;
-    }
-    if (o.timing) {
-        h->timer.enabled = true;
-        for (int i = 0; i < PhaseTimer::kMax; ++i) {
-            if (cudaEventCreate(&h->timer.b[i]) != cudaSuccess || cudaEventCreate(&h->timer.e[i]) != cudaSuccess) {
-                rtproj_destroy(h);
-                return RTPROJ_ECUDA;
-            }
-        }
-    }
-    if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess) {
+    h->A_user = A; h->lda_user = lda; h->lda = lda;
+    if (form_a(h, nullptr) != RTPROJ_OK) {
         rtproj_destroy(h);
         return RTPROJ_ECUDA;
     }
-    if (o.mode == RTPROJ_MIXED_REFINED) {
-        rtproj_status st = mixed_bind(h, b + L.mixed_base, L.mixed_bytes);
+    rtproj_status st = finish_handle(h);
+    if (st == RTPROJ_OK && o.mode == RTPROJ_MIXED_REFINED) {
+        st = mixed_bind(h, h->ws + L.mixed_base, L.mixed_bytes);
         if (st == RTPROJ_OK) st = mixed_prepare_a(h);
-        if (st != RTPROJ_OK) {
-            rtproj_destroy(h);
-            return st;
-        }
+    }
+    if (st != RTPROJ_OK) {
+        rtproj_destroy(h);
+        return st;
+    }
+    *out = h;
+    return RTPROJ_OK;
+}
+
+size_t rtproj_sparse_workspace_bytes(int64_t m, int64_t n, int64_t nnz, int64_t r, int64_t l_max, int64_t k_max,
+                                     const rtproj_opts* opts) {
+    rtproj_opts o;
+    rtproj_default_opts(&o);
+    if (opts) o = *opts;
+    if (m < 1 || n < m || nnz < 0 || r < 0 || l_max < m || l_max > n || k_max < 1 || !valid_opts(o)) return 0;
+    if (m > 4096 || n > (int64_t)1 << 30 || r > kMaxLowRank || r > m || nnz > kMaxNnz || k_max > 65535) return 0;
+    o.mode = RTPROJ_PLAIN_FP64;
+    return make_layout(m, n, l_max, k_max, o).total + sparse_bytes(m, n, nnz, r, l_max, k_max);
+}
+
+rtproj_status rtproj_create_sparse(rtproj_t* out, int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                   const int32_t* col_idx, const double* val, int64_t r, const double* U,
+                                   const double* V, int64_t l_max, int64_t k_max, void* workspace, size_t ws_bytes,
+                                   void* stream, const rtproj_opts* opts) {
+    if (!out) return RTPROJ_EINVAL;
+    *out = nullptr;
+    rtproj_opts o;
+    rtproj_default_opts(&o);
+    if (opts) o = *opts;
+    if (!valid_opts(o)) return RTPROJ_EINVAL;
+    if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || (r > 0 && (!U || !V)) || !workspace) return RTPROJ_EINVAL;
+    if (m < 1 || n < m || nnz < 0 || r < 0 || l_max < m || l_max > n || k_max < 1) return RTPROJ_EINVAL;
+    if (m > 4096 || n > (int64_t)1 << 30 || r > kMaxLowRank || r > m || nnz > kMaxNnz || k_max > 65535)
+        return RTPROJ_EUNSUPPORTED;
+    if (o.dtype != RTPROJ_F64 || o.scalable) return RTPROJ_EUNSUPPORTED;
+    if (((uintptr_t)workspace) % kAlign) return RTPROJ_EINVAL;
+    o.mode = RTPROJ_PLAIN_FP64;   // the sparse form: float64 products, double-double residuals
+    const Layout L = make_layout(m, n, l_max, k_max, o);
+    if (ws_bytes < L.total + sparse_bytes(m, n, nnz, r, l_max, k_max)) return RTPROJ_ENOMEM;
+    // the row pointers bound every later read of col_idx and val: checked here, on the host
+    std::vector<int64_t> rp((size_t)m + 1);
+    if (cudaMemcpyAsync(rp.data(), row_ptr, rp.size() * 8, cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return RTPROJ_ECUDA;
+    if (rp[0] != 0 || rp[m] != nnz) return RTPROJ_EINVAL;
+    for (int64_t i = 0; i < m; ++i)
+        if (rp[i + 1] < rp[i]) return RTPROJ_EINVAL;
+    rtproj_ctx* h = bind_handle(m, n, l_max, k_max, workspace, ws_bytes, stream, o, L);
+    if (!h) return RTPROJ_ENOMEM;
+    h->sparse = true;
+    h->nnz = nnz;
+    h->csr_ptr = row_ptr; h->csr_col = col_idx; h->csr_val = val;
+    h->lr = (int)r; h->lrU = U; h->lrV = V;
+    sparse_bind(h, h->ws + L.total);
+    rtproj_status st = finish_handle(h);
+    if (st == RTPROJ_OK) st = sparse_chunks(h, rp.data());
+    if (st == RTPROJ_OK) st = sparse_prepare(h);
+    if (st == RTPROJ_OK) {
+        // column indices in range and values finite, or the handle is refused
+        int dev_status = 0;
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess ||
+            cudaMemcpy(&dev_status, h->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            st = RTPROJ_ECUDA;
+        else
+            st = (rtproj_status)dev_status;
+    }
+    if (st != RTPROJ_OK) {
+        rtproj_destroy(h);
+        return st;
     }
     *out = h;
     return RTPROJ_OK;
@@ -419,8 +496,9 @@ rtproj_status rtproj_set_scaling(rtproj_t h, const double* d) {
 
 rtproj_status rtproj_sketch(rtproj_t h, uint64_t seed, int64_t l, double* S, int64_t lds) {
     if (!h || !S || l < h->m || l > h->l_max || lds < l) return RTPROJ_EINVAL;
-    rtproj_status st = h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_sketch(h, seed, l, S, lds)
-                                                            : sketch_fp64(h, seed, l, S, lds);
+    rtproj_status st = h->sparse ? sparse_sketch(h, seed, l, S, lds)
+                       : h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_sketch(h, seed, l, S, lds)
+                                                              : sketch_fp64(h, seed, l, S, lds);
     if (st != RTPROJ_OK) return st;
     return cuda_status(cudaStreamSynchronize(h->stream));
 }
@@ -440,12 +518,14 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
         RT_CHECK(cudaMemcpyAsync(h->status, h->a_status_dev, sizeof(int), cudaMemcpyDeviceToDevice, s));
     } else {
         RT_CHECK(cudaMemsetAsync(h->status, 0, sizeof(int), s));
-        RT_CHECK(check_finite(h->A, h->lda, m, (int)h->n, h->status, s));
+        // a sparse A's values were checked at create
+        if (!h->sparse) RT_CHECK(check_finite(h->A, h->lda, m, (int)h->n, h->status, s));
     }
     // 1. S = A G (Eq. 12)
     phase_begin(h, RTPROJ_PHASE_SKETCH);
-    rtproj_status st = h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_sketch(h, seed, l, h->S, l)
-                                                            : sketch_fp64(h, seed, l, h->S, l);
+    rtproj_status st = h->sparse ? sparse_sketch(h, seed, l, h->S, l)
+                       : h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_sketch(h, seed, l, h->S, l)
+                                                              : sketch_fp64(h, seed, l, h->S, l);
     if (st != RTPROJ_OK) return st;
     phase_end(h, RTPROJ_PHASE_SKETCH);
     // 2. S^* = Q R Pi (Eq. 13)
@@ -459,7 +539,12 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
         RT_CHECK(pivoted_qr_cluster(h->S, m, (int)l, l, h->R, h->perm, qr_flag, s, &cluster));
     RT_CHECK(pivoted_qr(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s, h->spin_limit,
                         cluster ? qr_flag : nullptr));
-    const double tol = h->opts.rank_tol > 0 ? h->opts.rank_tol : 64.0 * (double)l * std::ldexp(1.0, -52);
+    // default threshold: 8 times the sketch's relative precision -- 2^-52 in float64, 2^(-8 s)
+    // for the s digits of A that the mixed form's sketch reads
+    const double u_sketch = h->opts.mode == RTPROJ_MIXED_REFINED && !h->sparse
+                                ? std::max(std::ldexp(1.0, -8 * h->opts.sketch_slices), std::ldexp(1.0, -52))
+                                : std::ldexp(1.0, -52);
+    const double tol = h->opts.rank_tol > 0 ? h->opts.rank_tol : 8.0 * u_sketch;
     RT_CHECK(qr_check(h->R, h->perm, m, tol, h->status, s));
     phase_end(h, RTPROJ_PHASE_QR);
     // R^{-*} (the transpose of P^- of Eq. 15, up to Pi)
@@ -469,7 +554,7 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_end(h, RTPROJ_PHASE_FACTOR);
     // 3. X = P^{-1} A A^* P^{-*} (Eq. 14 via steps a-e, as W W^*)
     phase_begin(h, RTPROJ_PHASE_GRAM);
-    st = h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_gram(h) : gram_fp64(h);
+    st = h->sparse ? sparse_gram(h) : h->opts.mode == RTPROJ_MIXED_REFINED ? mixed_gram(h) : gram_fp64(h);
     if (st != RTPROJ_OK) return st;
     phase_end(h, RTPROJ_PHASE_GRAM);
     // 4. X = L L^* (in place of Y = X^{-1}, Eq. 16), T1 = L^{-1} R^{-*}
@@ -511,6 +596,7 @@ rtproj_status rtproj_project(rtproj_t h, const void* B, int64_t ldb, int64_t k, 
         Bd = h->B64;
         ldbd = h->n;
     }
+    if (h->sparse) return sparse_project(h, Bd, ldbd, (int)k, Z, ldz, ROW, ldr, X, ldx);
     if (h->opts.mode == RTPROJ_MIXED_REFINED) return mixed_project(h, Bd, ldbd, (int)k, Z, ldz, ROW, ldr, X, ldx);
     return project_fp64(h, Bd, ldbd, (int)k, Z, ldz, ROW, ldr, X, ldx);
 }

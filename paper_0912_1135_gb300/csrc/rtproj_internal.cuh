@@ -229,6 +229,17 @@ cudaError_t sliced_gemm(const SlicedGemm& g, void* scratch, size_t scratch_bytes
 
 struct rtproj_ctx;
 namespace rtp {
+// Sparse A (k_sparse.cu): workspace bytes beyond the float64 form's layout, binding,
+// the column-compressed copy and ||A||_F at create, and the sparse forms of the sketch,
+// the Gram matrix and the apply.
+size_t sparse_bytes(int64_t m, int64_t n, int64_t nnz, int64_t r, int64_t l_max, int64_t k_max);
+void sparse_bind(rtproj_ctx* h, char* base);
+rtproj_status sparse_chunks(rtproj_ctx* h, const int64_t* rp_host);
+rtproj_status sparse_prepare(rtproj_ctx* h);
+rtproj_status sparse_sketch(rtproj_ctx* h, uint64_t seed, int64_t l, double* S, int64_t lds);
+rtproj_status sparse_gram(rtproj_ctx* h);
+rtproj_status sparse_project(rtproj_ctx* h, const double* B, int64_t ldb, int k, void* Z, int64_t ldz, void* ROW,
+                             int64_t ldr, void* X, int64_t ldx);
 void phase_begin(rtproj_ctx* h, int phase);
 void phase_end(rtproj_ctx* h, int phase);
 // Steps 2-6 of the apply in float64: out = Pi^* T1^* T1 Pi c (c, out: m x k, ld k).
@@ -324,6 +335,32 @@ struct rtproj_ctx {
     long long spin_limit = 4000000000ll;
     int last_passes = 0;
     double norm_A_host = 0.0;
+
+    // sparse A = S + U V (k_sparse.cu): S borrowed in compressed sparse row form, its
+    // column-compressed copy built at create
+    bool sparse = false;
+    int64_t nnz = 0;
+    const int64_t* csr_ptr = nullptr;
+    const int32_t* csr_col = nullptr;
+    const double* csr_val = nullptr;
+    int64_t* csc_ptr = nullptr;       // n + 1
+    int32_t* csc_row = nullptr;       // nnz, ordered by row within each column
+    double* csc_val = nullptr;        // nnz
+    int64_t* csc_cursor = nullptr;    // n (column counts, then scatter cursors)
+    int64_t* scan_tot = nullptr;      // per-block totals of the column scan
+    double* Pminus = nullptr;         // m x m, P^- = Pi^* R^{-1}
+    double* Esp = nullptr;            // m x m, A A^* P^-
+    int lr = 0;                       // rank r of the low-rank term (0: none)
+    const double* lrU = nullptr;      // m x r, borrowed
+    const double* lrV = nullptr;      // r x n, borrowed
+    double* lr_a = nullptr;           // r x max(l_max, m): V G, U^* P^-, V D
+    double* lr_b = nullptr;           // r x k_max: V b or U^* h
+    double* lr_small = nullptr;       // U^* U, V V^* and partial sums (||A||_F)
+    int nchunks = 0;                  // rows cut into chunks of nonzeros for A x
+    int32_t* chunk_row = nullptr;     // row of each chunk
+    int64_t* chunk_beg = nullptr;     // first nonzero of each chunk
+    int32_t* row_chunk = nullptr;     // m + 1: first chunk of each row
+    double* chunk_part = nullptr;     // chunks x k_max double-double partial sums
 
     rtp::PhaseTimer timer;
     int64_t l = 0;

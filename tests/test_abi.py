@@ -69,3 +69,35 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
                            None, ctypes.byref(o)) == 1          # misaligned workspace
     assert L.rtproj_precondition(None, 1, 8) == 1
     assert L.rtproj_null_project(None, None, 0, 1, None, 0) == 1
+
+
+def test_sparse_entry_points_check_arguments_on_the_host(lib):
+    """Sparse handles: workspace sizing is host arithmetic, and every argument error is
+    returned before the device is touched (no GPU here)."""
+    L = rt.load_library()
+    o = rt.make_opts("fp64")
+    sz = L.rtproj_sparse_workspace_bytes(64, 4096, 5 * 4096, 0, 256, 16, ctypes.byref(o))
+    assert sz >= 64 * 4096 * 8 + 5 * 4096 * 12          # D = A^* P^- (n x m) and the CSC copy
+    assert L.rtproj_sparse_workspace_bytes(64, 4096, 5 * 4096, 10, 256, 16, ctypes.byref(o)) > sz
+    assert L.rtproj_sparse_workspace_bytes(64, 4096, 5 * 4096, 65, 256, 16, ctypes.byref(o)) == 0   # r > 64
+    assert L.rtproj_sparse_workspace_bytes(64, 4096, -1, 0, 256, 16, ctypes.byref(o)) == 0
+    assert L.rtproj_sparse_workspace_bytes(64, 4096, 10, 0, 256, 70000, ctypes.byref(o)) == 0        # k_max
+    h = ctypes.c_void_p()
+    p = ctypes.c_void_p(256)
+    args = lambda **kw: dict(dict(m=8, n=16, nnz=40, rp=p, ci=p, v=p, r=0, U=None, V=None, l=8, k=1, ws=p,
+                                  wsb=1 << 30, o=o), **kw)
+
+    def create(a):
+        return L.rtproj_create_sparse(ctypes.byref(h), a["m"], a["n"], a["nnz"], a["rp"], a["ci"], a["v"], a["r"],
+                                      a["U"], a["V"], a["l"], a["k"], a["ws"], a["wsb"], None, ctypes.byref(a["o"]))
+    assert create(args(rp=None)) == 1
+    assert create(args(v=None)) == 1
+    assert create(args(r=2)) == 1                        # U, V missing
+    assert create(args(n=4)) == 1                        # n < m
+    assert create(args(r=9, U=p, V=p)) == 9              # r > m
+    assert create(args(k=70000)) == 9
+    assert create(args(ws=ctypes.c_void_p(257))) == 1
+    assert create(args(wsb=16)) == 7
+    o32 = rt.make_opts("fp64")
+    o32.dtype = 1
+    assert create(args(o=o32)) == 9

@@ -133,6 +133,48 @@ def paper_test_matrix(m: int, n: int, kappa: float, seed: int, return_parts: boo
     return a
 
 
+def paper_test_csr(m: int, n: int, kappa: float, seed: int):
+    """The same matrix as ``paper_test_matrix(m, n, kappa, seed)`` (same B, same
+    permutations), in compressed sparse row form without densifying: row i of A is row
+    pu[i] of [B|...|B], whose nonzeros sit in columns t m + (pu[i] + o) mod m, o = -2..2,
+    of each block t, moved to column pv[t m + k]. Entries within a row are ordered by
+    block, then by offset o (not by column). Returns (row_ptr int64, col_idx int32,
+    val float64, b, pu, pv)."""
+    if n % m != 0:
+        raise ValueError("n must be a multiple of m")
+    if m < 5:
+        raise ValueError("the pentadiagonal stencil needs m >= 5")
+    rng = np.random.default_rng(seed)
+    d = 16.0 / (float(kappa) - 1.0)
+    b = np.zeros((m, m))
+    for k in range(m):
+        b[(k - 2) % m, k] = 1.0
+        b[(k - 1) % m, k] = -4.0
+        b[k, k] = 6.0 + d
+        b[(k + 1) % m, k] = -4.0
+        b[(k + 2) % m, k] = 1.0
+    pu = rng.permutation(m)
+    pv = rng.permutation(n)
+    q = n // m
+    offs = np.arange(-2, 3)
+    j = pu[:, None]                                       # row of [B|...|B] behind row i
+    k = (j + offs[None, :]) % m                           # m x 5: its nonzero columns in B
+    cols = (np.arange(q)[None, :, None] * m + k[:, None, :])      # m x q x 5, in [B|...|B]
+    col_idx = pv[cols].reshape(m, 5 * q).astype(np.int32)
+    val = np.broadcast_to(b[j, k][:, None, :], (m, q, 5)).reshape(m, 5 * q).copy()
+    row_ptr = np.arange(m + 1, dtype=np.int64) * (5 * q)
+    return row_ptr, col_idx.reshape(-1), val.reshape(-1), b, pu, pv
+
+
+def paper_low_rank(m: int, n: int, seed: int, r: int = 10):
+    """The low-rank term of the paper's Eq. 22: E F / sqrt(m n) with E (m x r) and F
+    (r x n) i.i.d. standard normal, returned as U = E / sqrt(m n) and V = F."""
+    rng = np.random.default_rng(seed)
+    E = rng.standard_normal((m, r))
+    F = rng.standard_normal((r, n))
+    return np.ascontiguousarray(E / np.sqrt(float(m) * float(n))), np.ascontiguousarray(F)
+
+
 def rhs(k: int, n: int, seed: int, dtype=np.float64) -> np.ndarray:
     """k right-hand sides with i.i.d. N(0,1) entries, as a k x n row-major array."""
     rng = np.random.default_rng(seed)
