@@ -270,8 +270,11 @@ def time_steps_pipelined(torch, Ps, Bt, seed, l, steps, stream, Zs):
         P.stream.wait_stream(stream)
     for i in range(steps):
         P = Ps[i % len(Ps)]
-        P.precondition(seed + i, l)
-        P.null_project(Bt, out=Zs[i % len(Ps)])
+        # issued with the handle's stream current, so that the binding adds no wait on
+        # another stream: consecutive steps are ordered only through their own handle
+        with torch.cuda.stream(P.stream):
+            P.precondition(seed + i, l)
+            P.null_project(Bt, out=Zs[i % len(Ps)])
     for P in Ps:
         stream.wait_stream(P.stream)
     ev1.record(stream)
@@ -436,8 +439,9 @@ def run_ours(args, w, world, rank, local):
         "config": {"workload": w.name, "mode": args.mode, "m": w.m, "n": w.n, "k": w.k, "l": w.l,
                    "kappa": 1.0 / w.sigma_min, "omega": "gaussian (Box-Muller on Philox4x32-10, 2^-12 grid)",
                    "step": "precondition(seed, l) + null_project(k RHS)",
-                   "pipeline": (f"{args.pipeline} handles on {args.pipeline} streams: a step's apply overlaps the next "
-                                "step's precondition") if args.pipeline > 1 else "one handle, steps in order",
+                   "pipeline": (f"up to {args.pipeline} consecutive steps in flight, each on its own handle and "
+                                "stream: one step's latency-bound QR and Cholesky overlap the others' tensor-core "
+                                "products") if args.pipeline > 1 else "one handle, steps in order",
                    "l2": f"inputs larger than L2 (A is {A.nbytes / 1e6:.0f} MB float64)",
                    "parallelism": f"replicas x{world}", "options": wopts},
         "phase_ms_per_step": {p: phase_ms[p] / args.steps for p in phase_ms if phase_cnt[p]},
@@ -583,20 +587,22 @@ def e2e(torch, rt, A, B, w, args, dev):
     handle's latched status is read after the timed region."""
     Ah = torch.from_numpy(A).pin_memory()
     Bh = torch.from_numpy(B).pin_memory()
-    Zh = [torch.empty(B.shape, dtype=torch.float64).pin_memory() for _ in range(2)]
+    npipe = max(1, min(args.pipeline, 4))               # steps in flight, one compute stream each
+    Zh = [torch.empty(B.shape, dtype=torch.float64).pin_memory() for _ in range(npipe)]
     steps = max(1, min(args.steps, 15))
     comp = torch.cuda.current_stream(dev)
+    comps = [torch.cuda.Stream(dev) for _ in range(npipe)]
     copy = torch.cuda.Stream(dev)
     d2h = torch.cuda.Stream(dev)
-    Ad = [torch.empty(A.shape, dtype=torch.float64, device=dev) for _ in range(2)]
-    Bd = [torch.empty(B.shape, dtype=torch.float64, device=dev) for _ in range(2)]
-    copied = [torch.cuda.Event() for _ in range(2)]
-    freed = [torch.cuda.Event() for _ in range(2)]
+    Ad = [torch.empty(A.shape, dtype=torch.float64, device=dev) for _ in range(npipe)]
+    Bd = [torch.empty(B.shape, dtype=torch.float64, device=dev) for _ in range(npipe)]
+    copied = [torch.cuda.Event() for _ in range(npipe)]
+    freed = [torch.cuda.Event() for _ in range(npipe)]
     for ev in freed:
         ev.record(comp)
 
     def issue_copy(i):
-        s = i % 2
+        s = i % npipe
         with torch.cuda.stream(copy):
             copy.wait_event(freed[s])          # the buffers' previous step is done with them
             Ad[s].copy_(Ah, non_blocking=True)
@@ -606,13 +612,15 @@ def e2e(torch, rt, A, B, w, args, dev):
     handles = []
 
     def run(i):
-        s = i % 2
-        comp.wait_event(copied[s])
-        P = rt.Projector(Ad[s], l_max=w.l, k_max=w.k, mode=args.mode, stream=comp, async_=1)
-        P.precondition(w.seed_omega + i, w.l)
-        Z = P.null_project(Bd[s])
-        handles.append(P)
-        freed[s].record(comp)
+        s = i % npipe
+        cs = comps[s]
+        with torch.cuda.stream(cs):
+            cs.wait_event(copied[s])
+            P = rt.Projector(Ad[s], l_max=w.l, k_max=w.k, mode=args.mode, stream=cs, async_=1)
+            P.precondition(w.seed_omega + i, w.l)
+            Z = P.null_project(Bd[s])
+            handles.append(P)
+            freed[s].record(cs)
         d2h.wait_event(freed[s])
         with torch.cuda.stream(d2h):
             Zh[s].copy_(Z, non_blocking=True)
@@ -634,8 +642,9 @@ def e2e(torch, rt, A, B, w, args, dev):
         P.close()
     return {"value": w.k * steps / wall, "unit": "projections/s", "h2d_bytes_per_step": int(A.nbytes + B.nbytes),
             "d2h_bytes_per_step": int(B.nbytes), "steps": steps, "handles_with_nonzero_status": bad,
-            "pipelining": "the next step's H2D copies and the previous step's D2H copy overlap the "
-                          "current step's compute (second and third streams); asynchronous handles"}
+            "pipelining": f"consecutive steps compute on {npipe} rotating streams; the next step's H2D "
+                          "copies and the previous step's D2H copy overlap the compute (two more streams); "
+                          "asynchronous handles"}
 
 
 def _family_errors(torch, rt, dev, m, n, l, kappa, mode, nb=100, seed=5, **kw):
@@ -861,10 +870,13 @@ def _sparse_row(torch, rt, dev, m, n, l, kappa, low_rank, nb=100, seed=5, refine
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     out = {"m": m, "n": n, "l": l, "kappa": kappa, "nnz": int(len(v)), "low_rank": 10 if low_rank else 0}
     with rt.SparseProjector(t(rp), t(ci), t(v), n, U=t(U) if low_rank else None, V=t(V) if low_rank else None,
-                            l_max=l, k_max=nb, refine_passes=refine[0], refine_tol=refine[1]) as P:
+                            l_max=l, k_max=nb, refine_passes=refine[0], refine_tol=refine[1], timing=1) as P:
         Bt = t(B)
         P.precondition(seed + 2, l)
         P.null_project(Bt[:1])
+        P.timings()
+        P.precondition(seed + 2, l)
+        out["precondition_phases_ms"] = {k: round(v[0], 3) for k, v in P.timings().items() if v[1]}
         stream = torch.cuda.current_stream(dev)
         ev[0].record(stream)
         P.precondition(seed + 2, l)
@@ -940,7 +952,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the float64-form comparison")
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
-    ap.add_argument("--pipeline", type=int, default=2,
+    ap.add_argument("--pipeline", type=int, default=4,
                     help="handles (and streams) the timed steps rotate over; > 1 overlaps consecutive steps")
     ap.add_argument("--study", choices=["accuracy", "variates", "batch", "sparse"], default=None,
                     help="run a study (Section 5 accuracy; variates and sketch sizes) instead of the bench")

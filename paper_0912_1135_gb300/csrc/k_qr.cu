@@ -246,8 +246,18 @@ __device__ __forceinline__ void publish_best(const PqrDev& p, int b, int G, int 
 // e.g. 2048 x 4128): each CTA updates its own columns in place, readers take the pivot
 // column straight from S through L2 (no staging copies), and the retired column's diagonal
 // entry is kept in shared memory so that no reader sees a half-written pivot column.
+// Threads per CTA: 4 warps when the columns sit in shared memory (one warp per column at
+// cpc <= 4); 16 when they stay in global memory, so that a CTA's columns (cpc up to 27 at
+// m = 4096) are updated by many warps at once and their L2 loads overlap.
 template <bool GLOBAL_COLS>
-__global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) {
+struct PqrShape {
+    static constexpr int NT = GLOBAL_COLS ? 512 : PQ_THREADS;
+    static constexpr int NW = NT / 32;
+};
+
+template <bool GLOBAL_COLS>
+__global__ void __launch_bounds__(PqrShape<GLOBAL_COLS>::NT, 1) qr_persistent_kernel(PqrDev p) {
+    constexpr int NT = PqrShape<GLOBAL_COLS>::NT, NW = PqrShape<GLOBAL_COLS>::NW;
     extern __shared__ double smem_d[];
     const int l = p.l, m = p.m, cpc = p.cpc;
     const int64_t cs = GLOBAL_COLS ? p.lds : (int64_t)l;                        // column stride
@@ -256,8 +266,8 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
     __shared__ double nsq[PQ_MAXC];        // squared norm of rows j+1 .. l-1 (exact, this step)
     __shared__ double alphaq[PQ_MAXC];     // GLOBAL_COLS: the retired column's diagonal entry
     __shared__ int posq[PQ_MAXC];          // step at which the column was retired, -1 while active
-    __shared__ unsigned long long redb[2 * PQ_WARPS];
-    __shared__ int redi[2 * PQ_WARPS];
+    __shared__ unsigned long long redb[2 * NW];
+    __shared__ int redi[2 * NW];
     __shared__ int ok_s;
     const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (p.run_if && *(volatile const int*)p.run_if == 0) return;   // the same value for every CTA
@@ -267,13 +277,13 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
 
     if (!GLOBAL_COLS)
         for (int q = 0; q < nc; ++q)
-            for (int i = t; i < l; i += PQ_THREADS) {
+            for (int i = t; i < l; i += NT) {
                 const double x = p.S[(int64_t)(c0 + q) * p.lds + i];
                 cols[(size_t)q * l + i] = x;
                 p.slots[((size_t)b * cpc + q) * l + i] = x;           // step 0's staging copy
             }
     __syncthreads();
-    for (int q = warp; q < nc; q += PQ_WARPS) {
+    for (int q = warp; q < nc; q += NW) {
         const double* c = cols + (size_t)q * cs;
         double s0 = 0.0, s1 = 0.0;
         int i = lane;
@@ -299,7 +309,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         // global pivot: largest squared norm, lowest column index on ties
         unsigned long long best = 0;
         int bi = m;
-        for (int g = t; g < G; g += PQ_THREADS) {
+        for (int g = t; g < G; g += NT) {
             const unsigned long long x = sq_bits(__ldcg(p.bval + par * G + g));
             const int i = __ldcg(p.bidx + par * G + g);
             if (i < m && (bi == m || x > best || (x == best && i < bi))) { best = x; bi = i; }
@@ -310,15 +320,15 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
         }
-        if (lane == 0) { redb[par * PQ_WARPS + warp] = best; redi[par * PQ_WARPS + warp] = bi; }
+        if (lane == 0) { redb[par * NW + warp] = best; redi[par * NW + warp] = bi; }
         __syncthreads();
         // every thread combines the warps' results (double-buffered by step parity, so no
         // second barrier is needed before they are overwritten)
-        unsigned long long bb = redb[par * PQ_WARPS];
-        int ii = redi[par * PQ_WARPS];
-        for (int w = 1; w < PQ_WARPS; ++w) {
-            const unsigned long long xb = redb[par * PQ_WARPS + w];
-            const int xi = redi[par * PQ_WARPS + w];
+        unsigned long long bb = redb[par * NW];
+        int ii = redi[par * NW];
+        for (int w = 1; w < NW; ++w) {
+            const unsigned long long xb = redb[par * NW + w];
+            const int xi = redi[par * NW + w];
             if (xi < m && (ii == m || xb > bb || (xb == bb && xi < ii))) { bb = xb; ii = xi; }
         }
         if (ii >= m) { alive = false; break; }             // cannot happen while columns remain
@@ -332,7 +342,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         double vr[PQ_VLOAD];
 #pragma unroll
         for (int k = 0; k < PQ_VLOAD; ++k) {
-            const int i = j + t + k * PQ_THREADS;
+            const int i = j + t + k * NT;
             vr[k] = i < l ? __ldcg(slot + i) : 0.0;
         }
         const double x0 = __ldcg(slot + j);
@@ -344,10 +354,10 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         }
 #pragma unroll
         for (int k = 0; k < PQ_VLOAD; ++k) {
-            const int i = j + t + k * PQ_THREADS;
+            const int i = j + t + k * NT;
             if (i < l) v[i - j] = i == j ? x0 - alpha : vr[k];
         }
-        for (int i = j + t + PQ_VLOAD * PQ_THREADS; i < l; i += PQ_THREADS) v[i - j] = __ldcg(slot + i);
+        for (int i = j + t + PQ_VLOAD * NT; i < l; i += NT) v[i - j] = __ldcg(slot + i);
         if (t == 0 && piv >= c0 && piv < c0 + nc) {
             const int q = piv - c0;
             if (GLOBAL_COLS) alphaq[q] = alpha;
@@ -360,33 +370,49 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         // 3. each active column: w = beta v^* c, c <- c - w v (row j is the R entry), the
         //    squared norm of rows j+1 .. l-1 and their copy to the staging slot of step j+1
         double* next = p.slots + (size_t)(par ^ 1) * slot_par;
-        for (int q = warp; q < nc; q += PQ_WARPS) {
+        for (int q = warp; q < nc; q += NW) {
             if (posq[q] >= 0) continue;
             double* c = cols + (size_t)q * cs + j;
-            double wa = 0.0, wb = 0.0;
+            // four independent loads and partial sums per lane and pass (latency overlap)
+            double wa0 = 0.0, wa1 = 0.0, wa2 = 0.0, wa3 = 0.0;
             int i = lane;
-            for (; i + 32 < len; i += 64) {
-                wa = fma(v[i], c[i], wa);
-                wb = fma(v[i + 32], c[i + 32], wb);
+            for (; i + 96 < len; i += 128) {
+                const double c0 = c[i], c1 = c[i + 32], c2 = c[i + 64], c3 = c[i + 96];
+                wa0 = fma(v[i], c0, wa0);
+                wa1 = fma(v[i + 32], c1, wa1);
+                wa2 = fma(v[i + 64], c2, wa2);
+                wa3 = fma(v[i + 96], c3, wa3);
             }
-            if (i < len) wa = fma(v[i], c[i], wa);
-            const double w = warp_sum(wa + wb) * beta;
+            for (; i < len; i += 32) wa0 = fma(v[i], c[i], wa0);
+            const double w = warp_sum((wa0 + wa1) + (wa2 + wa3)) * beta;
             double* dst = next + ((size_t)b * cpc + q) * l + j;
-            double s0 = 0.0, s1 = 0.0;
-            for (i = 1 + lane; i < len; i += 64) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (i = 1 + lane; i + 96 < len; i += 128) {
+                const double c0 = c[i], c1 = c[i + 32], c2 = c[i + 64], c3 = c[i + 96];
+                const double x0 = fma(-w, v[i], c0), x1 = fma(-w, v[i + 32], c1);
+                const double x2 = fma(-w, v[i + 64], c2), x3 = fma(-w, v[i + 96], c3);
+                c[i] = x0;
+                c[i + 32] = x1;
+                c[i + 64] = x2;
+                c[i + 96] = x3;
+                if (!GLOBAL_COLS) {
+                    dst[i] = x0;
+                    dst[i + 32] = x1;
+                    dst[i + 64] = x2;
+                    dst[i + 96] = x3;
+                }
+                s0 = fma(x0, x0, s0);
+                s1 = fma(x1, x1, s1);
+                s2 = fma(x2, x2, s2);
+                s3 = fma(x3, x3, s3);
+            }
+            for (; i < len; i += 32) {
                 const double x = fma(-w, v[i], c[i]);
                 c[i] = x;
                 if (!GLOBAL_COLS) dst[i] = x;
                 s0 = fma(x, x, s0);
-                const int i2 = i + 32;
-                if (i2 < len) {
-                    const double y = fma(-w, v[i2], c[i2]);
-                    c[i2] = y;
-                    if (!GLOBAL_COLS) dst[i2] = y;
-                    s1 = fma(y, y, s1);
-                }
             }
-            const double ssq = warp_sum(s0 + s1);
+            const double ssq = warp_sum((s0 + s1) + (s2 + s3));
             if (lane == 0) {
                 c[0] = fma(-w, v[0], c[0]);
                 nsq[q] = ssq;
@@ -402,7 +428,7 @@ __global__ void __launch_bounds__(PQ_THREADS, 1) qr_persistent_kernel(PqrDev p) 
         const int pos = posq[q];
         if (pos < 0) continue;
         const double* c = cols + (size_t)q * cs;
-        for (int i = t; i < m; i += PQ_THREADS)
+        for (int i = t; i < m; i += NT)
             p.R[(int64_t)i * m + pos] = i < pos ? c[i] : i == pos ? (GLOBAL_COLS ? alphaq[q] : c[i]) : 0.0;
     }
 }
@@ -507,10 +533,11 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
         const bool in_smem = smem_shared + 4096 <= (size_t)smem_optin;
         const size_t smem = in_smem ? smem_shared : smem_global;
         const void* kern = in_smem ? (const void*)qr_persistent_kernel<false> : (const void*)qr_persistent_kernel<true>;
+        const int nt = in_smem ? PqrShape<false>::NT : PqrShape<true>::NT;
         if (cpc <= PQ_MAXC && G <= PQ_MAX_G && smem + 4096 <= (size_t)smem_optin) {
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             int per_sm = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PQ_THREADS, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
             if (per_sm >= 1 && G <= per_sm * sms) {
                 PqrDev p;
                 p.S = S; p.m = m; p.l = l; p.lds = lds; p.R = R; p.perm = perm; p.cpc = cpc;
@@ -527,7 +554,7 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
                 if (e != cudaSuccess) return e;
                 void* args[] = {&p};
-                e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(PQ_THREADS), args, smem, s);
+                e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(nt), args, smem, s);
                 note_launch();
                 if (e == cudaSuccess) return cudaGetLastError();
                 cudaGetLastError();   // clear and fall back

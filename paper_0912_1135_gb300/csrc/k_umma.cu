@@ -10,10 +10,15 @@
 // every 128 k: for every level up to 7 each float32 partial sum stays below 2^24, so
 // those level sums are exact; levels 8 and 9 (relative weight 2^-64 and below) may
 // round by a unit of their own scale. The readout folds the level sums into two int64
-// words per entry,
-//   hi = sum_{g<=4} L_g 2^{8(4-g)},  lo = sum_{5<=g<=9} L_g 2^{8(9-g)}  (lo kept below 2^40),
-// so that sum_k A B = 2^{ea+eb-86} (hi 2^40 + lo) exactly up to the digit truncation.
-// Split-K partials stay in int64 and are summed in 128-bit integers by the reduce kernel.
+// words per entry. Level g sits at position P = g + 1 of a ten-position fixed point (level
+// 9, used only with terms = 10 and already inexact, is floored to the unit 2^8 of P = 10):
+//   hi = sum_{P<=4} L_g 2^{8(4-P)},  lo = sum_{5<=P<=9} L_g 2^{8(9-P)} (+ floor(L_9 / 2^8))
+// with lo kept below 2^40, so that sum_k A B = 2^{ea+eb-78} (hi 2^40 + lo) exactly up to the
+// digit truncation. Every k adds at most 2^78 to |hi 2^40 + lo| < 2^103, so hi cannot
+// overflow while a split's K stays below 2^25; choose_splits keeps every split within that
+// bound where the scratch allows. (Position offset 1 rather than 0 buys the factor 2^8.)
+// Split-K partials are summed in 128-bit integers by the reduce kernel and converted to
+// float64 from all 128 bits.
 //
 // CTA: 128 threads; tile 128 (A rows, MMA M) x 32 (B rows, MMA N); K block 64 (one
 // 128-byte swizzle row per operand row). Thread 0 issues the MMAs; all threads stage
@@ -143,24 +148,24 @@ __device__ __forceinline__ int exact_f2i(float x) {
 // Adds the level-g sums of one 128-row x 32-column readout (r) into the int64 words.
 // When every value of the warp's readout is below 2^22 in magnitude (the usual case) one
 // magic-offset add converts each; otherwise the two-part exact_f2i is used.
-__device__ __forceinline__ void fold_level(int g, const uint32_t (&r)[32], long long (&hi)[32], long long (&lo)[32]) {
+// The position offset of the fixed point (see the top); the same for every product.
+__host__ __device__ constexpr int level_offset(int /*terms*/) { return 1; }
+constexpr long long kSplitKCap = 1ll << 25;   // largest K of one split (see the top)
+
+__device__ __forceinline__ void fold_level(int g, int D, const uint32_t (&r)[32], long long (&hi)[32],
+                                           long long (&lo)[32]) {
     bool small = true;
 #pragma unroll
     for (int j = 0; j < 32; ++j) small &= fabsf(__uint_as_float(r[j])) < 4194304.0f;
     const bool fast = __all_sync(0xffffffffu, small);
-    const int sh = g <= 4 ? 8 * (4 - g) : 8 * (9 - g);
-    if (fast) {
+    const int P = g + D;
+    const int sh = P <= 4 ? 8 * (4 - P) : P <= 9 ? 8 * (9 - P) : 0;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int v = __float_as_int(__fadd_rn(__uint_as_float(r[j]), 12582912.0f)) - 0x4B400000;
-            if (g <= 4) hi[j] += (long long)v << sh; else lo[j] += (long long)v << sh;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int v = exact_f2i(__uint_as_float(r[j]));
-            if (g <= 4) hi[j] += (long long)v << sh; else lo[j] += (long long)v << sh;
-        }
+    for (int j = 0; j < 32; ++j) {
+        int v = fast ? __float_as_int(__fadd_rn(__uint_as_float(r[j]), 12582912.0f)) - 0x4B400000
+                     : exact_f2i(__uint_as_float(r[j]));
+        if (P > 9) v >>= 8;                           // floor to the unit 2^8 of position 10
+        if (P <= 4) hi[j] += (long long)v << sh; else lo[j] += (long long)v << sh;
     }
 }
 
@@ -172,11 +177,18 @@ __device__ __forceinline__ void fold_level(int g, const uint32_t (&r)[32], long 
 // every sign and magnitude: the earlier form with a branch per shift range took about
 // 1000 cycles per element in the epilogue. A result outside the normal range is delegated
 // to ldexp.
+__device__ __forceinline__ double u128_to_double(unsigned long long H, unsigned long long L, int e);
+
 __device__ __forceinline__ double words_to_double(long long hi, long long lo, int e) {
     // V = hi * 2^40 + lo as a 128-bit two's complement value (H:L)
-    unsigned long long L = ((unsigned long long)hi << 40) + (unsigned long long)lo;
+    const unsigned long long L = ((unsigned long long)hi << 40) + (unsigned long long)lo;
     const unsigned long long carry = L < ((unsigned long long)hi << 40) ? 1ull : 0ull;
-    unsigned long long H = (unsigned long long)(hi >> 24) + (unsigned long long)(lo >> 63) + carry;
+    const unsigned long long H = (unsigned long long)(hi >> 24) + (unsigned long long)(lo >> 63) + carry;
+    return u128_to_double(H, L, e);
+}
+
+// V * 2^e for the 128-bit two's-complement integer V = (H:L), rounded to nearest even.
+__device__ __forceinline__ double u128_to_double(unsigned long long H, unsigned long long L, int e) {
     // |V| by a masked negation (no branch: the lanes of a warp hold values of either sign)
     const unsigned long long sg = (unsigned long long)((long long)H >> 63);
     L ^= sg;
@@ -249,9 +261,9 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 
-// Level g of the 10-level fixed point goes to word hi (g <= 4) or lo (g >= 5), scaled by
-// 2^level_shift(g).
-__host__ __device__ constexpr int level_shift(int g) { return g <= 4 ? 8 * (4 - g) : 8 * (9 - g); }
+// Position P of the fixed point goes to word hi (P <= 4) or lo (P >= 5), scaled by
+// 2^level_shift(P); position 10 enters lo floored by 2^8 (shift 0 of v >> 8).
+__host__ __device__ constexpr int level_shift(int P) { return P <= 4 ? 8 * (4 - P) : P <= 9 ? 8 * (9 - P) : 0; }
 
 // acc += v * 2^SH modulo 2^64: one wide multiply-add (SH < 32) or one add to the upper word.
 template <int SH>
@@ -263,12 +275,16 @@ __device__ __forceinline__ void add_shifted(unsigned long long& acc, int v) {
     }
 }
 
-// Sum over levels [G0, G1) that land in word `hi_word` of 0x4B400000 * 2^level_shift, modulo
-// 2^64: the offset that the magic-number conversion adds to every value.
-__host__ __device__ constexpr unsigned long long magic_bias(int G0, int G1, bool hi_word) {
+// Sum over levels [G0, G1) (positions g + D) that land in word `hi_word` of
+// 0x4B400000 * 2^level_shift, modulo 2^64: the offset that the magic-number conversion
+// adds to every value (0x4B400000 / 2^8 at position 10, exactly).
+__host__ __device__ constexpr unsigned long long magic_bias(int G0, int G1, bool hi_word, int D) {
     unsigned long long b = 0;
-    for (int g = G0; g < G1; ++g)
-        if ((g <= 4) == hi_word) b += 0x4B400000ull << level_shift(g);
+    for (int g = G0; g < G1; ++g) {
+        const int P = g + D;
+        if ((P <= 4) != hi_word) continue;
+        b += P > 9 ? (0x4B400000ull >> 8) : (0x4B400000ull << level_shift(P));
+    }
     return b;
 }
 
@@ -276,27 +292,28 @@ __host__ __device__ constexpr unsigned long long magic_bias(int G0, int G1, bool
 // its word. Every value enters with the same offset 0x4B400000: the raw bits of
 // x + 1.5 * 2^23 (FAST, exact when |x| < 2^22) or the exact integer plus that offset; the
 // sum of the offsets is removed once per chunk.
-template <int L, bool FAST, int CB, int NCOL>
+template <int P, bool FAST, int CB, int NCOL>
 __device__ __forceinline__ void fold_one(const uint32_t (&r)[16], unsigned long long (&hi)[NCOL],
                                          unsigned long long (&lo)[NCOL]) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
         const int v = FAST ? __float_as_int(__fadd_rn(__uint_as_float(r[j]), 12582912.0f))
                            : exact_f2i(__uint_as_float(r[j])) + 0x4B400000;
-        if constexpr (L <= 4) add_shifted<level_shift(L)>(hi[CB * 16 + j], v);
-        else add_shifted<level_shift(L)>(lo[CB * 16 + j], v);
+        if constexpr (P <= 4) add_shifted<level_shift(P)>(hi[CB * 16 + j], v);
+        else if constexpr (P <= 9) add_shifted<level_shift(P)>(lo[CB * 16 + j], v);
+        else add_shifted<0>(lo[CB * 16 + j], v >> 8);   // v > 0: the offset keeps it positive
     }
 }
-template <int L0, bool FAST, int CB, int NCOL, int... I>
+template <int P0, bool FAST, int CB, int NCOL, int... I>
 __device__ __forceinline__ void fold_levels(const uint32_t (&r)[sizeof...(I)][16], unsigned long long (&hi)[NCOL],
                                             unsigned long long (&lo)[NCOL], std::integer_sequence<int, I...>) {
-    (fold_one<L0 + I, FAST, CB, NCOL>(r[I], hi, lo), ...);
+    (fold_one<P0 + I, FAST, CB, NCOL>(r[I], hi, lo), ...);
 }
 
 // Loads levels L0 .. L0+NG-1 of one 16-column unit (TMEM address `addr` + level * tn),
 // checks them, and folds them in; with `release` the TMEM buffer is handed back to the
 // MMA warp as soon as the values are in registers.
-template <int L0, int NG, int CB, int NCOL>
+template <int L0, int NG, int CB, int NCOL, int D>
 __device__ __forceinline__ void fold_group(uint32_t addr, uint32_t tn, unsigned long long (&hi)[NCOL],
                                            unsigned long long (&lo)[NCOL], bool release, uint64_t* empty_bar) {
     uint32_t r[NG][16];
@@ -313,9 +330,9 @@ __device__ __forceinline__ void fold_group(uint32_t addr, uint32_t tn, unsigned 
 #pragma unroll
         for (int j = 0; j < 16; ++j) mx = fmaxf(mx, fabsf(__uint_as_float(r[g][j])));
     if (__all_sync(0xffffffffu, mx < 4194304.0f))
-        fold_levels<L0, true, CB, NCOL>(r, hi, lo, std::make_integer_sequence<int, NG>{});
+        fold_levels<L0 + D, true, CB, NCOL>(r, hi, lo, std::make_integer_sequence<int, NG>{});
     else
-        fold_levels<L0, false, CB, NCOL>(r, hi, lo, std::make_integer_sequence<int, NG>{});
+        fold_levels<L0 + D, false, CB, NCOL>(r, hi, lo, std::make_integer_sequence<int, NG>{});
 }
 
 // Level groups of one chunk readout: 16-column units in order, levels in groups of GS.
@@ -325,7 +342,7 @@ __device__ __forceinline__ void readout_rec(uint32_t addr0, uint32_t tn, unsigne
     constexpr int GS = NCOL == 16 ? 5 : 1;
     constexpr int NG = (TERMS - L0) < GS ? (TERMS - L0) : GS;
     constexpr bool last = (CB == NCOL / 16 - 1) && (L0 + NG >= TERMS);
-    fold_group<L0, NG, CB, NCOL>(addr0 + CB * 16, tn, hi, lo, last, empty_bar);
+    fold_group<L0, NG, CB, NCOL, level_offset(TERMS)>(addr0 + CB * 16, tn, hi, lo, last, empty_bar);
     if constexpr (L0 + NG < TERMS) readout_rec<TERMS, NCOL, CB, L0 + NG>(addr0, tn, hi, lo, empty_bar);
     else if constexpr (CB + 1 < NCOL / 16) readout_rec<TERMS, NCOL, CB + 1, 0>(addr0, tn, hi, lo, empty_bar);
 }
@@ -336,7 +353,8 @@ template <int TERMS, int NCOL>
 __device__ __forceinline__ void readout(uint32_t addr0, uint32_t tn, unsigned long long (&hi)[NCOL],
                                         unsigned long long (&lo)[NCOL], uint64_t* empty_bar) {
     readout_rec<TERMS, NCOL, 0, 0>(addr0, tn, hi, lo, empty_bar);
-    constexpr unsigned long long bh = magic_bias(0, TERMS, true), bl = magic_bias(0, TERMS, false);
+    constexpr int D = level_offset(TERMS);
+    constexpr unsigned long long bh = magic_bias(0, TERMS, true, D), bl = magic_bias(0, TERMS, false, D);
 #pragma unroll
     for (int j = 0; j < NCOL; ++j) {
         hi[j] -= bh;
@@ -486,7 +504,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gemm_kernel(SgDev p) {
                 uint32_t r[32];
                 tmem_ld32(lane_base + (uint32_t)(g * TN), r);
                 tmem_ld_wait();
-                fold_level(g, r, hi, lo);
+                fold_level(g, level_offset(p.terms), r, hi, lo);
             }
 #pragma unroll
             for (int j = 0; j < TN; ++j) {          // keep |lo| < 2^40
@@ -520,7 +538,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) sliced_gemm_kernel(SgDev p) {
             for (int j = 0; j < TN; ++j) {
                 const int gj = j0 + j;
                 if (gj >= p.N || (p.lower_only && gj > i)) continue;
-                const double v = words_to_double(hi[j], lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86);
+                const double v =
+                    words_to_double(hi[j], lo[j], ea + (p.eb ? p.eb[gj] : 0) - 86 + 8 * level_offset(p.terms));
                 p.C[row * p.c_rs + (int64_t)gj * p.c_cs] =
                     epilogue_value(v, p.amode, p.alpha, p.bmode, p.beta, p.Cin + (int64_t)i * p.cin_rs + (int64_t)gj * p.cin_cs);
             }
@@ -539,6 +558,7 @@ struct SgReduceDev {
     int amode, bmode;
     const double* Cin; int64_t cin_rs, cin_cs;
     int lower_only;
+    int eoff;            // -86 + 8 level_offset(terms) = -78
 };
 
 __global__ void sliced_reduce_kernel(SgReduceDev r) {
@@ -552,10 +572,9 @@ __global__ void sliced_reduce_kernel(SgReduceDev r) {
         const longlong2 q = *reinterpret_cast<const longlong2*>(r.part + ((int64_t)z * total + idx) * 2);
         acc += ((__int128)q.x << 40) + (__int128)q.y;
     }
-    const long long h = (long long)(acc >> 40);
-    const long long l = (long long)(acc - ((__int128)h << 40));   // in [0, 2^40)
-    const int e = (r.ea ? r.ea[i] : 0) + (r.eb ? r.eb[j] : 0) - 86;
-    const double v = words_to_double(h, l, e);
+    // all 128 bits: the sum of the splits may exceed what one split's hi word can hold
+    const int e = (r.ea ? r.ea[i] : 0) + (r.eb ? r.eb[j] : 0) + r.eoff;
+    const double v = u128_to_double((unsigned long long)(acc >> 64), (unsigned long long)acc, e);
     const int64_t row = r.crow ? (int64_t)r.crow[i] : (int64_t)i;
     r.C[row * r.c_rs + (int64_t)j * r.c_cs] =
         epilogue_value(v, r.amode, r.alpha, r.bmode, r.beta, r.Cin + (int64_t)i * r.cin_rs + (int64_t)j * r.cin_cs);
@@ -587,6 +606,7 @@ constexpr int A_SLOT_BYTES = A_PPS * A_PLANE_BYTES;
 
 struct Sg2Dev {
     int M, N, Kp, sa, sb, terms, k_per_split, chunk_kb, splits;
+    int eoff;                     // -86 + 8 level_offset(terms) = -78: exponent of the output words
     const int32_t* ea; const int32_t* eb;
     long long* part;
     double* C; int64_t c_rs, c_cs; const int32_t* crow;
@@ -855,7 +875,7 @@ __device__ __forceinline__ void epilogue_role(const Sg2Dev& p, uint32_t tmem, ui
         } else {
             // column exponents: one load per lane, shared through the warp
             const int ebl = (p.eb && lane < NCOL && jb + lane < p.N) ? p.eb[jb + lane] : 0;
-            const int ea = (p.ea && valid ? p.ea[i] : 0) - 86;
+            const int ea = (p.ea && valid ? p.ea[i] : 0) + p.eoff;
             const int64_t row = p.crow && valid ? (int64_t)p.crow[i] : (int64_t)i;
             double* crow_p = p.C + row * p.c_rs;
             const double* cin_p = p.Cin + (int64_t)i * p.cin_rs;
@@ -1160,6 +1180,7 @@ void launch_reduce(const SlicedGemm& g, int splits, void* scratch, cudaStream_t 
     r.alpha = g.alpha; r.beta = g.beta; r.amode = alpha_mode(g.alpha); r.bmode = beta_mode(g.beta);
     r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
     r.lower_only = g.lower_only ? 1 : 0;
+    r.eoff = -86 + 8 * level_offset(g.terms);
     const int64_t total = (int64_t)r.M * r.N;
     sliced_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
     note_launch();
@@ -1197,6 +1218,9 @@ static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t s
     const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
     const int sms = sm_count();
     if (tiles < 2 * sms) splits = std::min(max_splits, (2 * sms + tiles - 1) / tiles);
+    // every split within the fixed point's capacity (see the top), where the scratch allows
+    const long long kcap = kSplitKCap;
+    splits = std::max<long long>(splits, std::min<long long>(max_splits, (Kp + kcap - 1) / kcap));
     while (splits > 1 && (size_t)splits * M * N * 16 > scratch_bytes) --splits;
     int kps = (Kp + splits - 1) / splits;
     kps = (kps + kchunk - 1) / kchunk * kchunk;
@@ -1229,6 +1253,7 @@ static cudaError_t sliced_gemm_sync(const SlicedGemm& g, void* scratch, size_t s
         r.alpha = g.alpha; r.beta = g.beta; r.amode = alpha_mode(g.alpha); r.bmode = beta_mode(g.beta);
     r.Cin = g.Cin; r.cin_rs = g.cin_rs; r.cin_cs = g.cin_cs;
         r.lower_only = g.lower_only ? 1 : 0;
+        r.eoff = -86 + 8 * level_offset(g.terms);
         const int64_t total = (int64_t)M * N;
         sliced_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(r);
         note_launch();
@@ -1253,23 +1278,34 @@ static int chunk_for(const SlicedGemm& g) {
 // fill and output) and per split (the partial sums written and reduced), both counted in
 // K blocks of 64; the lowest cost wins, fewer splits on ties. A split count just past a
 // multiple of the SM count would add a nearly empty round.
-static int choose_splits(int tiles, int M, int N, int Kp, size_t scratch_bytes, int kchunk, int* kps_out) {
+// Splits whose K exceeds the fixed point's capacity (2^25, see the top) are taken only
+// when the scratch cannot hold enough partials for any split count within it.
+static int choose_splits(int tiles, int M, int N, int Kp, size_t scratch_bytes, int kchunk, int terms,
+                         int* kps_out) {
     const int kSMs = sm_count();
     const int max_splits = std::max(1, (Kp + kchunk - 1) / kchunk);
     const double per_split = (double)M * N * 32.0 / (7.0e12 / 1.0e6);   // partials: microseconds
+    const long long kcap = kSplitKCap;
+    const int min_sp = (int)std::min<long long>(max_splits, (Kp + kcap - 1) / kcap);
+    const int top = std::max(std::min(max_splits, 64), min_sp);
     int best = 1, best_kps = (Kp + kchunk - 1) / kchunk * kchunk;
     double best_cost = 1e300;
-    for (int sp = 1; sp <= std::min(max_splits, 64); ++sp) {
+    bool best_capped = false;
+    for (int sp = 1; sp <= top; ++sp) {
         if (sp > 1 && (size_t)sp * M * N * 16 > scratch_bytes) break;
         int kps = (Kp + sp - 1) / sp;
         kps = (kps + kchunk - 1) / kchunk * kchunk;
         const int eff = (Kp + kps - 1) / kps;
         if (eff != sp) continue;
+        const bool capped = kps <= kcap;
+        if (best_capped && !capped) continue;
         const long long units = (long long)tiles * eff;
         const long long rounds = (units + kSMs - 1) / kSMs;
         // one K block of 64 is about one microsecond on one SM for these products
         const double cost = (double)rounds * ((double)kps / KB + 3.0) + (sp > 1 ? per_split * sp : 0.0);
-        if (cost < best_cost - 1e-9) { best_cost = cost; best = eff; best_kps = kps; }
+        if ((capped && !best_capped) || cost < best_cost - 1e-9) {
+            best_cost = cost; best = eff; best_kps = kps; best_capped = capped;
+        }
     }
     *kps_out = best_kps;
     return best;
@@ -1311,9 +1347,10 @@ cudaError_t sliced_gemm_impl(const SlicedGemm& g0, void* scratch, size_t scratch
     int kps = 0;
     const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + tn - 1) / tn;
     const TileSched ts{tiles_m, tiles_n, tn, g.lower_only ? 1 : 0, tiles_m <= tiles_n ? 1 : 0};
-    const int splits = choose_splits(ts.per_split(), M, N, Kp, scratch_bytes, kchunk, &kps);
+    const int splits = choose_splits(ts.per_split(), M, N, Kp, scratch_bytes, kchunk, g.terms, &kps);
     Sg2Dev p;
     p.M = M; p.N = N; p.Kp = Kp; p.sa = g.a.s; p.sb = g.b.s; p.terms = g.terms; p.k_per_split = kps;
+    p.eoff = -86 + 8 * level_offset(g.terms);
     p.chunk_kb = kchunk / KB;
     p.ea = g.a.e; p.eb = g.b.e;
     p.part = (long long*)scratch;

@@ -146,6 +146,26 @@ def test_paper_family_closed_form():
     assert metrics.max_rel_err(Z, Zc) < Z_TOL
 
 
+def test_long_reduction_over_flat_rows():
+    """The paper family at 40 x 10^6: W = P^{-1} A repeats each of its m distinct columns
+    n/m times, so the diagonal of X = W W^* is a coherent sum of 10^6 squares near the row
+    maximum -- the largest value the sliced product's fixed point has to hold (about
+    2^{20+86-8D} for K = 10^6). The preconditioner must still factor and Z match the closed
+    form."""
+    torch = torch_cuda()
+    rt = rt_module()
+    m, n, l = 40, 10 ** 6, 44
+    A, Bb, pu, pv = workloads.paper_test_matrix(m, n, 1e8, 5, return_parts=True)
+    B = workloads.rhs(2, n, 6)
+    Zc, _, _ = closed_form.project(Bb, pu, pv, B)
+    with _mixed(rt, torch, A, l, 2, refine_passes=4, refine_tol=1e-12) as P:
+        P.precondition(seed=7, l=l)
+        Z = P.null_project(to_dev(torch, B)).cpu().numpy()
+        inf = P.info()
+    assert inf["status"] == 0 and inf["kappa_pre"] < 100, inf
+    assert metrics.max_rel_err(Z, Zc) < Z_TOL
+
+
 def test_alias_and_entry_points_agree():
     torch = torch_cuda()
     rt = rt_module()
