@@ -324,7 +324,9 @@ def phase_work(mode, w, o):
                     "sliced_gemm2_kernel"),
         "apply_at": (2.0 * m * n * k * (digit_pairs(rs, rs, rs) + passes * digit_pairs(ap, ap, ap)), "tensor",
                      "sliced_gemm2_kernel"),
-        "qr": (qr, "alu", "qr_persistent_kernel"),
+        # float-float on the FP32 pipe; counted as the float64 work it replaces, against the
+        # FP64 pipe (the kernel is bound by the latency of its m sequential grid exchanges)
+        "qr": (qr, "alu", "qr_persistent_ff_kernel" if getattr(o, "qr_form", 0) == 0 else "qr_persistent_kernel"),
     }
 
 
@@ -922,8 +924,14 @@ def study_sparse(args):
     t6 = {key(r): r for r in tim["table6"]}
     dev = torch.device("cuda", 0)
     rows = []
+    only = None
+    if args.sparse_row:
+        mm, nn, ll, kk = args.sparse_row.split(",")
+        only = (int(mm), int(nn), int(ll), float(kk))
     for low_rank, tt, te in ((False, t1, t2), (True, t5, t6)):
         for k in tt:
+            if only is not None and k != only:
+                continue
             m, n, l, kappa = k
             try:
                 r = _sparse_row(torch, rt, dev, m, n, l, kappa, low_rank)
@@ -954,6 +962,8 @@ def main():
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
     ap.add_argument("--pipeline", type=int, default=4,
                     help="handles (and streams) the timed steps rotate over; > 1 overlaps consecutive steps")
+    ap.add_argument("--sparse-row", default=None,
+                    help="with --study sparse: only the rows m,n,l,kappa of Tables 1 and 5 (e.g. 1000,300000,1004,1e8)")
     ap.add_argument("--study", choices=["accuracy", "variates", "batch", "sparse"], default=None,
                     help="run a study (Section 5 accuracy; variates and sketch sizes) instead of the bench")
     args = ap.parse_args()

@@ -124,11 +124,15 @@ typedef struct {
     int scalable;        /* 1: reserve what rtproj_set_scaling needs (the float64 form keeps
                             A diag(d) in the workspace; the mixed form forms it in the Gram
                             matrix's buffer and needs nothing more). Default 0.             */
-    int qr_form;         /* mixed form's pivoted QR: 0 (default) the float64 persistent kernel
-                            (one grid exchange per step); 1 the float-float kernel on one
-                            16-CTA cluster (exchange through distributed shared memory) when
-                            S^* fits its shared memory, else 0. Both give a valid pivoted QR;
-                            on GB300 form 0 measured faster (2.6 against 3.4 ms at 512 x 516). */
+    int qr_form;         /* mixed form's pivoted QR: 0 (default) float-float on the whole
+                            grid (one grid exchange per step, the column updates on the FP32
+                            pipe); 1 float-float on one 16-CTA cluster (exchange through
+                            distributed shared memory) when S^* fits its shared memory, else
+                            2; 2 the float64 kernel of the float64 form. Forms 0 and 1 fall
+                            back to 2 by themselves when the entries' range would take
+                            float-float near float's underflow. All give a valid pivoted
+                            QR; the preconditioner tolerates float-float's 2^-48 and the
+                            refinement makes the projection exact.                      */
     int async;           /* 1: rtproj_create and rtproj_precondition do not synchronize; the
                             conditions they would return (non-finite A, ERANK, ENOTSPD,
                             ETIMEOUT) stay latched in the device status word, which

@@ -272,4 +272,163 @@ cudaError_t check_finite(const double* X, int64_t rs, int rows, int cols, int* s
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------------
+// Narrow products C (M x N) = A (M x K) B (K x N) with M <= 64 (the rows of a low-rank
+// factor) and a long K: the 64 x 64 tiles of gemm64 would waste most of their rows. The K
+// range is cut into chunks; a CTA takes one chunk and a range of columns j and keeps NR
+// rows' partial sums per column in registers, reading A's chunk from shared memory. B is
+// read with the columns j contiguous (one thread per column), or with K contiguous (a warp
+// per column, lanes over k), or generated (G of Eq. 12). The chunks' partial sums are
+// added in chunk order by a second kernel (deterministic).
+// ---------------------------------------------------------------------------------
+namespace {
+
+constexpr int NR_ROWS = 16;     // rows per register pass
+constexpr int NR_KC = 64;       // K entries of A staged per pass
+constexpr int NR_T = 256;
+
+struct NarrowDev {
+    int M, N, K, kchunk;
+    const double* A; int64_t a_rs;
+    const double* B; int64_t b_rs, b_cs;
+    int omega_dist; uint32_t key0, key1;
+    double* part;               // [chunk][M][N]
+};
+
+__device__ __forceinline__ double narrow_warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// B(k, j) for k = k0 .. k0 + 3 (k0 a multiple of 4), zero at k >= ke, into b[0..3]
+__device__ __forceinline__ void narrow_b4(const NarrowDev& p, int k0, int ke, int j, double (&b)[4]) {
+    if (p.omega_dist == RTPROJ_OMEGA_GAUSSIAN) {
+        int N4[4];
+        gauss_quad((uint32_t)(k0 >> 2), (uint32_t)j, p.key0, p.key1, N4);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = k0 + u < ke ? (double)N4[u] * (1.0 / 4096.0) : 0.0;
+    } else if (p.omega_dist >= 0) {
+        const uint4 w = philox4x32_10(make_uint4((uint32_t)(k0 >> 4), (uint32_t)j, 0u, 0u), p.key0, p.key1);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            b[u] = k0 + u < ke ? (double)omega_from_byte(block_byte(w, (k0 & 15) + u), p.omega_dist) : 0.0;
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = k0 + u < ke ? p.B[(int64_t)(k0 + u) * p.b_rs + (int64_t)j * p.b_cs] : 0.0;
+    }
+}
+
+// one thread per column j; rows [r0, r0 + NR_ROWS) of A; chunk blockIdx.y
+__global__ void __launch_bounds__(NR_T) narrow_rows_kernel(NarrowDev p) {
+    __shared__ double As[NR_ROWS][NR_KC];
+    const int j = blockIdx.x * NR_T + threadIdx.x;
+    const int kb = blockIdx.y * p.kchunk, ke = min(p.K, kb + p.kchunk);
+    for (int r0 = 0; r0 < p.M; r0 += NR_ROWS) {
+        double acc[NR_ROWS];
+#pragma unroll
+        for (int i = 0; i < NR_ROWS; ++i) acc[i] = 0.0;
+        for (int k0 = kb; k0 < ke; k0 += NR_KC) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < NR_ROWS * NR_KC; e += NR_T) {
+                const int i = e / NR_KC, k = k0 + e % NR_KC;
+                As[i][e % NR_KC] = (r0 + i < p.M && k < ke) ? p.A[(int64_t)(r0 + i) * p.a_rs + k] : 0.0;
+            }
+            __syncthreads();
+            if (j < p.N) {
+                const int kn = min(NR_KC, ke - k0);
+                for (int kk = 0; kk < kn; kk += 4) {
+                    double b[4];
+                    narrow_b4(p, k0 + kk, ke, j, b);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int i = 0; i < NR_ROWS; ++i) acc[i] = fma(As[i][kk + u], b[u], acc[i]);
+                }
+            }
+        }
+        if (j < p.N) {
+#pragma unroll
+            for (int i = 0; i < NR_ROWS; ++i)
+                if (r0 + i < p.M) p.part[((int64_t)blockIdx.y * p.M + r0 + i) * p.N + j] = acc[i];
+        }
+    }
+}
+
+// one warp per column j, lanes over k (B with K contiguous: b_rs == 1)
+__global__ void __launch_bounds__(NR_T) narrow_cols_kernel(NarrowDev p) {
+    __shared__ double As[NR_ROWS][NR_KC];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (NR_T / 32) + warp;
+    const int kb = blockIdx.y * p.kchunk, ke = min(p.K, kb + p.kchunk);
+    for (int r0 = 0; r0 < p.M; r0 += NR_ROWS) {
+        double acc[NR_ROWS];
+#pragma unroll
+        for (int i = 0; i < NR_ROWS; ++i) acc[i] = 0.0;
+        for (int k0 = kb; k0 < ke; k0 += NR_KC) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < NR_ROWS * NR_KC; e += NR_T) {
+                const int i = e / NR_KC, k = k0 + e % NR_KC;
+                As[i][e % NR_KC] = (r0 + i < p.M && k < ke) ? p.A[(int64_t)(r0 + i) * p.a_rs + k] : 0.0;
+            }
+            __syncthreads();
+            if (j < p.N)
+                for (int kk = lane; kk < NR_KC && k0 + kk < ke; kk += 32) {
+                    const double b = p.B[(int64_t)(k0 + kk) + (int64_t)j * p.b_cs];
+#pragma unroll
+                    for (int i = 0; i < NR_ROWS; ++i) acc[i] = fma(As[i][kk], b, acc[i]);
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < NR_ROWS; ++i) acc[i] = narrow_warp_sum(acc[i]);
+        if (j < p.N && lane == 0) {
+#pragma unroll
+            for (int i = 0; i < NR_ROWS; ++i)
+                if (r0 + i < p.M) p.part[((int64_t)blockIdx.y * p.M + r0 + i) * p.N + j] = acc[i];
+        }
+    }
+}
+
+__global__ void narrow_reduce_kernel(const double* part, int chunks, int M, int N, double* C, int64_t c_rs) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)M * N) return;
+    const int i = (int)(idx / N), j = (int)(idx % N);
+    double s = 0.0;
+    for (int z = 0; z < chunks; ++z) s += part[((int64_t)z * M + i) * N + j];
+    C[(int64_t)i * c_rs + j] = s;
+}
+
+}  // namespace
+
+cudaError_t gemm64_narrow(const Narrow64& g, double* part, size_t part_elems, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    if (g.M > 64 || g.K <= 0) return cudaErrorInvalidValue;
+    const bool cols = g.omega_dist < 0 && g.b_rs == 1;
+    const int per_block = cols ? NR_T / 32 : NR_T;
+    const int gx = (g.N + per_block - 1) / per_block;
+    // chunks: about four CTAs per SM in all, each chunk a multiple of 16 (whole Philox blocks)
+    const int want = std::max(1, 4 * sm_count() / gx);
+    const size_t cap = std::max<size_t>(1, part_elems / ((size_t)g.M * g.N));
+    int chunks = (int)std::min<size_t>((size_t)std::min(want, 65535), cap);
+    int kchunk = (g.K + chunks - 1) / chunks;
+    kchunk = (kchunk + 15) / 16 * 16;
+    chunks = (g.K + kchunk - 1) / kchunk;
+    if ((size_t)chunks * g.M * g.N > part_elems) return cudaErrorInvalidValue;
+    NarrowDev p;
+    p.M = g.M; p.N = g.N; p.K = g.K; p.kchunk = kchunk;
+    p.A = g.A; p.a_rs = g.a_rs;
+    p.B = g.B; p.b_rs = g.b_rs; p.b_cs = g.b_cs;
+    p.omega_dist = g.omega_dist;
+    p.key0 = (uint32_t)(g.seed & 0xFFFFFFFFull); p.key1 = (uint32_t)(g.seed >> 32);
+    p.part = part;
+    const dim3 grid((unsigned)gx, (unsigned)chunks);
+    if (cols) narrow_cols_kernel<<<grid, NR_T, 0, s>>>(p);
+    else narrow_rows_kernel<<<grid, NR_T, 0, s>>>(p);
+    const int64_t total = (int64_t)g.M * g.N;
+    narrow_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(part, chunks, g.M, g.N, g.C, g.c_rs);
+    note_launch(2);
+    return cudaGetLastError();
+}
+
 }  // namespace rtp

@@ -11,6 +11,11 @@
 //   kernel 2 (one warp per remaining column): apply I - beta v v^* and downdate.
 // On exit R[i][c] = S[c][i] (i <= c) and S[:, perm] factors as in Eq. 13.
 #include "rtproj_internal.cuh"
+#include "ff.cuh"
+
+#include <climits>
+#include <cstdlib>
+#include <algorithm>
 
 namespace rtp {
 namespace {
@@ -195,6 +200,8 @@ struct PqrDev {
     int* status;
     long long timeout;
     const int* run_if;       // when set, the kernel runs only if *run_if != 0
+    int* fallback;           // float-float form: set to 1 when the float64 kernel must run instead
+    int* emax;               // float-float form: G exponents of the CTAs' largest entries
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
@@ -433,6 +440,225 @@ __global__ void __launch_bounds__(PqrShape<GLOBAL_COLS>::NT, 1) qr_persistent_ke
     }
 }
 
+
+// ---------------------------------------------------------------------------------
+// Float-float form of the persistent kernel (the mixed form's QR). The same exchange,
+// pivot rule (squared norms summed afresh every step, largest first, lowest index on ties)
+// and column layout, with every column held as float-float pairs on the FP32 pipe (GB300's
+// FP64 pipe takes 64 cycles per warp instruction, which bounds the float64 kernel's column
+// updates). Before step 0 the CTAs exchange the exponents of their largest entries once,
+// and S^* is scaled by 2^-E (exact) so that its largest entry lies below 1; R is scaled
+// back on output. A pivot whose squared norm falls below 2^-100 (float-float would lose
+// the digits of a trailing norm near float's underflow) makes every CTA return before
+// writing R or perm and sets *fallback, so that the float64 kernel, enqueued after this
+// one, runs instead; S itself is not modified (the global form keeps its float-float
+// columns in the work area). Accuracy: R is the exact factor of S^* + E with ||E|| of
+// order l 2^-48 ||S||, which the preconditioner tolerates while 2^-48 kappa(A) << 1; the
+// refinement makes the projection exact whatever the preconditioner's rounding.
+template <bool GLOBAL_COLS>
+__device__ __forceinline__ void publish_best_ff(const PqrDev& p, int b, int G, int s, int nc, const int* posq,
+                                                const ff* nsq) {
+    int bq = -1;
+    for (int q = 0; q < nc; ++q)
+        if (posq[q] < 0 && (bq < 0 || ff_gt(nsq[q], nsq[bq]))) bq = q;
+    const int par = s & 1;
+    p.bval[par * G + b] = bq >= 0 ? ff_to_double(nsq[bq]) : 0.0;
+    p.bidx[par * G + b] = bq >= 0 ? b * p.cpc + bq : p.m;
+    red_release_add(p.counter, 1u);
+}
+
+template <bool GLOBAL_COLS, int NT>
+__global__ void __launch_bounds__(NT, 1) qr_persistent_ff_kernel(PqrDev p) {
+    constexpr int NW = NT / 32;
+    extern __shared__ float2 smem_f[];
+    const int l = p.l, m = p.m, cpc = p.cpc;
+    const int b = blockIdx.x, G = gridDim.x, t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float2* slots = reinterpret_cast<float2*>(p.slots);
+    const size_t slot_par = (size_t)G * cpc * l;                     // float2 per parity buffer
+    float2* cols = GLOBAL_COLS ? slots + (size_t)b * cpc * l : smem_f;     // cpc x l
+    float2* v = GLOBAL_COLS ? smem_f : cols + (size_t)cpc * l;             // l
+    __shared__ ff nsq[PQ_MAXC];
+    __shared__ ff alphaq[PQ_MAXC];
+    __shared__ int posq[PQ_MAXC];
+    __shared__ unsigned long long redb[2 * NW];
+    __shared__ int redi[2 * NW];
+    __shared__ double red_d[NW];
+    __shared__ int ok_s, e_s;
+    const int c0 = b * cpc;
+    const int nc = max(0, min(cpc, m - c0));
+
+    // 0. the scale: exponents of the CTAs' largest entries, exchanged once
+    double mx = 0.0;
+    for (int q = 0; q < nc; ++q)
+        for (int i = t; i < l; i += NT) mx = fmax(mx, fabs(p.S[(int64_t)(c0 + q) * p.lds + i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red_d[warp] = mx;
+    __syncthreads();
+    if (t == 0) {
+        double bm = 0.0;
+        for (int w = 0; w < NW; ++w) bm = fmax(bm, red_d[w]);
+        int e = INT_MIN / 2;
+        if (bm > 0.0) frexp(bm, &e);                       // bm < 2^e
+        p.emax[b] = e;
+        red_release_add(p.counter, 1u);
+        ok_s = wait_geq(p.counter, (unsigned int)G, p.abort_flag, p.status, p.timeout);
+        int E = INT_MIN / 2;
+        if (ok_s)
+            for (int g = 0; g < G; ++g) E = max(E, __ldcg(p.emax + g));
+        e_s = E == INT_MIN / 2 ? 0 : E;
+    }
+    __syncthreads();
+    if (!ok_s) return;
+    const int E = e_s;
+    const double sc = ldexp(1.0, -E);
+    for (int q = 0; q < nc; ++q)
+        for (int i = t; i < l; i += NT) {
+            const ff x = ff_from_double(p.S[(int64_t)(c0 + q) * p.lds + i] * sc);
+            cols[(size_t)q * l + i] = make_float2(x.hi, x.lo);
+            if (!GLOBAL_COLS) slots[((size_t)b * cpc + q) * l + i] = make_float2(x.hi, x.lo);
+        }
+    __syncthreads();
+    for (int q = warp; q < nc; q += NW) {
+        const float2* c = cols + (size_t)q * l;
+        ff a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+        int i = lane;
+        for (; i + 32 < l; i += 64) {
+            const ff x = {c[i].x, c[i].y}, y = {c[i + 32].x, c[i + 32].y};
+            ff_dot_acc(a0, x, x);
+            ff_dot_acc(a1, y, y);
+        }
+        if (i < l) { const ff x = {c[i].x, c[i].y}; ff_dot_acc(a0, x, x); }
+        const ff s2 = ff_warp_sum(ff_add(ff_renorm(a0), ff_renorm(a1)));
+        if (lane == 0) { nsq[q] = s2; posq[q] = -1; }
+    }
+    __syncthreads();
+    if (t == 0) publish_best_ff<GLOBAL_COLS>(p, b, G, 0, nc, posq, nsq);
+
+    for (int j = 0; j < m; ++j) {
+        const int par = j & 1;
+        // 1. wait for every candidate of step j (after the scale exchange: G more arrivals)
+        if (t == 0) ok_s = wait_geq(p.counter, (unsigned int)(j + 2) * (unsigned int)G, p.abort_flag, p.status,
+                                     p.timeout);
+        __syncthreads();
+        if (!ok_s) return;
+        unsigned long long best = 0;
+        int bi = m;
+        for (int g = t; g < G; g += NT) {
+            const unsigned long long x = sq_bits(__ldcg(p.bval + par * G + g));
+            const int i = __ldcg(p.bidx + par * G + g);
+            if (i < m && (bi == m || x > best || (x == best && i < bi))) { best = x; bi = i; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { redb[par * NW + warp] = best; redi[par * NW + warp] = bi; }
+        __syncthreads();
+        unsigned long long bb = redb[par * NW];
+        int ii = redi[par * NW];
+        for (int w = 1; w < NW; ++w) {
+            const unsigned long long xb = redb[par * NW + w];
+            const int xi = redi[par * NW + w];
+            if (xi < m && (ii == m || xb > bb || (xb == bb && xi < ii))) { bb = xb; ii = xi; }
+        }
+        if (ii >= m) return;                                   // cannot happen while columns remain
+        const int piv = ii;
+        const ff npiv = ff_from_double(__longlong_as_double((long long)bb));
+        if (npiv.hi < 7.888609052210118e-31f) {                // 2^-100: the float64 kernel takes over
+            if (b == 0 && t == 0) *p.fallback = 1;
+            return;
+        }
+        // 2. the reflector from the pivot column (rows j .. l-1)
+        const float2* slot = GLOBAL_COLS ? slots + (size_t)piv * l : slots + (size_t)par * slot_par + (size_t)piv * l;
+        const float2 x0f = __ldcg(slot + j);
+        const ff x0 = {x0f.x, x0f.y};
+        const ff nx = ff_sqrt(npiv);
+        const ff ax = x0.hi >= 0.f ? x0 : ff_neg(x0);
+        const ff alpha = x0.hi >= 0.f ? ff_neg(nx) : nx;
+        const ff beta = ff_recip(ff_mul(nx, ff_add(nx, ax)));
+        for (int i = j + t; i < l; i += NT) {
+            if (i == j) {
+                const ff v0 = ff_add(x0, ff_neg(alpha));
+                v[0] = make_float2(v0.hi, v0.lo);
+            } else {
+                v[i - j] = __ldcg(slot + i);
+            }
+        }
+        if (t == 0 && piv >= c0 && piv < c0 + nc) {
+            const int q = piv - c0;
+            alphaq[q] = alpha;
+            posq[q] = j;
+            p.perm[j] = piv;
+        }
+        __syncthreads();
+        const int len = l - j;
+        // 3. each active column: w = beta v^* c, c <- c - w v, the squared norm of rows
+        //    j+1 .. l-1 and their copy to the staging slot of step j+1
+        float2* next = slots + (size_t)(par ^ 1) * slot_par;
+        for (int q = warp; q < nc; q += NW) {
+            if (posq[q] >= 0) continue;
+            float2* c = cols + (size_t)q * l + j;
+            ff a0 = {0.f, 0.f}, a1 = {0.f, 0.f}, a2 = {0.f, 0.f}, a3 = {0.f, 0.f};
+            int i = lane;
+            for (; i + 96 < len; i += 128) {
+                const float2 c0f = c[i], c1f = c[i + 32], c2f = c[i + 64], c3f = c[i + 96];
+                const float2 v0 = v[i], v1 = v[i + 32], v2 = v[i + 64], v3 = v[i + 96];
+                ff_dot_acc(a0, {v0.x, v0.y}, {c0f.x, c0f.y});
+                ff_dot_acc(a1, {v1.x, v1.y}, {c1f.x, c1f.y});
+                ff_dot_acc(a2, {v2.x, v2.y}, {c2f.x, c2f.y});
+                ff_dot_acc(a3, {v3.x, v3.y}, {c3f.x, c3f.y});
+            }
+            for (; i < len; i += 32) ff_dot_acc(a0, {v[i].x, v[i].y}, {c[i].x, c[i].y});
+            const ff dot = ff_warp_sum(ff_add(ff_add(ff_renorm(a0), ff_renorm(a1)), ff_add(ff_renorm(a2), ff_renorm(a3))));
+            const ff nw = ff_neg(ff_mul(dot, beta));
+            float2* dst = next + ((size_t)b * cpc + q) * l + j;
+            ff s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+            for (i = 1 + lane; i + 32 < len; i += 64) {
+                const float2 ca = c[i], cb = c[i + 32];
+                const float2 va = v[i], vb = v[i + 32];
+                const ff xa = ff_add({ca.x, ca.y}, ff_mul(nw, {va.x, va.y}));
+                const ff xb = ff_add({cb.x, cb.y}, ff_mul(nw, {vb.x, vb.y}));
+                c[i] = make_float2(xa.hi, xa.lo);
+                c[i + 32] = make_float2(xb.hi, xb.lo);
+                if (!GLOBAL_COLS) {
+                    dst[i] = make_float2(xa.hi, xa.lo);
+                    dst[i + 32] = make_float2(xb.hi, xb.lo);
+                }
+                ff_dot_acc(s0, xa, xa);
+                ff_dot_acc(s1, xb, xb);
+            }
+            for (; i < len; i += 32) {
+                const ff x = ff_add({c[i].x, c[i].y}, ff_mul(nw, {v[i].x, v[i].y}));
+                c[i] = make_float2(x.hi, x.lo);
+                if (!GLOBAL_COLS) dst[i] = make_float2(x.hi, x.lo);
+                ff_dot_acc(s0, x, x);
+            }
+            const ff ssq = ff_warp_sum(ff_add(ff_renorm(s0), ff_renorm(s1)));
+            if (lane == 0) {
+                const ff r0 = ff_add({c[0].x, c[0].y}, ff_mul(nw, {v[0].x, v[0].y}));
+                c[0] = make_float2(r0.hi, r0.lo);
+                nsq[q] = ssq;
+            }
+        }
+        __syncthreads();
+        // 4. the CTA's candidate for step j+1
+        if (t == 0) publish_best_ff<GLOBAL_COLS>(p, b, G, j + 1, nc, posq, nsq);
+    }
+    // R[:, pos] = first pos+1 entries of the retired column, scaled back by 2^E
+    for (int q = 0; q < nc; ++q) {
+        const int pos = posq[q];
+        if (pos < 0) continue;
+        const float2* c = cols + (size_t)q * l;
+        for (int i = t; i < m; i += NT) {
+            const double r = i < pos ? ff_to_double({c[i].x, c[i].y}) : i == pos ? ff_to_double(alphaq[q]) : 0.0;
+            p.R[(int64_t)i * m + pos] = ldexp(r, E);
+        }
+    }
+}
+
 }  // namespace
 
 cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, int32_t* perm,
@@ -464,7 +690,7 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
 size_t pivoted_qr_work_doubles(int m, int l) {
     const size_t steps = (size_t)3 * m + 3 * (size_t)l + 2048;                       // per-step form
     // staging slots (G * cpc < m + cpc columns per parity), candidates, counter and flag
-    const size_t persistent = (size_t)2 * ((size_t)m + PQ_MAXC) * l + 4 * (size_t)PQ_MAX_G + 64;
+    const size_t persistent = (size_t)2 * ((size_t)m + PQ_MAXC) * l + 5 * (size_t)PQ_MAX_G + 64;
     return steps > persistent ? steps : persistent;
 }
 
@@ -501,6 +727,79 @@ cudaError_t qr_check(const double* R, int32_t* perm, int m, double tol, int* sta
     qr_check_kernel<<<1, 1024, 0, s>>>(R, perm, m, tol, status);
     note_launch();
     return cudaGetLastError();
+}
+
+// Columns per CTA of the float-float kernel's shared-memory form (RTPROJ_QR_COLS overrides
+// it for measurements; the default came from a sweep at 512 x 516).
+int ff_cols_per_cta() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = std::getenv("RTPROJ_QR_COLS");
+        v = e ? std::max(1, std::min(PQ_MAXC, std::atoi(e))) : 4;
+    }
+    return v;
+}
+
+cudaError_t pivoted_qr_ff(double* S, int m, int l, int64_t lds, double* R, int32_t* perm, double* work, int* status,
+                          cudaStream_t s, long long spin_limit, int* fallback, bool* launched) {
+    *launched = false;
+    int dev = 0, sms = 0, coop = 0, smem_optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop || sms <= 0) return cudaSuccess;
+    // columns in shared memory: about ff_cols_per_cta() columns per CTA, one warp each, so
+    // that fewer CTAs take part in each step's exchange (and the rest of the GPU stays free
+    // for other work); one CTA per SM with 16 warps when the columns stay in global memory
+    const int cpc_min = (m + sms - 1) / sms;
+    const int cpc_s = std::min(PQ_MAXC, std::max(cpc_min, ff_cols_per_cta()));
+    const size_t smem_shared = ((size_t)cpc_s * l + l) * sizeof(float2);
+    const bool in_smem = smem_shared + 4096 <= (size_t)smem_optin;
+    const int cpc = in_smem ? cpc_s : cpc_min;
+    const int G = (m + cpc - 1) / cpc;
+    const size_t smem_global = (size_t)l * sizeof(float2);
+    const size_t smem = in_smem ? smem_shared : smem_global;
+    const int warps_s = std::min(32, std::max(4, cpc));
+    const void* kern = !in_smem        ? (const void*)qr_persistent_ff_kernel<true, 512>
+                       : warps_s <= 4  ? (const void*)qr_persistent_ff_kernel<false, 128>
+                       : warps_s <= 8  ? (const void*)qr_persistent_ff_kernel<false, 256>
+                       : warps_s <= 16 ? (const void*)qr_persistent_ff_kernel<false, 512>
+                                       : (const void*)qr_persistent_ff_kernel<false, 1024>;
+    const int nt = !in_smem ? 512 : warps_s <= 4 ? 128 : warps_s <= 8 ? 256 : warps_s <= 16 ? 512 : 1024;
+    if (cpc > PQ_MAXC || G > PQ_MAX_G || smem + 4096 > (size_t)smem_optin) return cudaSuccess;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem);
+    if (per_sm < 1 || G > per_sm * sms) return cudaSuccess;
+    PqrDev p;
+    p.S = S; p.m = m; p.l = l; p.lds = lds; p.R = R; p.perm = perm; p.cpc = cpc;
+    double* w = work;
+    // float-float columns: the staging slots (two parities) in shared-memory form, the
+    // columns themselves in the global form; both fit the float64 form's slot area
+    p.slots = w;                    w += in_smem ? (size_t)2 * G * cpc * l : (size_t)G * cpc * l;
+    p.bval = w;                     w += 2 * (size_t)G;
+    p.bidx = (int*)w;               w += G;          // 2G ints
+    p.emax = (int*)w;               w += G;          // G ints
+    unsigned int* ctr = (unsigned int*)w;            // counter, abort
+    p.counter = ctr;
+    p.abort_flag = (int*)(ctr + 1);
+    p.status = status;
+    p.timeout = spin_limit;
+    p.run_if = nullptr;
+    p.fallback = fallback;
+    cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fallback, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&p};
+    e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(nt), args, smem, s);
+    note_launch();
+    if (e == cudaSuccess) {
+        *launched = true;
+        return cudaSuccess;
+    }
+    cudaGetLastError();   // clear; the float64 kernel runs unconditionally
+    return cudaSuccess;
 }
 
 bool pivoted_qr_persistent_ok(int m, int l) {
@@ -551,6 +850,8 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 p.status = status;
                 p.timeout = spin_limit;
                 p.run_if = run_if;
+                p.fallback = nullptr;
+                p.emax = nullptr;
                 cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
                 if (e != cudaSuccess) return e;
                 void* args[] = {&p};

@@ -32,6 +32,7 @@
 // of a trailing norm near float's underflow), the kernel leaves R and perm untouched and
 // sets *fallback, and the float64 persistent kernel that follows it runs instead.
 #include "rtproj_internal.cuh"
+#include "ff.cuh"
 
 #include <cooperative_groups.h>
 
@@ -44,63 +45,6 @@ constexpr int CQ_CTAS = 16;
 constexpr int CQ_THREADS = 512;
 constexpr int CQ_WARPS = CQ_THREADS / 32;
 constexpr int CQ_MAXC = 64;
-
-struct ff {
-    float hi, lo;
-};
-
-__device__ __forceinline__ ff two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    return {s, (a - (s - bb)) + (b - bb)};
-}
-
-__device__ __forceinline__ ff quick_two_sum(float a, float b) {
-    const float s = a + b;
-    return {s, b - (s - a)};
-}
-
-__device__ __forceinline__ ff ff_add(ff x, ff y) {
-    ff s = two_sum(x.hi, y.hi);
-    return quick_two_sum(s.hi, s.lo + (x.lo + y.lo));
-}
-
-__device__ __forceinline__ ff ff_neg(ff x) { return {-x.hi, -x.lo}; }
-
-__device__ __forceinline__ ff ff_mul(ff x, ff y) {
-    const float p = x.hi * y.hi;
-    float e = fmaf(x.hi, y.hi, -p);
-    e = fmaf(x.hi, y.lo, e);
-    e = fmaf(x.lo, y.hi, e);
-    return quick_two_sum(p, e);
-}
-
-__device__ __forceinline__ ff ff_sqrt(ff x) {
-    if (!(x.hi > 0.f)) return {0.f, 0.f};
-    const float s = sqrtf(x.hi);
-    const float e = (fmaf(-s, s, x.hi) + x.lo) / (2.f * s);
-    return quick_two_sum(s, e);
-}
-
-__device__ __forceinline__ ff ff_recip(ff d) {
-    const float q = 1.f / d.hi;
-    const float r = fmaf(-d.hi, q, 1.f) - d.lo * q;     // 1 - d q, to float-float accuracy
-    return quick_two_sum(q, r * q);
-}
-
-// x > y for normalised float-float values (|lo| <= ulp(hi) / 2)
-__device__ __forceinline__ bool ff_gt(ff x, ff y) { return x.hi > y.hi || (x.hi == y.hi && x.lo > y.lo); }
-
-__device__ __forceinline__ ff ff_warp_sum(ff v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        ff w;
-        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
-        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
-        v = ff_add(v, w);
-    }
-    return v;
-}
 
 // Warp-wide maximum of (value, index): largest value, lowest index on ties; an index of m
 // marks an empty entry. Every lane receives the result.

@@ -413,12 +413,12 @@ cudaError_t ut_times(const rtproj_ctx* h, const double* Y, int64_t ldy, int cols
 }
 
 cudaError_t v_times_t(const rtproj_ctx* h, const double* Y, int64_t ldy, int cols, double* C, int64_t ldc) {
-    Gemm64 g;
+    Narrow64 g;
     g.M = h->lr; g.N = cols; g.K = (int)h->n;
-    g.A = h->lrV; g.a_rs = h->n; g.a_cs = 1;
+    g.A = h->lrV; g.a_rs = h->n;
     g.B = Y; g.b_rs = 1; g.b_cs = ldy;
-    g.C = C; g.c_rs = ldc; g.c_cs = 1;
-    return gemm64(g, h->part, h->part_elems, h->stream);
+    g.C = C; g.c_rs = ldc;
+    return gemm64_narrow(g, h->part, h->part_elems, h->stream);
 }
 
 }  // namespace
@@ -545,13 +545,13 @@ rtproj_status sparse_prepare(rtproj_ctx* h) {
 
 rtproj_status sparse_sketch(rtproj_ctx* h, uint64_t seed, int64_t l, double* S, int64_t lds) {
     const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFull), k1 = (uint32_t)(seed >> 32);
-    if (h->lr > 0) {   // V G (r x l): the float64 GEMM with G generated in its tile loader
-        Gemm64 g;
+    if (h->lr > 0) {   // V G (r x l), G generated where it is used
+        Narrow64 g;
         g.M = h->lr; g.N = (int)l; g.K = (int)h->n;
-        g.A = h->lrV; g.a_rs = h->n; g.a_cs = 1;
+        g.A = h->lrV; g.a_rs = h->n;
         g.omega_dist = h->opts.omega; g.seed = seed;
-        g.C = h->lr_a; g.c_rs = l; g.c_cs = 1;
-        SP_CHECK(gemm64(g, h->part, h->part_elems, h->stream));
+        g.C = h->lr_a; g.c_rs = l;
+        SP_CHECK(gemm64_narrow(g, h->part, h->part_elems, h->stream));
     }
     const dim3 grid((unsigned)((l + 31) / 32), (unsigned)h->m);
     sparse_sketch_kernel<<<grid, 32 * SK_WARPS, 0, h->stream>>>(h->csr_ptr, h->csr_col, h->csr_val, (int)l,
@@ -575,12 +575,12 @@ rtproj_status sparse_gram(rtproj_ctx* h) {
         h->csc_ptr, h->csc_row, h->csc_val, h->Pminus, m, n, r, h->lrV, h->lr_a, D);
     note_launch();
     if (r > 0) {                                                                        // V D
-        Gemm64 g;
+        Narrow64 g;
         g.M = r; g.N = m; g.K = n;
-        g.A = h->lrV; g.a_rs = n; g.a_cs = 1;
+        g.A = h->lrV; g.a_rs = n;
         g.B = D; g.b_rs = m; g.b_cs = 1;
-        g.C = h->lr_a; g.c_rs = m; g.c_cs = 1;
-        SP_CHECK(gemm64(g, h->part, h->part_elems, s));
+        g.C = h->lr_a; g.c_rs = m;
+        SP_CHECK(gemm64_narrow(g, h->part, h->part_elems, s));
     }
     sparse_e_kernel<<<m, row_threads(m), 0, s>>>(h->csr_ptr, h->csr_col, h->csr_val, D, m, r, h->lrU, h->lr_a,
                                                  h->Esp);

@@ -98,7 +98,7 @@ bool valid_opts(const rtproj_opts& o) {
     if (o.refine_passes < 0 || o.refine_passes > 8) return false;
     if (o.async != 0 && o.async != 1) return false;
     if (o.scalable != 0 && o.scalable != 1) return false;
-    if (o.qr_form != 0 && o.qr_form != 1) return false;
+    if (o.qr_form < 0 || o.qr_form > 2) return false;
     if (o.dtype != RTPROJ_F64 && o.dtype != RTPROJ_F32) return false;
     if (o.spin_limit_cycles < 1) return false;
     if (!(o.refine_tol >= 0.0)) return false;
@@ -530,15 +530,21 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_end(h, RTPROJ_PHASE_SKETCH);
     // 2. S^* = Q R Pi (Eq. 13)
     phase_begin(h, RTPROJ_PHASE_QR);
-    // opts.qr_form = 1 (mixed form): the float-float cluster QR when S^* fits one cluster's
-    // shared memory (the float64 persistent kernel follows and runs only if the cluster
-    // kernel's range check sent the factorization back to it); otherwise the float64 QR
-    bool cluster = false;
+    // mixed form: a float-float QR first -- on the whole grid (opts.qr_form = 0) or on one
+    // cluster when S^* fits its shared memory (qr_form = 1) -- with the float64 persistent
+    // kernel after it, which runs only if the float-float kernel's range check sent the
+    // factorization back; the float64 QR alone for qr_form = 2 and the other forms
+    bool ff_first = false;
     int* qr_flag = h->status + 4;
-    if (h->opts.mode == RTPROJ_MIXED_REFINED && h->opts.qr_form == 1 && pivoted_qr_persistent_ok(m, (int)l))
-        RT_CHECK(pivoted_qr_cluster(h->S, m, (int)l, l, h->R, h->perm, qr_flag, s, &cluster));
+    if (h->opts.mode == RTPROJ_MIXED_REFINED && !h->sparse) {
+        if (h->opts.qr_form == 1 && pivoted_qr_persistent_ok(m, (int)l))
+            RT_CHECK(pivoted_qr_cluster(h->S, m, (int)l, l, h->R, h->perm, qr_flag, s, &ff_first));
+        else if (h->opts.qr_form == 0)
+            RT_CHECK(pivoted_qr_ff(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s, h->spin_limit,
+                                   qr_flag, &ff_first));
+    }
     RT_CHECK(pivoted_qr(h->S, m, (int)l, l, h->R, h->perm, h->qr_work, h->status, s, h->spin_limit,
-                        cluster ? qr_flag : nullptr));
+                        ff_first ? qr_flag : nullptr));
     // default threshold: 8 times the sketch's relative precision -- 2^-52 in float64, 2^(-8 s)
     // for the s digits of A that the mixed form's sketch reads
     const double u_sketch = h->opts.mode == RTPROJ_MIXED_REFINED && !h->sparse

@@ -110,6 +110,18 @@ struct Gemm64 {
 // Enqueues the GEMM + reduce. part/part_elems: scratch for the partial slabs.
 cudaError_t gemm64(const Gemm64& g, double* part, size_t part_elems, cudaStream_t s);
 
+// C (M x N, M <= 64, ld c_rs) = A (M x K, ld a_rs) B (K x N) for a long K, where
+// B(k, j) = B[k b_rs + j b_cs] or, with omega_dist >= 0, G(k, j) of Eq. 12 (k_fp64.cu).
+// part: chunks x M x N doubles of scratch.
+struct Narrow64 {
+    int M = 0, N = 0, K = 0;
+    const double* A = nullptr; int64_t a_rs = 0;
+    const double* B = nullptr; int64_t b_rs = 0, b_cs = 0;
+    int omega_dist = -1; uint64_t seed = 0;
+    double* C = nullptr; int64_t c_rs = 0;
+};
+cudaError_t gemm64_narrow(const Narrow64& g, double* part, size_t part_elems, cudaStream_t s);
+
 // Small helpers (k_fp64.cu)
 cudaError_t set_identity(double* X, int m, cudaStream_t s);
 cudaError_t transpose_copy(const double* src, int64_t s_rs, double* dst, int64_t d_rs, int rows, int cols, cudaStream_t s);
@@ -129,6 +141,11 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                        double* work, int* status, cudaStream_t s, long long spin_limit,
                        const int* run_if = nullptr);
 bool pivoted_qr_persistent_ok(int m, int l);
+// The mixed form's QR in float-float on the whole grid (k_qr.cu): sets *launched when the
+// kernel was enqueued; the kernel writes *fallback = 1 when the entries' range needs the
+// float64 kernel, which must follow with run_if = fallback.
+cudaError_t pivoted_qr_ff(double* S, int m, int l, int64_t lds, double* R, int32_t* perm, double* work, int* status,
+                          cudaStream_t s, long long spin_limit, int* fallback, bool* launched);
 // The mixed form's QR on one 16-CTA cluster in float-float arithmetic (k_qr_cluster.cu).
 // Sets *launched when the kernel was enqueued; the kernel then writes *fallback = 1 if the
 // entries' range needs the float64 kernel (which must follow with run_if = fallback).

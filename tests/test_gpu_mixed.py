@@ -217,17 +217,20 @@ def test_nonfinite_entry_of_a_is_reported_by_precondition():
         assert e.value.code == 5
 
 
-@pytest.mark.parametrize("m,n,l", [(64, 2048, 256), (37, 1000, 41), (512, 8192, 516)])
-def test_cluster_qr_is_a_valid_pivoted_qr(m, n, l):
-    """The mixed form's float-float cluster QR, checked by properties that do not depend on
-    how near-ties between pivots resolve: R^* R equals the Gram matrix of the permuted S^*
-    (S^* Pi = Q R with orthonormal Q) to float-float accuracy, R is upper triangular, and
-    every diagonal entry dominates the trailing part of its row's columns (the column-pivoting
-    property: |R_jj|^2 >= sum_{i >= j} R_ic^2 for c > j)."""
+@pytest.mark.parametrize("m,n,l,form", [(64, 2048, 256, 1), (37, 1000, 41, 1), (512, 8192, 516, 1),
+                                         (64, 2048, 256, 0), (37, 1000, 41, 0), (512, 8192, 516, 0),
+                                         (2048, 8192, 4128, 0)])
+def test_float_float_qr_is_a_valid_pivoted_qr(m, n, l, form):
+    """The mixed form's float-float QRs (qr_form 0: the whole grid, columns in shared memory
+    or, at 2048 x 4128, in global memory; 1: one cluster), checked by properties that do not
+    depend on how near-ties between pivots resolve: R^* R equals the Gram matrix of the
+    permuted S^* (S^* Pi = Q R with orthonormal Q) to float-float accuracy, R is upper
+    triangular, and every diagonal entry dominates the trailing part of its row's columns
+    (the column-pivoting property: |R_jj|^2 >= sum_{i >= j} R_ic^2 for c > j)."""
     torch = torch_cuda()
     rt = rt_module()
     A = workloads.haar_spectrum_matrix(m, n, 1e-8, 80 + m)
-    with _mixed(rt, torch, A, l, 1, qr_form=1) as P:
+    with _mixed(rt, torch, A, l, 1, qr_form=form) as P:
         S = P.sketch(seed=21, l=l).cpu().numpy()
         P.precondition(seed=21, l=l)
         R, perm, _ = P.export_state()
@@ -241,14 +244,14 @@ def test_cluster_qr_is_a_valid_pivoted_qr(m, n, l):
         assert R[j, j] ** 2 >= (1 - 1e-6) * np.max(tail[j, j + 1:])
 
 
-def test_cluster_and_float64_qr_give_the_same_projection():
+def test_qr_forms_give_the_same_projection():
     torch = torch_cuda()
     rt = rt_module()
     m, n, l, k = 64, 4096, 256, 4
     A = workloads.haar_spectrum_matrix(m, n, 1e-10, 85)
     B = workloads.rhs(k, n, 86)
     Zx, _, _ = exact.exact_project(A, B)
-    for form in (0, 1):
+    for form in (0, 1, 2):
         with _mixed(rt, torch, A, l, k, qr_form=form) as P:
             P.precondition(seed=5, l=l)
             assert P.info()["kappa_R"] > 1e8                 # rank revealing: R_11 / R_mm ~ kappa
