@@ -729,16 +729,11 @@ cudaError_t qr_check(const double* R, int32_t* perm, int m, double tol, int* sta
     return cudaGetLastError();
 }
 
-// Columns per CTA of the float-float kernel's shared-memory form (RTPROJ_QR_COLS overrides
-// it for measurements; the default came from a sweep at 512 x 516).
-int ff_cols_per_cta() {
-    static int v = -1;
-    if (v < 0) {
-        const char* e = std::getenv("RTPROJ_QR_COLS");
-        v = e ? std::max(1, std::min(PQ_MAXC, std::atoi(e))) : 4;
-    }
-    return v;
-}
+// Columns per CTA of the float-float kernel's shared-memory form. Measured at 512 x 516:
+// 4 (128 CTAs) 2.40 ms per factorization, 8 (64 CTAs) 2.57 ms, 16 (32 CTAs) 3.26 ms; with
+// four steps in flight the smaller grids left more SMs to the other steps (17,886, 18,463
+// and 18,508 projections/s), a smaller gain than the latency they cost one step.
+constexpr int ff_cols_per_cta() { return 4; }
 
 cudaError_t pivoted_qr_ff(double* S, int m, int l, int64_t lds, double* R, int32_t* perm, double* work, int* status,
                           cudaStream_t s, long long spin_limit, int* fallback, bool* launched) {
