@@ -333,8 +333,7 @@ def phase_work(mode, w, o):
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
 # `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu-baseline --no-accuracy --no-fp64-form`
 # on the 512 x 65536 workload; to be replaced by None whenever that kernel changes.
-PROFILED_TRAFFIC = {("dense_512x65536", "qr_persistent_kernel"): 2160128 + 217600,
-                    ("dense_512x65536", "qr_persistent_ff_kernel"): 2182912 + 307456}
+PROFILED_TRAFFIC = {("dense_512x65536", "qr_persistent_kernel"): 2160128 + 217600}
 
 
 def roofline_entry(mode, phase_ms, phase_cnt, steps, w, pk, opts):

@@ -183,7 +183,6 @@ __global__ void qr_extract_r_kernel(const double* S, int m, int64_t lds, double*
 // (GB300's FP64 pipe takes 64 cycles per warp instruction, active lanes or not, so long
 // float64 chains are split into independent partial sums.)
 constexpr int PQ_THREADS = 128;
-constexpr int PQ_WARPS = PQ_THREADS / 32;
 constexpr int PQ_MAXC = 32;
 constexpr int PQ_MAX_G = 256;
 constexpr int PQ_VLOAD = 5;             // slot entries per thread held in registers (l <= 640)
@@ -202,6 +201,7 @@ struct PqrDev {
     const int* run_if;       // when set, the kernel runs only if *run_if != 0
     int* fallback;           // float-float form: set to 1 when the float64 kernel must run instead
     int* emax;               // float-float form: G exponents of the CTAs' largest entries
+    unsigned long long* best;   // float-float form: m + 1 packed winners, one word per step (zeroed)
 };
 
 __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
@@ -455,6 +455,12 @@ __global__ void __launch_bounds__(PqrShape<GLOBAL_COLS>::NT, 1) qr_persistent_ke
 // columns in the work area). Accuracy: R is the exact factor of S^* + E with ||E|| of
 // order l 2^-48 ||S||, which the preconditioner tolerates while 2^-48 kappa(A) << 1; the
 // refinement makes the projection exact whatever the preconditioner's rounding.
+// The CTA's best remaining column for step s: its exact squared norm in bval, and a packed
+// key in the step's word best[s] by one 64-bit atomic maximum -- the norm's bit pattern
+// without its 12 lowest mantissa bits (the order of non-negative doubles), then 4095 minus
+// the column index -- so that after the exchange every CTA reads the winner with one load
+// instead of every CTA's candidate. Columns whose norms agree to 40 mantissa bits count as
+// tied (lowest index first).
 template <bool GLOBAL_COLS>
 __device__ __forceinline__ void publish_best_ff(const PqrDev& p, int b, int G, int s, int nc, const int* posq,
                                                 const ff* nsq) {
@@ -462,8 +468,13 @@ __device__ __forceinline__ void publish_best_ff(const PqrDev& p, int b, int G, i
     for (int q = 0; q < nc; ++q)
         if (posq[q] < 0 && (bq < 0 || ff_gt(nsq[q], nsq[bq]))) bq = q;
     const int par = s & 1;
-    p.bval[par * G + b] = bq >= 0 ? ff_to_double(nsq[bq]) : 0.0;
-    p.bidx[par * G + b] = bq >= 0 ? b * p.cpc + bq : p.m;
+    if (bq >= 0) {
+        const double v = ff_to_double(nsq[bq]);
+        p.bval[par * G + b] = v;
+        const unsigned long long key =
+            ((sq_bits(v) >> 12) << 12) | (unsigned long long)(4095 - (b * p.cpc + bq));
+        atomicMax(p.best + s, key);
+    }
     red_release_add(p.counter, 1u);
 }
 
@@ -480,8 +491,6 @@ __global__ void __launch_bounds__(NT, 1) qr_persistent_ff_kernel(PqrDev p) {
     __shared__ ff nsq[PQ_MAXC];
     __shared__ ff alphaq[PQ_MAXC];
     __shared__ int posq[PQ_MAXC];
-    __shared__ unsigned long long redb[2 * NW];
-    __shared__ int redi[2 * NW];
     __shared__ double red_d[NW];
     __shared__ int ok_s, e_s;
     const int c0 = b * cpc;
@@ -542,31 +551,11 @@ __global__ void __launch_bounds__(NT, 1) qr_persistent_ff_kernel(PqrDev p) {
                                      p.timeout);
         __syncthreads();
         if (!ok_s) return;
-        unsigned long long best = 0;
-        int bi = m;
-        for (int g = t; g < G; g += NT) {
-            const unsigned long long x = sq_bits(__ldcg(p.bval + par * G + g));
-            const int i = __ldcg(p.bidx + par * G + g);
-            if (i < m && (bi == m || x > best || (x == best && i < bi))) { best = x; bi = i; }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (oi < m && (bi == m || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; }
-        }
-        if (lane == 0) { redb[par * NW + warp] = best; redi[par * NW + warp] = bi; }
-        __syncthreads();
-        unsigned long long bb = redb[par * NW];
-        int ii = redi[par * NW];
-        for (int w = 1; w < NW; ++w) {
-            const unsigned long long xb = redb[par * NW + w];
-            const int xi = redi[par * NW + w];
-            if (xi < m && (ii == m || xb > bb || (xb == bb && xi < ii))) { bb = xb; ii = xi; }
-        }
-        if (ii >= m) return;                                   // cannot happen while columns remain
-        const int piv = ii;
-        const ff npiv = ff_from_double(__longlong_as_double((long long)bb));
+        const unsigned long long key = __ldcg(p.best + j);
+        if (key == 0ull) return;                               // cannot happen while columns remain
+        const int piv = 4095 - (int)(key & 4095ull);
+        if (piv < 0 || piv >= m) return;
+        const ff npiv = ff_from_double(__ldcg(p.bval + par * G + piv / cpc));
         if (npiv.hi < 7.888609052210118e-31f) {                // 2^-100: the float64 kernel takes over
             if (b == 0 && t == 0) *p.fallback = 1;
             return;
@@ -690,7 +679,7 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
 size_t pivoted_qr_work_doubles(int m, int l) {
     const size_t steps = (size_t)3 * m + 3 * (size_t)l + 2048;                       // per-step form
     // staging slots (G * cpc < m + cpc columns per parity), candidates, counter and flag
-    const size_t persistent = (size_t)2 * ((size_t)m + PQ_MAXC) * l + 5 * (size_t)PQ_MAX_G + 64;
+    const size_t persistent = (size_t)2 * ((size_t)m + PQ_MAXC) * l + 5 * (size_t)PQ_MAX_G + (size_t)m + 65;
     return steps > persistent ? steps : persistent;
 }
 
@@ -776,6 +765,7 @@ cudaError_t pivoted_qr_ff(double* S, int m, int l, int64_t lds, double* R, int32
     p.bval = w;                     w += 2 * (size_t)G;
     p.bidx = (int*)w;               w += G;          // 2G ints
     p.emax = (int*)w;               w += G;          // G ints
+    p.best = (unsigned long long*)w; w += m + 1;     // one word per step
     unsigned int* ctr = (unsigned int*)w;            // counter, abort
     p.counter = ctr;
     p.abort_flag = (int*)(ctr + 1);
@@ -784,6 +774,7 @@ cudaError_t pivoted_qr_ff(double* S, int m, int l, int64_t lds, double* R, int32
     p.run_if = nullptr;
     p.fallback = fallback;
     cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.best, 0, (size_t)(m + 1) * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(fallback, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     void* args[] = {&p};
@@ -847,6 +838,7 @@ cudaError_t pivoted_qr(double* S, int m, int l, int64_t lds, double* R, int32_t*
                 p.run_if = run_if;
                 p.fallback = nullptr;
                 p.emax = nullptr;
+                p.best = nullptr;
                 cudaError_t e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s);
                 if (e != cudaSuccess) return e;
                 void* args[] = {&p};
