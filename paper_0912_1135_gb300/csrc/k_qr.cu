@@ -555,26 +555,36 @@ __global__ void __launch_bounds__(NT, 1) qr_persistent_ff_kernel(PqrDev p) {
         if (key == 0ull) return;                               // cannot happen while columns remain
         const int piv = 4095 - (int)(key & 4095ull);
         if (piv < 0 || piv >= m) return;
-        const ff npiv = ff_from_double(__ldcg(p.bval + par * G + piv / cpc));
+        // 2. the reflector from the pivot column (rows j .. l-1): the column's loads, its norm
+        //    and its first entry are all issued before any of them is used
+        const float2* slot = GLOBAL_COLS ? slots + (size_t)piv * l : slots + (size_t)par * slot_par + (size_t)piv * l;
+        float2 vr[PQ_VLOAD];
+#pragma unroll
+        for (int k = 0; k < PQ_VLOAD; ++k) {
+            const int i = j + t + k * NT;
+            vr[k] = i < l ? __ldcg(slot + i) : make_float2(0.f, 0.f);
+        }
+        const double nsq_piv = __ldcg(p.bval + par * G + piv / cpc);
+        const float2 x0f = __ldcg(slot + j);
+        const ff npiv = ff_from_double(nsq_piv);
         if (npiv.hi < 7.888609052210118e-31f) {                // 2^-100: the float64 kernel takes over
             if (b == 0 && t == 0) *p.fallback = 1;
             return;
         }
-        // 2. the reflector from the pivot column (rows j .. l-1)
-        const float2* slot = GLOBAL_COLS ? slots + (size_t)piv * l : slots + (size_t)par * slot_par + (size_t)piv * l;
-        const float2 x0f = __ldcg(slot + j);
         const ff x0 = {x0f.x, x0f.y};
         const ff nx = ff_sqrt(npiv);
         const ff ax = x0.hi >= 0.f ? x0 : ff_neg(x0);
         const ff alpha = x0.hi >= 0.f ? ff_neg(nx) : nx;
         const ff beta = ff_recip(ff_mul(nx, ff_add(nx, ax)));
-        for (int i = j + t; i < l; i += NT) {
-            if (i == j) {
-                const ff v0 = ff_add(x0, ff_neg(alpha));
-                v[0] = make_float2(v0.hi, v0.lo);
-            } else {
-                v[i - j] = __ldcg(slot + i);
-            }
+#pragma unroll
+        for (int k = 0; k < PQ_VLOAD; ++k) {
+            const int i = j + t + k * NT;
+            if (i < l) v[i - j] = vr[k];
+        }
+        for (int i = j + t + PQ_VLOAD * NT; i < l; i += NT) v[i - j] = __ldcg(slot + i);
+        if (t == 0) {
+            const ff v0 = ff_add(x0, ff_neg(alpha));
+            v[0] = make_float2(v0.hi, v0.lo);
         }
         if (t == 0 && piv >= c0 && piv < c0 + nc) {
             const int q = piv - c0;
