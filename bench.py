@@ -333,7 +333,8 @@ def phase_work(mode, w, o):
 # DRAM bytes (read + write) per launch of a kernel, from one ncu capture of
 # `bench.py --steps 1 --warmup 3 --no-e2e --no-cpu-baseline --no-accuracy --no-fp64-form`
 # on the 512 x 65536 workload; to be replaced by None whenever that kernel changes.
-PROFILED_TRAFFIC = {("dense_512x65536", "qr_persistent_kernel"): 2160128 + 217600}
+PROFILED_TRAFFIC = {("dense_512x65536", "qr_persistent_kernel"): 2160128 + 217600,
+                    ("dense_512x65536", "qr_persistent_ff_kernel"): 2189568 + 289024}
 
 
 def roofline_entry(mode, phase_ms, phase_cnt, steps, w, pk, opts):
@@ -370,6 +371,9 @@ def run_ours(args, w, world, rank, local):
     pk = peaks()
     key = workload_key(w)
     wopts = dict(WORKLOAD_OPTS.get(key, {})) if args.mode == "mixed" else {}
+    for kv in args.opt or []:                 # --opt name=value: an rtproj_opts field
+        name, val = kv.split("=", 1)
+        wopts[name] = float(val) if name.endswith("_tol") else int(val)
     A = w.matrix(device=dev) if key in DEVICE_GENERATED else w.matrix()
     B = w.rhs()
     At = torch.from_numpy(A).to(dev)
@@ -968,6 +972,8 @@ def main():
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
     ap.add_argument("--pipeline", type=int, default=4,
                     help="handles (and streams) the timed steps rotate over; > 1 overlaps consecutive steps")
+    ap.add_argument("--opt", action="append", default=None,
+                    help="an rtproj_opts field for the timed handles, name=value (repeatable)")
     ap.add_argument("--sparse-row", default=None,
                     help="with --study sparse: only the rows m,n,l,kappa of Tables 1 and 5 (e.g. 1000,300000,1004,1e8)")
     ap.add_argument("--study", choices=["accuracy", "variates", "batch", "sparse"], default=None,
