@@ -244,6 +244,27 @@ def test_float_float_qr_is_a_valid_pivoted_qr(m, n, l, form):
         assert R[j, j] ** 2 >= (1 - 1e-6) * np.max(tail[j, j + 1:])
 
 
+@pytest.mark.parametrize("form", [0, 1])
+def test_float_float_qr_hands_a_wide_range_to_the_float64_kernel(form):
+    """Rows of A scaled by 2^0 .. 2^-100 (the row space, hence Z, is unchanged): the columns
+    of S^* then span 2^100 in norm, their squares 2^200 -- beyond float-float's range -- so
+    the float-float QR (grid or cluster) must hand the factorization to the float64 kernel,
+    and the projection must still be that of the unscaled matrix."""
+    torch = torch_cuda()
+    rt = rt_module()
+    m, n, l, k = 64, 2048, 256, 3
+    A = workloads.haar_spectrum_matrix(m, n, 1e-3, 91)
+    B = workloads.rhs(k, n, 92)
+    Zx, _, _ = exact.exact_project(A, B)
+    As = A * (2.0 ** (-100.0 * np.arange(m) / (m - 1)))[:, None]
+    # R_mm / R_11 is about 2^-100 kappa^-1 here by construction, so the rank test is opened
+    with _mixed(rt, torch, As, l, k, qr_form=form, refine_passes=4, refine_tol=1e-13, rank_tol=1e-300) as P:
+        P.precondition(seed=93, l=l)
+        Z = P.null_project(to_dev(torch, B)).cpu().numpy()
+        assert P.info()["status"] == 0
+    assert_rows_close(Z, Zx, Z_TOL, f"Z (qr_form={form})")
+
+
 def test_qr_forms_give_the_same_projection():
     torch = torch_cuda()
     rt = rt_module()
