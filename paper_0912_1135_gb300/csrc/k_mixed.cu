@@ -40,7 +40,7 @@ int s_all(const rtproj_opts& o) {
 }
 
 struct MixedLayout {
-    size_t A, eA, AT, eAT, G, eG, Mp, Ms, eM, W, eW, B, eB, H, eH, S, eS, T, eT, Tt, eTt, scratch, total;
+    size_t A, eA, AT, eAT, G, eG, Mp, Ms, eM, W, eW, B, eB, H, eH, S, eS, T, eT, Tt, eTt, negEA, scratch, total;
 };
 
 MixedLayout mixed_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtproj_opts& o) {
@@ -71,6 +71,7 @@ MixedLayout mixed_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, con
     L.eT = take((size_t)m * 4);
     L.Tt = take((size_t)o.apply_slices * m * ldm * 2);
     L.eTt = take((size_t)m * 4);
+    L.negEA = take((size_t)m * 4);
     L.scratch = take(kScratch);
     L.total = off;
     return L;
@@ -118,6 +119,15 @@ __global__ void permute_columns_kernel(const double* T, const int32_t* perm, int
     if (idx >= (int64_t)m * m) return;
     const int i = (int)(idx / m), t = (int)(idx % m);
     D[(int64_t)i * m + perm[t]] = T[idx];
+}
+
+// D'[i][t] = D[i][t] 2^{e[t]} in place (exact), and ne[t] = -e[t]
+__global__ void scale_columns_pow2_kernel(double* D, const int32_t* e, int m, int32_t* ne) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)m * m) return;
+    const int t = (int)(idx % m);
+    D[idx] = ldexp(D[idx], e[t]);
+    if (idx < m) ne[idx] = -e[idx];
 }
 
 __global__ void axpy_kernel(double* y, const double* x, int64_t n) {
@@ -170,6 +180,7 @@ rtproj_status mixed_bind(rtproj_ctx* h, char* base, size_t bytes) {
     h->Ss = stack(base, L.S, L.eS, (int)h->k_max, n, o.resid_slices, ldn);
     h->Ts = stack(base, L.T, L.eT, m, m, o.apply_slices, ldm);
     h->Tts = stack(base, L.Tt, L.eTt, m, m, o.apply_slices, ldm);
+    h->neg_eA = (int32_t*)(base + L.negEA);
     h->sg_scratch = base + L.scratch;
     h->sg_scratch_bytes = kScratch;
     return RTPROJ_OK;
@@ -219,6 +230,10 @@ rtproj_status mixed_gram(rtproj_ctx* h) {
 // k right-hand sides. Every digit product is exact, so each product is accurate to
 // 2^{-8 apply_slices} relative to |D||c| -- tighter than float64 rounding of the same
 // products, and the refinement pass corrects what remains.
+// Entry t of c = A b carries the scale of row t of A (2^{e_A[t]}), and column t of D its
+// inverse, so the first product runs as D' c' with D' = D diag(2^{e_A}) and c' = c
+// diag(2^{-e_A}): digits sliced per right-hand side then keep every row's digits whatever
+// the spread of A's row scales (rows scaled apart leave the projection unchanged).
 rtproj_status mixed_prepare_middle(rtproj_ctx* h) {
     const int m = (int)h->m;
     const int64_t total = (int64_t)m * m;
@@ -226,8 +241,12 @@ rtproj_status mixed_prepare_middle(rtproj_ctx* h) {
     permute_columns_kernel<<<(unsigned)((total + 255) / 256), 256, 0, h->stream>>>(h->T1, h->perm, m, h->Mprime);
     note_launch();
     MX_CHECK(cudaGetLastError());
-    MX_CHECK(slice_rows(h->Mprime, m, 1, nullptr, nullptr, h->Ts, h->status, h->stream));
-    MX_CHECK(slice_rows(h->Mprime, 1, m, nullptr, nullptr, h->Tts, h->status, h->stream));
+    MX_CHECK(slice_rows(h->Mprime, 1, m, nullptr, nullptr, h->Tts, h->status, h->stream));      // D^*
+    scale_columns_pow2_kernel<<<(unsigned)((total + 255) / 256), 256, 0, h->stream>>>(h->Mprime, h->As.e, m,
+                                                                                        h->neg_eA);
+    note_launch();
+    MX_CHECK(cudaGetLastError());
+    MX_CHECK(slice_rows(h->Mprime, m, 1, nullptr, nullptr, h->Ts, h->status, h->stream));      // D'
     phase_end(h, RTPROJ_PHASE_SLICE);
     return RTPROJ_OK;
 }
@@ -238,8 +257,8 @@ namespace {
 rtproj_status middle_mixed(rtproj_ctx* h, const double* c, double* out, int k) {
     const int ap = h->opts.apply_slices;
     const SliceStack Hk = rows_of(h->Hs, k, ap);
-    MX_CHECK(slice_rows(c, 1, k, nullptr, nullptr, Hk, h->status, h->stream));             // c^*: k x m
-    rtproj_status st = gemm(h, h->Ts, Hk, ap, h->ebuf, k, 1);                              // u = D c
+    MX_CHECK(slice_rows(c, 1, k, nullptr, h->neg_eA, Hk, h->status, h->stream));           // c'^*: k x m
+    rtproj_status st = gemm(h, h->Ts, Hk, ap, h->ebuf, k, 1);                              // u = D' c' = D c
     if (st != RTPROJ_OK) return st;
     MX_CHECK(slice_rows(h->ebuf, 1, k, nullptr, nullptr, Hk, h->status, h->stream));        // u^*: k x m
     return gemm(h, h->Tts, Hk, ap, out, k, 1);                                             // D^* u

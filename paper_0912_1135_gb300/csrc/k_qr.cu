@@ -491,34 +491,51 @@ __global__ void __launch_bounds__(NT, 1) qr_persistent_ff_kernel(PqrDev p) {
     __shared__ ff nsq[PQ_MAXC];
     __shared__ ff alphaq[PQ_MAXC];
     __shared__ int posq[PQ_MAXC];
-    __shared__ double red_d[NW];
-    __shared__ int ok_s, e_s;
+    __shared__ int ok_s, e_s, range_s;
     const int c0 = b * cpc;
     const int nc = max(0, min(cpc, m - c0));
 
-    // 0. the scale: exponents of the CTAs' largest entries, exchanged once
-    double mx = 0.0;
-    for (int q = 0; q < nc; ++q)
-        for (int i = t; i < l; i += NT) mx = fmax(mx, fabs(p.S[(int64_t)(c0 + q) * p.lds + i]));
+    // 0. the scale: exponents of the CTAs' largest entries, and of their columns' smallest
+    //    largest entry, exchanged once. Columns whose largest entries span more than 2^40
+    //    (a graded S^*, e.g. rows of A scaled far apart) would take float-float's products
+    //    toward float's underflow as the factorization reaches them: the float64 kernel
+    //    takes the whole factorization instead.
+    __shared__ double col_mx[PQ_MAXC];
+    for (int q = warp; q < nc; q += NW) {
+        double cm = 0.0;
+        for (int i = lane; i < l; i += 32) cm = fmax(cm, fabs(p.S[(int64_t)(c0 + q) * p.lds + i]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red_d[warp] = mx;
+        for (int o = 16; o > 0; o >>= 1) cm = fmax(cm, __shfl_xor_sync(0xffffffffu, cm, o));
+        if (lane == 0) col_mx[q] = cm;
+    }
     __syncthreads();
     if (t == 0) {
-        double bm = 0.0;
-        for (int w = 0; w < NW; ++w) bm = fmax(bm, red_d[w]);
-        int e = INT_MIN / 2;
-        if (bm > 0.0) frexp(bm, &e);                       // bm < 2^e
-        p.emax[b] = e;
+        int e_hi = INT_MIN / 2, e_lo = INT_MAX / 2;
+        for (int q = 0; q < nc; ++q) {
+            int e = INT_MIN / 2;
+            if (col_mx[q] > 0.0) frexp(col_mx[q], &e);   // col_mx < 2^e
+            e_hi = max(e_hi, e);
+            e_lo = min(e_lo, e);
+        }
+        p.emax[b] = e_hi;
+        p.emax[G + b] = e_lo;
         red_release_add(p.counter, 1u);
         ok_s = wait_geq(p.counter, (unsigned int)G, p.abort_flag, p.status, p.timeout);
-        int E = INT_MIN / 2;
+        int E = INT_MIN / 2, Elo = INT_MAX / 2;
         if (ok_s)
-            for (int g = 0; g < G; ++g) E = max(E, __ldcg(p.emax + g));
+            for (int g = 0; g < G; ++g) {
+                E = max(E, __ldcg(p.emax + g));
+                Elo = min(Elo, __ldcg(p.emax + G + g));
+            }
         e_s = E == INT_MIN / 2 ? 0 : E;
+        range_s = E - Elo;
     }
     __syncthreads();
     if (!ok_s) return;
+    if (range_s > 40) {                                     // the same decision in every CTA
+        if (b == 0 && t == 0) *p.fallback = 1;
+        return;
+    }
     const int E = e_s;
     const double sc = ldexp(1.0, -E);
     for (int q = 0; q < nc; ++q)
@@ -774,7 +791,7 @@ cudaError_t pivoted_qr_ff(double* S, int m, int l, int64_t lds, double* R, int32
     p.slots = w;                    w += in_smem ? (size_t)2 * G * cpc * l : (size_t)G * cpc * l;
     p.bval = w;                     w += 2 * (size_t)G;
     p.bidx = (int*)w;               w += G;          // 2G ints
-    p.emax = (int*)w;               w += G;          // G ints
+    p.emax = (int*)w;               w += G;          // 2G ints: largest and smallest exponents
     p.best = (unsigned long long*)w; w += m + 1;     // one word per step
     unsigned int* ctr = (unsigned int*)w;            // counter, abort
     p.counter = ctr;

@@ -335,6 +335,7 @@ struct rtproj_ctx {
     rtp::SliceStack Ts;          // T1 Pi (columns permuted): m x m, reduction over m
     rtp::SliceStack Tts;         // (T1 Pi)^*: m x m, reduction over m
     double* Mprime = nullptr;    // m x m
+    int32_t* neg_eA = nullptr;   // m: minus A's row exponents (the m x m stage's digit scales)
     void* sg_scratch = nullptr;  // int64 split-K partials
     size_t sg_scratch_bytes = 0;
 

@@ -244,7 +244,7 @@ def test_float_float_qr_is_a_valid_pivoted_qr(m, n, l, form):
         assert R[j, j] ** 2 >= (1 - 1e-6) * np.max(tail[j, j + 1:])
 
 
-@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("form", [0, 1, 2])
 def test_float_float_qr_hands_a_wide_range_to_the_float64_kernel(form):
     """Rows of A scaled by 2^0 .. 2^-100 (the row space, hence Z, is unchanged): the columns
     of S^* then span 2^100 in norm, their squares 2^200 -- beyond float-float's range -- so
