@@ -257,6 +257,18 @@ def time_steps(torch, P, Bt, seed, l, steps, stream):
     return ev0.elapsed_time(ev1)
 
 
+def pipeline_depth(torch, rt, args, w, wopts, P, dev):
+    """Handles for the pipelined steps: --pipeline, as many as fit in a third of the free
+    device memory (each handle holds its own digit planes of A and its own buffers)."""
+    if args.pipeline <= 1:
+        return 1
+    import ctypes
+    o = P.opts
+    per = int(rt.load_library().rtproj_workspace_bytes(w.m, w.n, w.l, w.k, ctypes.byref(o)))
+    free = torch.cuda.mem_get_info(dev)[0]
+    return max(1, min(args.pipeline, free // 3 // max(per, 1)))
+
+
 def time_steps_pipelined(torch, Ps, Bt, seed, l, steps, stream, Zs):
     """The same steps on len(Ps) handles bound to the same A, each on its own stream and in
     the asynchronous mode: step i runs on handle i mod len(Ps), so a step's apply (tensor
@@ -389,9 +401,10 @@ def run_ours(args, w, world, rank, local):
     torch.cuda.synchronize()
     P.timings()
     pipe = []
-    if args.pipeline > 1:
+    depth = pipeline_depth(torch, rt, args, w, wopts, P, dev)
+    if depth > 1:
         pipe = [rt.Projector(At, l_max=w.l, k_max=w.k, mode=args.mode, stream=torch.cuda.Stream(dev), async_=1,
-                             **wopts) for _ in range(args.pipeline)]
+                             **wopts) for _ in range(depth)]
         Zs = [torch.empty_like(Bt) for _ in pipe]
         time_steps_pipelined(torch, pipe, Bt, seed0, w.l, args.warmup, stream, Zs)
     launches0 = rt.launch_count()
@@ -444,9 +457,9 @@ def run_ours(args, w, world, rank, local):
         "config": {"workload": w.name, "mode": args.mode, "m": w.m, "n": w.n, "k": w.k, "l": w.l,
                    "kappa": 1.0 / w.sigma_min, "omega": "gaussian (Box-Muller on Philox4x32-10, 2^-12 grid)",
                    "step": "precondition(seed, l) + null_project(k RHS)",
-                   "pipeline": (f"up to {args.pipeline} consecutive steps in flight, each on its own handle and "
-                                "stream: one step's latency-bound QR and Cholesky overlap the others' tensor-core "
-                                "products") if args.pipeline > 1 else "one handle, steps in order",
+                   "pipeline": (f"up to {depth} consecutive steps in flight, each on its own handle and stream: "
+                                "their latency-bound QRs and Cholesky factorizations share the SMs, and so do their "
+                                "tensor-core products") if depth > 1 else "one handle, steps in order",
                    "l2": f"inputs larger than L2 (A is {A.nbytes / 1e6:.0f} MB float64)",
                    "parallelism": f"replicas x{world}", "options": wopts},
         "phase_ms_per_step": {p: phase_ms[p] / args.steps for p in phase_ms if phase_cnt[p]},
@@ -472,7 +485,7 @@ def run_ours(args, w, world, rank, local):
     if args.mode == "mixed" and not args.no_fp64_form:
         line["fp64_form"] = fp64_form(torch, rt, A, B, At, Bt, w, args, rank)
     if not args.no_e2e:
-        line["e2e"] = e2e(torch, rt, A, B, w, args, dev)
+        line["e2e"] = e2e(torch, rt, A, B, w, args, dev, wopts)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(A, B)
     if rank == 0:
@@ -581,7 +594,7 @@ def fp64_form(torch, rt, A, B, At, Bt, w, args, rank):
     return out
 
 
-def e2e(torch, rt, A, B, w, args, dev):
+def e2e(torch, rt, A, B, w, args, dev, wopts):
     """Same metric through the public API from pinned host buffers. Every step copies its A
     and B host-to-device, creates a Projector (A is sliced at create), preconditions,
     projects and copies Z device-to-host, all inside the timed region. As a serving loop
@@ -594,7 +607,13 @@ def e2e(torch, rt, A, B, w, args, dev):
     Bh = torch.from_numpy(B).pin_memory()
     npipe = max(1, min(args.pipeline, 4))               # steps in flight, one compute stream each
     Zh = [torch.empty(B.shape, dtype=torch.float64).pin_memory() for _ in range(npipe)]
-    steps = max(1, min(args.steps, 15))
+    # every step's handle stays alive until the end: as many steps as fit in half the free
+    # memory besides the device copies of A and B
+    import ctypes
+    o = rt.make_opts(args.mode, **wopts)
+    per = int(rt.load_library().rtproj_workspace_bytes(w.m, w.n, w.l, w.k, ctypes.byref(o)))
+    room = torch.cuda.mem_get_info(dev)[0] // 2 - npipe * (A.nbytes + B.nbytes)
+    steps = max(1, min(args.steps, 15, room // max(per, 1) - 1))
     comp = torch.cuda.current_stream(dev)
     comps = [torch.cuda.Stream(dev) for _ in range(npipe)]
     copy = torch.cuda.Stream(dev)
@@ -621,7 +640,7 @@ def e2e(torch, rt, A, B, w, args, dev):
         cs = comps[s]
         with torch.cuda.stream(cs):
             cs.wait_event(copied[s])
-            P = rt.Projector(Ad[s], l_max=w.l, k_max=w.k, mode=args.mode, stream=cs, async_=1)
+            P = rt.Projector(Ad[s], l_max=w.l, k_max=w.k, mode=args.mode, stream=cs, async_=1, **wopts)
             P.precondition(w.seed_omega + i, w.l)
             Z = P.null_project(Bd[s])
             handles.append(P)
@@ -970,7 +989,7 @@ def main():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true", help="skip the float64-form comparison")
     ap.add_argument("--l", type=int, default=None, help="sketch size (default: the workload's)")
-    ap.add_argument("--pipeline", type=int, default=4,
+    ap.add_argument("--pipeline", type=int, default=6,
                     help="handles (and streams) the timed steps rotate over; > 1 overlaps consecutive steps")
     ap.add_argument("--opt", action="append", default=None,
                     help="an rtproj_opts field for the timed handles, name=value (repeatable)")

@@ -76,7 +76,7 @@ constexpr size_t kPartElems = 1216ull * 4096ull;   // bounds every split-K slab 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t status, S, qr_work, perm, R, RinvT, Lc, Lt, T1, dinv, W, part, cbuf, ebuf, hbuf, dhbuf, sbuf;
+    size_t status, S, qr_work, perm, R, RinvT, Lc, Lt, T1, dinv, ffbuf, W, part, cbuf, ebuf, hbuf, dhbuf, sbuf;
     size_t A64, B64, normA, norm_part, bnorm, stats;
     size_t mixed_base, mixed_bytes;
     size_t total;
@@ -119,6 +119,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t l_max, int64_t k_max, const rtp
     L.Lt = take((size_t)m * m * 8);
     L.T1 = take((size_t)m * m * 8);
     L.dinv = take(trsm_work_doubles((int)m) * 8);
+    L.ffbuf = take(o.mode == RTPROJ_MIXED_REFINED ? ff_work_bytes((int)m) : 0);
     L.W = take((size_t)m * n * 8);
     L.part = take(kPartElems * 8);
     L.cbuf = take((size_t)m * k_max * 8);
@@ -319,6 +320,7 @@ rtproj_ctx* bind_handle(int64_t m, int64_t n, int64_t l_max, int64_t k_max, void
     h->Lt = (double*)(b + L.Lt);
     h->T1 = (double*)(b + L.T1);
     h->dinv = (double*)(b + L.dinv);
+    h->ffbuf = b + L.ffbuf;
     h->W = (double*)(b + L.W);
     h->part = (double*)(b + L.part);
     h->part_elems = kPartElems;
@@ -556,7 +558,19 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     // R^{-*} (the transpose of P^- of Eq. 15, up to Pi)
     phase_begin(h, RTPROJ_PHASE_FACTOR);
     RT_CHECK(set_identity(h->RinvT, m, s));
-    RT_CHECK(trsm(h->R, 1, m, true, m, h->RinvT, m, m, h->dinv, h->status, s, true));   // R^* X = I
+    // The mixed form takes R^{-*} and the Cholesky factor in float-float (the float64
+    // kernels enqueued behind them take over when the range check gives up): errors in
+    // R^{-*} cancel (any invertible N in place of R^{-*} Pi gives the same preconditioner,
+    // N^* (N A A^* N^*)^{-1} N), and the Cholesky's move kappa(X) 2^-48, as the float64
+    // pivot reciprocals' already do. T1 = L^{-1} R^{-*} stays in float64: in float-float its
+    // rounding raised ||dh|| / ||h|| of the first pass from 2e-6 to 1.3e-5 at 512 x 65536,
+    // kappa 1e10. The float64 and sparse forms keep every factor in float64.
+    const bool ff_factors = h->opts.mode == RTPROJ_MIXED_REFINED && !h->sparse;
+    int* ff_ctl = h->status + 10;
+    if (ff_factors)
+        RT_CHECK(trsm_ff(h->R, 1, m, m, h->RinvT, m, m, h->dinv, h->ffbuf, ff_ctl, h->status, s, true));
+    else
+        RT_CHECK(trsm(h->R, 1, m, true, m, h->RinvT, m, m, h->dinv, h->status, s, true));   // R^* X = I
     phase_end(h, RTPROJ_PHASE_FACTOR);
     // 3. X = P^{-1} A A^* P^{-*} (Eq. 14 via steps a-e, as W W^*)
     phase_begin(h, RTPROJ_PHASE_GRAM);
@@ -565,7 +579,10 @@ rtproj_status rtproj_precondition(rtproj_t h, uint64_t seed, int64_t l) {
     phase_end(h, RTPROJ_PHASE_GRAM);
     // 4. X = L L^* (in place of Y = X^{-1}, Eq. 16), T1 = L^{-1} R^{-*}
     phase_begin(h, RTPROJ_PHASE_FACTOR);
-    RT_CHECK(cholesky(h->Lc, m, h->part, h->part_elems, h->status, s, h->spin_limit));
+    if (ff_factors)
+        RT_CHECK(cholesky_ff(h->Lc, m, h->part, h->part_elems, h->ffbuf, ff_ctl, h->status, s, h->spin_limit));
+    else
+        RT_CHECK(cholesky(h->Lc, m, h->part, h->part_elems, h->status, s, h->spin_limit));
     // the solve reads L through its transpose, so that a warp's loads of T are coalesced
     RT_CHECK(transpose_copy(h->Lc, m, h->Lt, m, m, m, s));
     RT_CHECK(cudaMemcpyAsync(h->T1, h->RinvT, (size_t)m * m * 8, cudaMemcpyDeviceToDevice, s));

@@ -166,13 +166,29 @@ cudaError_t pivoted_qr_steps(double* S, int m, int l, int64_t lds, double* R, in
 // column counter). T is read row by row across a warp's threads: t_rs = 1 coalesces.
 // rhs_lower (lower solves only): Bm is zero above its diagonal, so the solution is too and
 // the rows above each column are skipped.
+// run_if (optional): the kernels return at once unless *run_if != 0 (a fallback enqueued
+// behind the float-float solve below).
 cudaError_t trsm(const double* T, int64_t t_rs, int64_t t_cs, bool lower, int m,
                  double* Bm, int64_t b_rs, int ncols, double* dinv_work, int* status, cudaStream_t s,
-                 bool rhs_lower = false);
+                 bool rhs_lower = false, const int* run_if = nullptr);
 size_t trsm_work_doubles(int m);
-// In-place lower Cholesky of the m x m row-major X (strict upper part zeroed).
+// In-place lower Cholesky of the m x m row-major X (strict upper part zeroed). With run_if
+// the cooperative kernel runs only if *run_if != 0 (cudaErrorNotSupported if it cannot be
+// launched).
 cudaError_t cholesky(double* X, int m, double* part, size_t part_elems, int* status, cudaStream_t s,
-                     long long spin_limit);
+                     long long spin_limit, const int* run_if = nullptr);
+// Float-float forms of the two for the mixed form (GB300's FP32 pipe runs 64 times the
+// FP64 pipe's rate; the preconditioner needs about 2^-48 of the factors, and the refinement
+// corrects the rest). Lower solves only, with the semantics of trsm(lower = true). Each
+// first checks the range of the diagonal on the device; beyond what float-float holds
+// (a span over 2^90, a zero, non-finite or non-positive pivot) it raises ctl[0] and the
+// float64 kernels, always enqueued behind, run instead. ffbuf: ff_work_bytes(m) bytes;
+// ctl: 4 ints of device memory.
+size_t ff_work_bytes(int m);
+cudaError_t trsm_ff(const double* T, int64_t t_rs, int64_t t_cs, int m, double* Bm, int64_t b_rs, int ncols,
+                    double* dinv_work, void* ffbuf, int* ctl, int* status, cudaStream_t s, bool rhs_lower);
+cudaError_t cholesky_ff(double* X, int m, double* part, size_t part_elems, void* ffbuf, int* ctl, int* status,
+                        cudaStream_t s, long long spin_limit);
 
 // ---------------------------------------------------------------------------
 // Mixed mode: fixed-point bfloat16 slicing and the sliced tensor-core GEMM.
@@ -315,6 +331,7 @@ struct rtproj_ctx {
     double* Lt = nullptr;        // m x m, chol(X)^* (read by the second triangular solve)
     double* T1 = nullptr;        // m x m, Lc^{-1} R^{-*}
     double* dinv = nullptr;      // inverses of the 32 x 32 diagonal blocks (trsm)
+    char* ffbuf = nullptr;       // mixed form: the float-float copy of a factor (ff_work_bytes)
     double* W = nullptr;         // m x n, P^{-1} A (float64 mode)
     double* part = nullptr;      // split-K partial slabs
     size_t part_elems = 0;
