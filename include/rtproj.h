@@ -72,7 +72,11 @@ typedef enum {
        (each operand split into s bfloat16 slices of 8 bits; slice products summed
        exactly in float32 and combined in 64-bit integers), a low-slice sketch,
        and one or more refinement passes (Remark 4.3) whose residuals carry more
-       than float64 accuracy. The m x m stage stays in float64. */
+       than float64 accuracy. The pivoted QR (qr_form), R^{-*} and the Cholesky factor
+       of X run in float-float on the FP32 pipe, each with the float64 kernel enqueued
+       behind it for ranges float-float cannot hold; T1 = L^{-1} R^{-*} is formed in
+       float64, and the m x m stage's products with it are sliced tensor-core products
+       (apply_slices). */
     RTPROJ_MIXED_REFINED = 1
 } rtproj_mode;
 
