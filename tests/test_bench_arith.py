@@ -1,5 +1,6 @@
 """The bench's roofline arithmetic (CPU): digit-pair counts of the sliced products and the
-apply's algorithmic bytes, against hand counts."""
+apply's algorithmic bytes, against hand counts; the pipelined steps' memory cap."""
+import ctypes
 import types
 
 import bench
@@ -35,3 +36,26 @@ def test_qr_flop_count():
     work = bench.phase_work("mixed", w, o)
     flops, bound, kernel = work["qr"]
     assert flops == 2.0 * 516 * 512 ** 2 - 2.0 * 512 ** 3 / 3.0 and kernel == "qr_persistent_ff_kernel"
+
+
+def test_pipeline_depth_is_capped_by_free_memory():
+    """--pipeline handles, as many as fit in a third of the free device memory."""
+    per = 2 << 30                                               # one handle's workspace
+
+    class Lib:
+        @staticmethod
+        def rtproj_workspace_bytes(m, n, l, k, opts):
+            return per
+
+    rt = types.SimpleNamespace(load_library=lambda: Lib)
+    P = types.SimpleNamespace(opts=ctypes.c_int(0))             # stands in for the handle's rtproj_opts
+    w = workloads.WORKLOADS["dense_512x65536"]
+
+    def depth(pipeline, free):
+        torch = types.SimpleNamespace(cuda=types.SimpleNamespace(mem_get_info=lambda dev: (free, 2 * free)))
+        return bench.pipeline_depth(torch, rt, types.SimpleNamespace(pipeline=pipeline), w, {}, P, None)
+
+    assert depth(6, 270 << 30) == 6                             # the headline size on a GB300
+    assert depth(6, 12 * per) == 4                              # a third of the room: four handles
+    assert depth(6, per) == 1                                   # never fewer than one
+    assert depth(1, 270 << 30) == 1
