@@ -70,8 +70,14 @@ def apply_roofline(w, opts, k, ms_call, passes, pk):
     tensor_flops = 2.0 * m * n * k * pairs + (1 + passes) * 2 * 2.0 * m * m * k * digit_pairs(ap, ap, ap)
     tpeak = float(pk.get("bf16_tflops_sustained") or pk["bf16_tflops"])
     fp64_equiv = 4.0 * m * n * k * (1 + passes)
+    # the HBM fraction of a call that took the longer of its two floors: the method's bytes
+    # at the HBM peak, the digit pairs at the tensor peak
+    t_bytes = bytes_alg / (float(pk["hbm_gbs"]) * 1e9)
+    t_pairs = tensor_flops / (tpeak * 1e12)
     return {
         "bound": "hbm", "achieved": hbm, "peak": float(pk["hbm_gbs"]), "unit": "GB/s", "frac": hbm / float(pk["hbm_gbs"]),
+        "frac_ceiling": t_bytes / max(t_bytes, t_pairs),
+        "frac_ceiling_note": "HBM fraction at the larger of the bytes' HBM floor and the digit pairs' tensor floor",
         "bytes_per_call": bytes_alg, "ms_per_call": ms_call, "peak_source": f"{pk['_source']} hbm_gbs",
         "tensor_digit_pairs": {"achieved": tensor_flops / t / 1e12, "peak": tpeak, "unit": "TFLOP/s",
                                "frac": tensor_flops / t / 1e12 / tpeak,

@@ -29,6 +29,20 @@ def test_apply_bytes_of_the_headline_workload():
     assert abs(e["achieved"] - 1141.112832) < 1e-9 and abs(e["frac"] - 1.141112832) < 1e-12
 
 
+def test_apply_ceiling_of_the_headline_workload():
+    """Digit pairs per call: c = A b and s - A^* dh at 7 digits (28 each), b - A^* h and
+    r = A s at 9 (45 each), plus the two m x m products per pass at 7; at the measured peaks
+    the pairs' tensor floor (0.366 ms) is above the bytes' HBM floor (0.168 ms)."""
+    w = workloads.WORKLOADS["dense_512x65536"]
+    opts = types.SimpleNamespace(apply_slices=7, resid_slices=9)
+    pk = {"hbm_gbs": 6780.7, "bf16_tflops": 1947.8, "bf16_tflops_sustained": 1724.9, "_source": "test"}
+    e = bench.apply_roofline(w, opts, 64, 1.0, 1, pk)
+    flops = 2.0 * 512 * 65536 * 64 * (28 + 45 + 45 + 28) + 2 * 2 * 2.0 * 512 * 512 * 64 * 28
+    t_pairs, t_bytes = flops / 1724.9e12, 1141112832 / 6780.7e9
+    assert abs(e["frac_ceiling"] - t_bytes / t_pairs) < 1e-12
+    assert 0.45 < e["frac_ceiling"] < 0.47
+
+
 def test_qr_flop_count():
     w = workloads.WORKLOADS["dense_512x65536"]
     o = types.SimpleNamespace(sketch_slices=5, gram_slices=7, gram2_slices=4, apply_slices=7, resid_slices=9,
